@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput of the GRPIC timestep on GB300.
+
+Workload (one GPU): Kerr a = 0.9 m, m = 4 cells, 128^3 grid, electron-ion plasma (mass ratio
+20), 8 particles per cell per species, u_th = 0.05 c, uniform contravariant B_z = 0.1,
+dt = 0.4 -- synthetic, seeded (paper_0904_0232_gb300.synth.kerr_ion_electron_128).
+
+A step is one whole cycle of the method: B half-step, push + deposit, B half-step, E step,
+removal + counting sort.  ``value`` counts particle-steps per second in the FP32-mixed path
+with inputs resident in HBM; the FP64 path is measured on the same state for comparison;
+``e2e`` repeats the measurement through the C ABI with host buffers (load, steps, read back).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grpic|reference]
+
+N > 1 (torchrun) runs N independent replicas, one per GPU (weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+RK4 Kerr push+deposit) FP32-mixed vs FP64; p50/p99 latency"
+UNIT = "particle-steps/s"
+
+# Arithmetic operations per particle-step of the push + deposit formulation (FMA = 2,
+# add/mul/div/sqrt = 1; index arithmetic excluded), by Gauss-Legendre order Q of Eq. 18.
+# Derivation table in DESIGN.md ("Algorithmic work per particle-step").
+ALG_FLOPS = {1: 3230, 2: 6890, 3: 12990}
+
+# Nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 lanes x 2 flops x 2070 MHz.
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
+
+# DRAM traffic of one push_deposit launch per particle, from an ncu capture (profiles/),
+# valid for the kernel source whose hash is recorded with it.
+PUSH_TRAFFIC = {"sha": None, "bytes_per_particle": None}
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("push.cu", "metric.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_0904_0232_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["grpic", "reference"], default="grpic")
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--quad", type=int, default=2)
+    p.add_argument("--sort-interval", type=int, default=1)
+    p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ---- distributed plumbing (replicas) ---------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+
+            td.init_process_group("gloo")
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v):
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks sampled during the timed region ---------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- CPU baseline (the oracle, as it stands) ---------------------------------------------------
+def cpu_sample_workload():
+    from paper_0904_0232_gb300 import synth
+
+    return synth.kerr_ion_electron_128(seed=2, n=40, max_particles=20000)
+
+
+def run_oracle_steps(wl, steps, warmup=0):
+    import oracle as O
+
+    o = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=0)
+    o.init_uniform_field(B=(0.0, 0.0, wl.B0))
+    for s, sp in enumerate(wl.species):
+        o.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=1)
+    for _ in range(warmup):
+        o.step(1)
+    n_before = sum(o.num_particles(s) for s in range(len(wl.species)))
+    t0 = time.perf_counter()
+    psteps = 0
+    per_step = []
+    for _ in range(steps):
+        n = sum(o.num_particles(s) for s in range(len(wl.species)))
+        t1 = time.perf_counter()
+        o.step(1)
+        per_step.append(time.perf_counter() - t1)
+        psteps += n
+    el = time.perf_counter() - t0
+    del n_before
+    return psteps, el, O.max_threads(), per_step
+
+
+def cpu_baseline(steps=6):
+    wl = cpu_sample_workload()
+    psteps, el, cores, _ = run_oracle_steps(wl, steps)
+    return {"value": psteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, Kerr a=0.9m m=4 on a {wl.nx}^3 window, {wl.n_particles} particles "
+                      f"(2 species), {steps} whole steps incl. field solve; {el:.1f} s wall"}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return None
+    wl = cpu_sample_workload()
+    psteps, el, cores, per = run_oracle_steps(wl, args.steps, warmup=args.warmup)
+    v = psteps / el
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kerr_ion_electron_128 (bounded CPU sample: 40^3 window, 40000 particles)",
+                       "grid": wl.nx, "particles": wl.n_particles, "m": wl.m, "a": wl.a, "dt": wl.dt},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of the 40^3 / 40000-particle sample"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---- GPU arm ------------------------------------------------------------------------------------
+def make_sim(wl, precision, args, device_inputs=True):
+    import torch
+
+    from paper_0904_0232_gb300.grpic import GRPIC_U_COV_SPATIAL, Simulation
+
+    sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=args.quad,
+                     sort_interval=args.sort_interval)
+    sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
+    for s, sp in enumerate(wl.species):
+        if device_inputs:
+            x = torch.from_numpy(sp.x4).cuda()
+            u = torch.from_numpy(np.vstack([sp.usp, np.zeros((1, sp.usp.shape[1]))])).cuda()
+            i = torch.from_numpy(sp.ids.view(np.int32)).cuda()
+            sim.load_particles(s, sp.q_over_m, sp.q_macro, x, u, i, umode=GRPIC_U_COV_SPATIAL)
+            del x, u, i
+        else:
+            sim.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=GRPIC_U_COV_SPATIAL)
+    torch.cuda.synchronize()
+    return sim
+
+
+def timed_steps(sim, steps, dist):
+    import torch
+
+    stream = torch.cuda.current_stream()
+    sim.sync()
+    st0 = sim.stats()["particle_steps"]
+    sim.profile(reset=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    prof, launches = sim.profile(reset=True)
+    psteps = sim.stats()["particle_steps"] - st0
+    return ms, psteps, prof, launches
+
+
+def run_gpu(args, dist):
+    import torch
+
+    from paper_0904_0232_gb300 import synth
+    from paper_0904_0232_gb300.build import build
+    from paper_0904_0232_gb300.grpic import GRPIC_FP32_MIXED, grpic_probe_fma_peak
+
+    torch.cuda.set_device(dist.local)
+    build()
+    wl = synth.kerr_ion_electron_128(seed=2, n=args.grid)
+
+    # --- FP32-mixed, inputs resident in HBM
+    sim = make_sim(wl, "fp32_mixed", args)
+    sim.set_profiling(True)
+    sim.step(args.warmup)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    ms, psteps, prof, launches = timed_steps(sim, args.steps, dist)
+    clk = clocks.stop()
+    st = sim.stats()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    t_max = dist.max(ms)
+    psteps_all = dist.sum(psteps)
+    value = psteps_all / (t_max * 1e-3)
+
+    push_ms, push_n = prof["push_deposit"]
+    # one push stage = one launch per species; per-launch figures use the stage average
+    flops = ALG_FLOPS[args.quad] * psteps
+    achieved = flops / (push_ms * 1e-3) if push_ms > 0 else 0.0
+    fp32_probe = grpic_probe_fma_peak(GRPIC_FP32_MIXED)
+    sha = kernel_sha()
+    traffic = None
+    if PUSH_TRAFFIC["sha"] == sha and PUSH_TRAFFIC["bytes_per_particle"]:
+        traffic = PUSH_TRAFFIC["bytes_per_particle"] * psteps / max(1, push_n)
+
+    # --- FP64 path on the same workload (fewer steps; FP64 runs at a small fraction of FP32)
+    fp64 = None
+    if args.fp64_steps > 0:
+        sim64 = make_sim(wl, "fp64", args)
+        sim64.set_profiling(True)
+        sim64.step(1)
+        ms64, ps64, prof64, _ = timed_steps(sim64, args.fp64_steps, dist)
+        sim64.close()
+        del sim64
+        torch.cuda.empty_cache()
+        fp64 = {"value": dist.sum(ps64) / (dist.max(ms64) * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "push_ms_per_step": prof64["push_deposit"][0] / args.fp64_steps}
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        d_h2d = d_d2h = 0
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = make_sim(wl, "fp32_mixed", args, device_inputs=False)
+        d_h2d = sum(sp.x4.nbytes + sp.usp.nbytes * 4 // 3 + sp.ids.nbytes for sp in wl.species)
+        sim.step_async(args.steps)
+        out_bytes = 0
+        for s in range(len(wl.species)):
+            x, u, ids = sim.get_particles(s)
+            out_bytes += x.nbytes + u.nbytes + ids.nbytes
+        d, b, J = sim.get_fields()
+        out_bytes += d.nbytes + b.nbytes + J.nbytes
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ps_e2e = sim.stats()["particle_steps"]
+        sim.close()
+        el = dist.max(el)
+        e2e = {"value": dist.sum(ps_e2e) / el, "unit": UNIT, "h2d_bytes_per_step": int(d_h2d / args.steps),
+               "d2h_bytes_per_step": int(out_bytes / args.steps),
+               "includes": "field init + particle load from host, u^4 completion, K steps, particle/field readback"}
+        del d_d2h
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    stage_ms = {k: round(v[0] / max(1, args.steps), 4) for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 metric/Christoffel for R^2 < 16m^2 + a^2; FP64 J)",
+        "data": "synthetic (seeded generator; stands in for the paper's disk/corona plasma)",
+        "config": {"workload": f"kerr_ion_electron_{args.grid}: Kerr a=0.9m, m=4 cells, {args.grid}^3 grid, "
+                               "e-/ion (mass ratio 20), 8 ppc per species, u_th=0.05c, B_z=0.1, dt=0.4",
+                   "particles": wl.n_particles, "quad_order": args.quad, "sort_interval": args.sort_interval,
+                   "parallelism": f"replicas x{dist.world}",
+                   "l2": "inputs larger than L2 (particle store %.2f GB)" % (wl.n_particles * 40 / 1e9)},
+        "gpu_launches": int(launches),
+        "stage_ms_per_step": stage_ms,
+        "roofline": {"kernel": "k_push_deposit (FP32-mixed)", "bound": "alu", "achieved": achieved / 1e12,
+                     "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_NOMINAL,
+                     "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)",
+                     "fma_probe_tflops": fp32_probe / 1e12,
+                     "flops_per_particle_step": ALG_FLOPS[args.quad], "kernel_sha": sha},
+        "fp64": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "stats": {k: st[k] for k in ("removed_horizon", "removed_outer", "gamma_fallbacks", "fp64_evals")},
+    }
+    return line
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        line = run_reference(args, dist)
+    else:
+        line = run_gpu(args, dist)
+    if dist.rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * grpic.h -- C ABI of the GB300 GRPIC library.
+ *
+ * One general-relativistic electromagnetic particle-in-cell timestep (Watson & Nishikawa,
+ * "A Method for Incorporating General Relativity in Electromagnetic Particle-in-Cell Code",
+ * arXiv:0904.0232) on one GPU: the B half-step, the per-particle gather + Kerr metric /
+ * Christoffel + RK4 four-velocity push + curved-metric current deposit, the second B
+ * half-step and the E step (Sec. 2.2, Fig. 1), followed by horizon / outer-boundary removal
+ * and a counting sort of the particles by cell.
+ *
+ * Conventions shared by every call
+ *   - Units: cell size 1 on all axes; x^4 = c t (Sec. 3); indices 1..4 of the paper are 0..3
+ *     here (x, y, z, x^4).  The central mass sits at ((nx-1)/2, (ny-1)/2, (nz-1)/2).
+ *   - Grid arrays are nz*ny*nx doubles, index (k*ny + j)*nx + i, three components back to
+ *     back (3*nz*ny*nx doubles).  Prognostic field components and their Yee locations:
+ *       d = F^{x4}, F^{y4}, F^{z4}  (contravariant; edges (i+1/2,j,k), (i,j+1/2,k), (i,j,k+1/2))
+ *       b = F_{yz}, F_{zx}, F_{xy}  (covariant;     faces (i,j+1/2,k+1/2), (i+1/2,j,k+1/2),
+ *                                                          (i+1/2,j+1/2,k))
+ *       J = J^x, J^y, J^z          (contravariant current density, at the d locations)
+ *     (Eq. 8 gives F^{4j} = E^j and F^{jk} = eps^{jkl} B^l for the contravariant tensor.)
+ *   - Particle arrays are planar: x4 holds x^1[0..n), x^2[0..n), x^3[0..n), x^4[0..n); u4 the
+ *     four-velocity u^1..u^4 (u^4 = c dt/dtau) alike.
+ *   - Memory: every pointer argument is host memory unless the call's `mem` / flags argument
+ *     says GRPIC_MEM_DEVICE, in which case it is device memory of the context's GPU.  The
+ *     library copies inputs; outputs go to caller-owned buffers.  The caller keeps ownership
+ *     of everything it passes.
+ *   - Streams: all device work of a context is ordered on the stream given to grpic_create.
+ *     Calls that return data synchronise that stream; grpic_step_async does not.
+ *   - Errors: every call returns a grpic_status; nothing is thrown across the ABI.  Device-side
+ *     faults (non-finite state, a particle moving a cell or more in one step) are recorded in a
+ *     device status word and reported by the next synchronising call; grpic_last_error() gives
+ *     a message.  After GRPIC_ERR_CFL or GRPIC_ERR_NONFINITE the state of the step is undefined.
+ *   - Thread safety: a context is used by one host thread at a time.
+ */
+#ifndef GRPIC_H_
+#define GRPIC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GRPIC_OK = 0,
+  GRPIC_ERR_INVALID = 1,   /* bad argument, or a particle/field input the method cannot take */
+  GRPIC_ERR_OOM = 2,       /* device allocation failed */
+  GRPIC_ERR_CUDA = 3,      /* a CUDA call failed */
+  GRPIC_ERR_CFL = 4,       /* c dt >= 1/sqrt(3) at create, or |dx^i| >= 1 cell in one step */
+  GRPIC_ERR_NONFINITE = 5, /* NaN/Inf in particle state */
+  GRPIC_ERR_TIMEOUT = 6,   /* a bounded wait gave up */
+  GRPIC_ERR_AGAIN = 7,     /* serving: request not finished / not admitted yet */
+  GRPIC_ERR_CAPACITY = 8   /* more particles than the context's capacity */
+} grpic_status;
+
+enum { GRPIC_FP64 = 0, GRPIC_FP32_MIXED = 1 };
+
+enum {
+  GRPIC_NO_GAMMA_IN_J = 1u /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
+};
+
+enum { GRPIC_MEM_HOST = 0, GRPIC_MEM_DEVICE = 1 };
+
+/* grpic_load_particles flags: how u4 is given (bits 0-1) and where the arrays live (bit 4). */
+enum {
+  GRPIC_U_FULL = 0,          /* u4 holds u^1..u^4 as is */
+  GRPIC_U_COV_SPATIAL = 1,   /* planes 0..2 hold covariant u_1..u_3; u^a is completed on the device */
+  GRPIC_U_CONTRA_SPATIAL = 2,/* planes 0..2 hold u^1..u^3; u^4 is completed (needs g_44 < 0) */
+  GRPIC_LOAD_DEVICE = 16     /* x4, u4, ids are device pointers */
+};
+
+/* Pipeline stages for grpic_stage (each is one row of the timestep). */
+enum {
+  GRPIC_STAGE_B_HALF = 0,       /* Sec. 3.1, Eq. 10: b <- b - (dx^4/2) curl e */
+  GRPIC_STAGE_ZERO_J = 1,       /* J <- 0 */
+  GRPIC_STAGE_PUSH_DEPOSIT = 2, /* Sec. 3.3 + Sec. 4: RK4 push, curved deposit, removal flags */
+  GRPIC_STAGE_E = 3,            /* Sec. 3.2, Eq. 12: d <- d + dx^4 (4 pi/c J - div F) */
+  GRPIC_STAGE_SORT = 4          /* counting sort by cell; drops removed particles */
+};
+
+typedef void* (*grpic_alloc_fn)(size_t bytes, void* user);
+typedef void (*grpic_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int nx, ny, nz;        /* nodes per axis, each >= 8 */
+  double m;              /* mass of the central object, in cells (Eq. 4), >= 0 */
+  double a;              /* spin parameter, |a| <= m (Eqs. 4-6) */
+  double c;              /* speed of light, cells per unit time */
+  double dt;             /* time step; c dt < 1/sqrt(3) is required */
+  int precision;         /* GRPIC_FP64 or GRPIC_FP32_MIXED */
+  int quad_order;        /* Q of the Q x Q Gauss-Legendre rule of Eq. 18: 1, 2 or 3 (0 -> 2) */
+  double r_excise;       /* fields at r < r_excise are frozen; <= 0 -> 0.5 r_+ */
+  unsigned flags;        /* GRPIC_NO_GAMMA_IN_J */
+  int sort_interval;     /* counting sort every k steps (<= 0 -> 1) */
+  int64_t max_particles; /* capacity per species (0 -> set by the first load) */
+  grpic_alloc_fn alloc;  /* device allocator (NULL -> cudaMalloc); e.g. a PyTorch caching allocator */
+  grpic_free_fn free_fn; /* matching free */
+  void* alloc_user;      /* passed to alloc / free_fn */
+} grpic_config;
+
+typedef struct {
+  int64_t steps;            /* timesteps taken */
+  int64_t removed_horizon;  /* particles removed at r <= r_+ */
+  int64_t removed_outer;    /* particles removed outside [1, n-2] */
+  int64_t gamma_fallbacks;  /* Eq. 16 square-root argument < 0: gamma_1 = u^4/c used */
+  int64_t fp64_evals;       /* FP32-mixed: metric evaluations promoted to FP64 (r < 4m region) */
+  int64_t particle_steps;   /* particles advanced, summed over steps */
+  int64_t n_alive[4];       /* particles per species after the last sort */
+} grpic_stats;
+
+typedef struct grpic_ctx grpic_ctx;
+
+/* Create a context on the current CUDA device.  Validates the configuration (Courant:
+ * c dt < 1/sqrt(3), Sec. 5), computes r_+ = m + sqrt(m^2 - a^2), and caches the metric at
+ * every field location.  `stream` is a cudaStream_t (NULL = default stream).
+ * Returns GRPIC_ERR_INVALID / GRPIC_ERR_CFL on bad input, GRPIC_ERR_OOM if allocation fails. */
+grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out);
+
+/* Free all device memory of the context (stream-ordered) and the context itself. */
+grpic_status grpic_destroy(grpic_ctx* ctx);
+
+/* Set the prognostic field: d (3 planes, contravariant F^{i4}) and b (3 planes, covariant
+ * F_{yz}, F_{zx}, F_{xy}) at their Yee locations (Sec. 3, Fig. 2).  FP32_MIXED rounds them. */
+grpic_status grpic_set_fields(grpic_ctx* ctx, const double* d3, const double* b3, int mem);
+
+/* Set a uniform contravariant field (Eq. 8: F^{4j} = E^j, F^{jk} = eps^{jkl} B^l) and convert
+ * it to the prognostic components at every location with the metric there (Sec. 6 starts from
+ * a uniform contravariant B_z). */
+grpic_status grpic_set_uniform_field(grpic_ctx* ctx, const double E_contra[3], const double B_contra[3]);
+
+/* Set J (3 planes); used to drive the E step on its own. */
+grpic_status grpic_set_j(grpic_ctx* ctx, const double* J3, int mem);
+
+/* Load (replace) the particles of one species (0..3): charge-to-mass ratio q/m of the push
+ * (Eq. 15), macro-particle charge q_macro of the deposit (Sec. 4), n particles with planar
+ * positions x4 and velocities u4 (see flags), and ids.  Positions must lie in [1, n_axis-2];
+ * completed four-velocities are the future-directed root of g_mn u^m u^n = -c^2.
+ * Returns GRPIC_ERR_INVALID for out-of-domain positions or an impossible completion,
+ * GRPIC_ERR_CAPACITY if n exceeds max_particles. */
+grpic_status grpic_load_particles(grpic_ctx* ctx, int species, double q_over_m, double q_macro, int64_t n,
+                                  const double* x4, const double* u4, const uint32_t* ids, int flags);
+
+/* Advance nsteps timesteps (Sec. 2.2 cycle: B half, push + deposit, B half, E; removal and
+ * sort), then synchronise and report the device status. */
+grpic_status grpic_step(grpic_ctx* ctx, int nsteps);
+
+/* As grpic_step, without the final synchronisation; errors surface at the next grpic_sync. */
+grpic_status grpic_step_async(grpic_ctx* ctx, int nsteps);
+
+/* Run one stage of the timestep (GRPIC_STAGE_*), then synchronise. */
+grpic_status grpic_stage(grpic_ctx* ctx, int stage);
+
+/* Wait for the context's stream and report the device status. */
+grpic_status grpic_sync(grpic_ctx* ctx);
+
+/* Copy out the prognostic field and J (any pointer may be NULL). */
+grpic_status grpic_get_fields(grpic_ctx* ctx, double* d3, double* b3, double* J3, int mem);
+
+/* Number of live particles of a species. */
+grpic_status grpic_num_particles(grpic_ctx* ctx, int species, int64_t* n);
+
+/* Copy out the live particles of a species in the library's (cell-sorted) order, with ids.
+ * *n_inout: capacity of the caller's arrays on entry, particles written on return.
+ * x^4 is returned as the particle's own clock coordinate. */
+grpic_status grpic_get_particles(grpic_ctx* ctx, int species, int64_t* n_inout, double* x4, double* u4,
+                                 uint32_t* ids, int mem);
+
+grpic_status grpic_get_stats(grpic_ctx* ctx, grpic_stats* out);
+
+/* Message for the last error on this context ("" if none); valid until the next call. */
+const char* grpic_last_error(const grpic_ctx* ctx);
+
+/* Name of a status code. */
+const char* grpic_status_string(grpic_status s);
+
+/* Tracing (not in the paper).  With profiling on, each stage is bracketed by CUDA events on
+ * the context stream; grpic_get_profile returns, per GRPIC_STAGE_*, the accumulated device
+ * milliseconds and the number of times the stage ran since the last reset (reset = 1 clears
+ * after reading), plus the number of kernels the library has launched in total. */
+grpic_status grpic_set_profiling(grpic_ctx* ctx, int on);
+grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[5], int64_t counts[5], int64_t* kernel_launches,
+                               int reset);
+
+/* Measure the sustained fused-multiply-add rate of this GPU's CUDA cores (not the tensor
+ * cores) with independent FMA chains in every lane: precision GRPIC_FP32_MIXED measures FP32,
+ * GRPIC_FP64 measures FP64.  *flops_per_s counts an FMA as two operations.  Used as the
+ * roofline denominator of the ALU-bound push. */
+grpic_status grpic_probe_fma_peak(int precision, double* flops_per_s);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched engine: many independent contexts advanced together.  Each stage of the timestep
+ * is one persistent launch over all (instance, work item) pairs read from a device table;
+ * the per-step stage sequence is captured once in a CUDA graph and replayed.
+ * Not in the paper: it runs the paper's cycle for several simulations at once.
+ * ------------------------------------------------------------------------------------- */
+typedef struct grpic_batch grpic_batch;
+
+/* Group n contexts, all FP32_MIXED or all FP64 and all on `stream`.  The contexts stay owned
+ * by the caller and must outlive the batch. */
+grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grpic_batch** out);
+grpic_status grpic_batch_step(grpic_batch* b, int nsteps);
+grpic_status grpic_batch_destroy(grpic_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRPIC_H_ */

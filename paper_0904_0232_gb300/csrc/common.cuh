@@ -1,0 +1,108 @@
+// Internal types shared by the CUDA translation units of the GRPIC library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grpic {
+
+constexpr uint32_t kDead = 0xffffffffu;  // sort key of a removed particle
+
+// Device status word (sticky until read by the host).
+enum : unsigned {
+  ST_NONFINITE = 1u,
+  ST_CFL = 2u,
+  ST_RANGE = 4u,        // an index had to be clamped (a position left the grid)
+  ST_LOAD_INVALID = 8u, // a loaded particle was outside the domain or had no u^4 solution
+  ST_LOAD_ERGO = 16u,   // contravariant u^i given where g_44 >= 0
+};
+
+struct DevStatus {
+  unsigned flags;
+  unsigned pad;
+  unsigned long long removed_horizon;
+  unsigned long long removed_outer;
+  unsigned long long fallbacks;
+  unsigned long long fp64_evals;
+  unsigned long long pushed;  // particle-steps advanced
+};
+
+// Geometry and constants of one simulation, passed by value to every kernel.
+struct Grid {
+  int nx, ny, nz;
+  long long ncell;
+  double m, a, c, dt;
+  double xc, yc, zc;  // centre of mass in grid coordinates
+  double r_plus, r_exc;
+  int quad_order;
+  unsigned flags;
+};
+
+// Field views.  Metric cache: for each of the 6 field locations of a cell, (f, k0, k1, k2)
+// as 4 planes -> mc[(loc*4 + q)*ncell + cell].  mask bit l of a cell: location l is advanced.
+template <typename T>
+struct Fields {
+  T* d[3];
+  T* b[3];
+  T* s[3];       // scratch: covariant e (B step) or contravariant h (E step)
+  double* J[3];
+  const T* mc;
+  const uint8_t* mask;
+};
+
+template <typename T>
+struct Particles {
+  T* x[4];  // x^1..x^3 in grid units; x[3] holds x^4 - c t_n
+  T* u[4];
+  uint32_t* id;
+  uint32_t* key;
+  long long n;       // entries in the arrays (live + removed-not-yet-sorted)
+  const int* n_dev;  // live+flagged count after the last sort (device)
+};
+
+__host__ __device__ inline long long cell_index(const Grid& g, int i, int j, int k) {
+  return ((long long)k * g.ny + j) * g.nx + i;
+}
+
+// ---- launchers (defined in fields.cu, push.cu, sort.cu) --------------------------------
+template <typename T>
+void launch_metric_cache(const Grid& g, T* mc, uint8_t* mask, cudaStream_t st);
+template <typename T>
+void launch_b_half(const Grid& g, const Fields<T>& F, cudaStream_t st);
+template <typename T>
+void launch_e_step(const Grid& g, const Fields<T>& F, cudaStream_t st);
+template <typename T>
+void launch_uniform_field(const Grid& g, const Fields<T>& F, const double E[3], const double B[3], cudaStream_t st);
+template <typename T>
+void launch_convert_in(T* dst, const double* src, long long n, cudaStream_t st);
+template <typename T>
+void launch_convert_out(double* dst, const T* src, long long n, cudaStream_t st);
+
+struct Species {
+  double qm, qmacro;
+};
+
+template <typename T>
+void launch_push_deposit(const Grid& g, const Fields<T>& F, const Particles<T>& P, const Species& sp,
+                         DevStatus* st, bool mixed, double t_offset, cudaStream_t stream);
+
+template <typename T>
+void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,
+                           const uint32_t* ids, int umode, double ct_now, DevStatus* st, cudaStream_t stream);
+template <typename T>
+void launch_unload_particles(const Particles<T>& P, long long n, double* x4, double* u4, uint32_t* ids,
+                             double ct_now, cudaStream_t stream);
+
+// Counting sort by cell of one species; removed particles (key == kDead) are dropped.
+// counts: nbins+1 ints, offsets: nbins+1 ints, blocks: scan scratch; n_out: device int.
+struct SortScratch {
+  int* counts;
+  int* offsets;
+  int* blocks;
+  int nblocks;
+};
+template <typename T>
+void launch_sort(const Grid& g, const Particles<T>& src, const Particles<T>& dst, const SortScratch& s,
+                 int* n_out, cudaStream_t stream);
+
+}  // namespace grpic

@@ -1,0 +1,750 @@
+// Host side of the GRPIC C ABI (include/grpic.h): context lifecycle, memory, the
+// stream-ordered timestep pipeline of Sec. 2.2 (Fig. 1) and the device status word.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grpic.h"
+#include "common.cuh"
+
+using namespace grpic;
+
+namespace grpic {
+int scan_tiles(long long nbins);
+}
+
+namespace {
+
+constexpr int kMaxSpecies = 4;
+
+struct SpeciesStore {
+  double qm = 0.0, qmacro = 0.0;
+  long long n = 0;    // array entries (upper bound of the live count)
+  long long cap = 0;  // capacity in particles
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  int* n_dev = nullptr;
+  int* n_shadow = nullptr;  // pinned host copy of n_dev
+  cudaEvent_t shadow_ev = nullptr;
+  bool shadow_pending = false;
+  bool loaded = false;
+};
+
+}  // namespace
+
+struct grpic_ctx {
+  grpic_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Grid g{};
+  bool mixed = false;
+  size_t tsize = 8;
+  std::string err;
+  void* fields = nullptr;  // 9 planes of T: d[3], b[3], scratch[3]
+  double* J = nullptr;     // 3 planes
+  void* mc = nullptr;      // 24 planes of T
+  uint8_t* mask = nullptr;
+  DevStatus* st = nullptr;
+  DevStatus* st_host = nullptr;  // pinned
+  SortScratch sort{};
+  SpeciesStore sp[kMaxSpecies];
+  long long steps = 0;
+  int since_sort = 0;
+  grpic_stats totals{};
+  // tracing
+  long long launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending {
+    cudaEvent_t a, b;
+    int stage;
+  };
+  std::vector<Pending> pending;
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  long long prof_cnt[5] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+void* dev_alloc(grpic_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (c->cfg.alloc) return c->cfg.alloc(bytes, c->cfg.alloc_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(grpic_ctx* c, void* p) {
+  if (!p) return;
+  if (c->cfg.free_fn) {
+    c->cfg.free_fn(p, c->cfg.alloc_user);
+    return;
+  }
+  cudaFree(p);
+}
+
+grpic_status fail(grpic_ctx* c, grpic_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+grpic_status cuda_check(grpic_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return GRPIC_OK;
+  return fail(c, GRPIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t particle_bytes(const grpic_ctx* c) { return 8 * c->tsize + 2 * sizeof(uint32_t); }
+
+template <typename T>
+Fields<T> fields_view(grpic_ctx* c) {
+  Fields<T> F;
+  T* base = static_cast<T*>(c->fields);
+  for (int q = 0; q < 3; ++q) {
+    F.d[q] = base + (size_t)q * c->g.ncell;
+    F.b[q] = base + (size_t)(3 + q) * c->g.ncell;
+    F.s[q] = base + (size_t)(6 + q) * c->g.ncell;
+    F.J[q] = c->J + (size_t)q * c->g.ncell;
+  }
+  F.mc = static_cast<const T*>(c->mc);
+  F.mask = c->mask;
+  return F;
+}
+
+template <typename T>
+Particles<T> particles_view(grpic_ctx* c, int s, int which) {
+  SpeciesStore& S = c->sp[s];
+  Particles<T> P;
+  char* base = static_cast<char*>(S.buf[which]);
+  const size_t cap = (size_t)S.cap;
+  for (int q = 0; q < 4; ++q) {
+    P.x[q] = reinterpret_cast<T*>(base + q * cap * sizeof(T));
+    P.u[q] = reinterpret_cast<T*>(base + (4 + q) * cap * sizeof(T));
+  }
+  P.id = reinterpret_cast<uint32_t*>(base + 8 * cap * sizeof(T));
+  P.key = reinterpret_cast<uint32_t*>(base + 8 * cap * sizeof(T) + cap * sizeof(uint32_t));
+  P.n = S.n;
+  P.n_dev = S.n_dev;
+  return P;
+}
+
+// Refresh the host upper bound of the live count from the last completed shadow copy.
+void refresh_count(SpeciesStore& S) {
+  if (S.shadow_pending && cudaEventQuery(S.shadow_ev) == cudaSuccess) {
+    S.n = std::min<long long>(S.n, *S.n_shadow);
+    S.shadow_pending = false;
+  }
+}
+
+template <typename T>
+void enqueue_stage(grpic_ctx* c, int stage) {
+  Fields<T> F = fields_view<T>(c);
+  switch (stage) {
+    case GRPIC_STAGE_B_HALF:
+      launch_b_half<T>(c->g, F, c->stream);
+      c->launches += 2;
+      break;
+    case GRPIC_STAGE_ZERO_J:
+      cudaMemsetAsync(c->J, 0, sizeof(double) * 3 * (size_t)c->g.ncell, c->stream);
+      break;
+    case GRPIC_STAGE_PUSH_DEPOSIT:
+      for (int s = 0; s < kMaxSpecies; ++s) {
+        SpeciesStore& S = c->sp[s];
+        if (!S.loaded || S.n == 0) continue;
+        refresh_count(S);
+        Species spc{S.qm, S.qmacro};
+        launch_push_deposit<T>(c->g, F, particles_view<T>(c, s, S.cur), spc, c->st, c->mixed, 0.0, c->stream);
+        c->launches += 1;
+      }
+      break;
+    case GRPIC_STAGE_E:
+      launch_e_step<T>(c->g, F, c->stream);
+      c->launches += 2;
+      break;
+    case GRPIC_STAGE_SORT:
+      for (int s = 0; s < kMaxSpecies; ++s) {
+        SpeciesStore& S = c->sp[s];
+        if (!S.loaded) continue;
+        launch_sort<T>(c->g, particles_view<T>(c, s, S.cur), particles_view<T>(c, s, 1 - S.cur), c->sort, S.n_dev,
+                       c->stream);
+        c->launches += S.n > 0 ? 6 : 4;
+        S.cur = 1 - S.cur;
+        cudaMemcpyAsync(S.n_shadow, S.n_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        cudaEventRecord(S.shadow_ev, c->stream);
+        S.shadow_pending = true;
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+cudaEvent_t pool_event(grpic_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold finished stage timings into the totals (called after the stream is synchronised).
+void collect_profile(grpic_ctx* c) {
+  for (const auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.stage] += ms;
+      c->prof_cnt[p.stage] += 1;
+    }
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
+void enqueue_stage_any(grpic_ctx* c, int stage) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->profiling) {
+    a = pool_event(c);
+    b = pool_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  if (c->mixed)
+    enqueue_stage<float>(c, stage);
+  else
+    enqueue_stage<double>(c, stage);
+  if (c->profiling) {
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({a, b, stage});
+  }
+}
+
+// One timestep (Sec. 2.2): B half, J = 0, push + deposit, B half, E; then removal + sort.
+void enqueue_step(grpic_ctx* c) {
+  enqueue_stage_any(c, GRPIC_STAGE_B_HALF);
+  enqueue_stage_any(c, GRPIC_STAGE_ZERO_J);
+  enqueue_stage_any(c, GRPIC_STAGE_PUSH_DEPOSIT);
+  enqueue_stage_any(c, GRPIC_STAGE_B_HALF);
+  enqueue_stage_any(c, GRPIC_STAGE_E);
+  c->steps += 1;
+  if (++c->since_sort >= std::max(1, c->cfg.sort_interval)) {
+    enqueue_stage_any(c, GRPIC_STAGE_SORT);
+    c->since_sort = 0;
+  }
+}
+
+grpic_status read_status(grpic_ctx* c) {
+  grpic_status s = cuda_check(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                                                 c->stream),
+                              "status copy");
+  if (s != GRPIC_OK) return s;
+  s = cuda_check(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (s != GRPIC_OK) return s;
+  collect_profile(c);
+  const DevStatus h = *c->st_host;
+  c->totals.removed_horizon = (int64_t)h.removed_horizon;
+  c->totals.removed_outer = (int64_t)h.removed_outer;
+  c->totals.gamma_fallbacks = (int64_t)h.fallbacks;
+  c->totals.fp64_evals = (int64_t)h.fp64_evals;
+  c->totals.particle_steps = (int64_t)h.pushed;
+  if (h.flags) {
+    // clear the sticky flags now that they are reported
+    cudaMemsetAsync(&c->st->flags, 0, sizeof(unsigned), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (h.flags & ST_NONFINITE) return fail(c, GRPIC_ERR_NONFINITE, "non-finite particle state");
+    if (h.flags & (ST_CFL | ST_RANGE))
+      return fail(c, GRPIC_ERR_CFL, "a particle moved a cell or more in one step (or left the grid)");
+    if (h.flags & ST_LOAD_ERGO)
+      return fail(c, GRPIC_ERR_INVALID, "contravariant u^i given where g_44 >= 0 (ergoregion): ambiguous u^4");
+    if (h.flags & ST_LOAD_INVALID)
+      return fail(c, GRPIC_ERR_INVALID, "particle outside [1, n-2] or without a future-directed unit u");
+  }
+  return GRPIC_OK;
+}
+
+grpic_status ensure_capacity(grpic_ctx* c, int s, long long n) {
+  SpeciesStore& S = c->sp[s];
+  long long want = std::max<long long>(n, c->cfg.max_particles);
+  if (c->cfg.max_particles > 0 && n > c->cfg.max_particles)
+    return fail(c, GRPIC_ERR_CAPACITY, "more particles than max_particles");
+  if (S.cap >= want && S.buf[0]) return GRPIC_OK;
+  for (int b = 0; b < 2; ++b) {
+    dev_free(c, S.buf[b]);
+    S.buf[b] = nullptr;
+  }
+  const size_t bytes = (size_t)std::max<long long>(want, 1) * particle_bytes(c);
+  for (int b = 0; b < 2; ++b) {
+    S.buf[b] = dev_alloc(c, bytes);
+    if (!S.buf[b]) return fail(c, GRPIC_ERR_OOM, "particle store allocation failed");
+  }
+  S.cap = std::max<long long>(want, 1);
+  return GRPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grpic_status_string(grpic_status s) {
+  switch (s) {
+    case GRPIC_OK: return "GRPIC_OK";
+    case GRPIC_ERR_INVALID: return "GRPIC_ERR_INVALID";
+    case GRPIC_ERR_OOM: return "GRPIC_ERR_OOM";
+    case GRPIC_ERR_CUDA: return "GRPIC_ERR_CUDA";
+    case GRPIC_ERR_CFL: return "GRPIC_ERR_CFL";
+    case GRPIC_ERR_NONFINITE: return "GRPIC_ERR_NONFINITE";
+    case GRPIC_ERR_TIMEOUT: return "GRPIC_ERR_TIMEOUT";
+    case GRPIC_ERR_AGAIN: return "GRPIC_ERR_AGAIN";
+    case GRPIC_ERR_CAPACITY: return "GRPIC_ERR_CAPACITY";
+  }
+  return "GRPIC_ERR_UNKNOWN";
+}
+
+const char* grpic_last_error(const grpic_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out) {
+  if (!cfg || !out) return GRPIC_ERR_INVALID;
+  *out = nullptr;
+  if (cfg->nx < 8 || cfg->ny < 8 || cfg->nz < 8) return GRPIC_ERR_INVALID;
+  if (!(cfg->m >= 0.0) || !(std::fabs(cfg->a) <= cfg->m) || !(cfg->c > 0.0) || !(cfg->dt > 0.0))
+    return GRPIC_ERR_INVALID;
+  if (cfg->precision != GRPIC_FP64 && cfg->precision != GRPIC_FP32_MIXED) return GRPIC_ERR_INVALID;
+  if (cfg->quad_order < 0 || cfg->quad_order > 3) return GRPIC_ERR_INVALID;
+  if ((cfg->alloc == nullptr) != (cfg->free_fn == nullptr)) return GRPIC_ERR_INVALID;
+  const long long ncell = (long long)cfg->nx * cfg->ny * cfg->nz;
+  if (ncell + 1 >= (1ll << 31)) return GRPIC_ERR_INVALID;
+  // Courant condition of the Yee update (Sec. 5): c dt < dx / sqrt(3)
+  if (!(cfg->c * cfg->dt < 1.0 / std::sqrt(3.0))) return GRPIC_ERR_CFL;
+
+  grpic_ctx* c = new grpic_ctx();
+  c->cfg = *cfg;
+  if (c->cfg.quad_order == 0) c->cfg.quad_order = 2;
+  if (c->cfg.sort_interval <= 0) c->cfg.sort_interval = 1;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  c->mixed = cfg->precision == GRPIC_FP32_MIXED;
+  c->tsize = c->mixed ? sizeof(float) : sizeof(double);
+  Grid& g = c->g;
+  g.nx = cfg->nx;
+  g.ny = cfg->ny;
+  g.nz = cfg->nz;
+  g.ncell = ncell;
+  g.m = cfg->m;
+  g.a = cfg->a;
+  g.c = cfg->c;
+  g.dt = cfg->dt;
+  g.xc = 0.5 * (cfg->nx - 1);
+  g.yc = 0.5 * (cfg->ny - 1);
+  g.zc = 0.5 * (cfg->nz - 1);
+  g.r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
+  g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : 0.5 * g.r_plus;
+  g.quad_order = c->cfg.quad_order;
+  g.flags = cfg->flags;
+
+  c->fields = dev_alloc(c, 9 * (size_t)ncell * c->tsize);
+  c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));
+  c->mc = dev_alloc(c, 24 * (size_t)ncell * c->tsize);
+  c->mask = static_cast<uint8_t*>(dev_alloc(c, (size_t)ncell));
+  c->st = static_cast<DevStatus*>(dev_alloc(c, sizeof(DevStatus)));
+  const long long nbins = ncell + 1;
+  c->sort.nblocks = scan_tiles(nbins);
+  c->sort.counts = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
+  c->sort.offsets = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
+  c->sort.blocks = static_cast<int*>(dev_alloc(c, sizeof(int) * (c->sort.nblocks + 1)));
+  bool ok = c->fields && c->J && c->mc && c->mask && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
+  for (int s = 0; s < kMaxSpecies && ok; ++s) {
+    c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
+    ok = c->sp[s].n_dev != nullptr;
+    if (ok) ok = cudaMallocHost(&c->sp[s].n_shadow, sizeof(int)) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&c->sp[s].shadow_ev, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (ok) ok = cudaMallocHost(&c->st_host, sizeof(DevStatus)) == cudaSuccess;
+  if (!ok) {
+    grpic_destroy(c);
+    return GRPIC_ERR_OOM;
+  }
+  cudaMemsetAsync(c->fields, 0, 9 * (size_t)ncell * c->tsize, c->stream);
+  cudaMemsetAsync(c->J, 0, 3 * (size_t)ncell * sizeof(double), c->stream);
+  cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+  for (int s = 0; s < kMaxSpecies; ++s) cudaMemsetAsync(c->sp[s].n_dev, 0, sizeof(int), c->stream);
+  if (c->mixed)
+    launch_metric_cache<float>(g, static_cast<float*>(c->mc), c->mask, c->stream);
+  else
+    launch_metric_cache<double>(g, static_cast<double*>(c->mc), c->mask, c->stream);
+  grpic_status s = cuda_check(c, cudaGetLastError(), "create");
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
+  if (s != GRPIC_OK) {
+    grpic_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_destroy(grpic_ctx* c) {
+  if (!c) return GRPIC_ERR_INVALID;
+  cudaStreamSynchronize(c->stream);
+  dev_free(c, c->fields);
+  dev_free(c, c->J);
+  dev_free(c, c->mc);
+  dev_free(c, c->mask);
+  dev_free(c, c->st);
+  dev_free(c, c->sort.counts);
+  dev_free(c, c->sort.offsets);
+  dev_free(c, c->sort.blocks);
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    dev_free(c, c->sp[s].buf[0]);
+    dev_free(c, c->sp[s].buf[1]);
+    dev_free(c, c->sp[s].n_dev);
+    if (c->sp[s].n_shadow) cudaFreeHost(c->sp[s].n_shadow);
+    if (c->sp[s].shadow_ev) cudaEventDestroy(c->sp[s].shadow_ev);
+  }
+  if (c->st_host) cudaFreeHost(c->st_host);
+  for (auto& p : c->pending) {
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return GRPIC_OK;
+}
+
+// Stage a host or device double array on the device; *tmp receives a temporary to free.
+static grpic_status stage_in(grpic_ctx* c, const void* src, size_t bytes, int mem, const void** dev, void** tmp) {
+  *tmp = nullptr;
+  if (mem == GRPIC_MEM_DEVICE) {
+    *dev = src;
+    return GRPIC_OK;
+  }
+  void* t = dev_alloc(c, bytes);
+  if (!t) return fail(c, GRPIC_ERR_OOM, "staging allocation failed");
+  grpic_status s = cuda_check(c, cudaMemcpyAsync(t, src, bytes, cudaMemcpyHostToDevice, c->stream), "H2D copy");
+  *tmp = t;
+  *dev = t;
+  return s;
+}
+
+static void release_tmp(grpic_ctx* c, void* tmp) {
+  if (!tmp) return;
+  cudaStreamSynchronize(c->stream);
+  dev_free(c, tmp);
+}
+
+grpic_status grpic_set_fields(grpic_ctx* c, const double* d3, const double* b3, int mem) {
+  if (!c || !d3 || !b3) return GRPIC_ERR_INVALID;
+  const long long n3 = 3 * c->g.ncell;
+  const void *dd, *bd;
+  void *td, *tb;
+  grpic_status s = stage_in(c, d3, sizeof(double) * n3, mem, &dd, &td);
+  if (s == GRPIC_OK) s = stage_in(c, b3, sizeof(double) * n3, mem, &bd, &tb);
+  if (s != GRPIC_OK) return s;
+  if (c->mixed) {
+    float* base = static_cast<float*>(c->fields);
+    launch_convert_in<float>(base, static_cast<const double*>(dd), n3, c->stream);
+    launch_convert_in<float>(base + n3, static_cast<const double*>(bd), n3, c->stream);
+  } else {
+    double* base = static_cast<double*>(c->fields);
+    cudaMemcpyAsync(base, dd, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(base + n3, bd, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  s = cuda_check(c, cudaGetLastError(), "set_fields");
+  release_tmp(c, td);
+  release_tmp(c, tb);
+  return s;
+}
+
+grpic_status grpic_set_uniform_field(grpic_ctx* c, const double E[3], const double B[3]) {
+  if (!c || !E || !B) return GRPIC_ERR_INVALID;
+  if (c->mixed)
+    launch_uniform_field<float>(c->g, fields_view<float>(c), E, B, c->stream);
+  else
+    launch_uniform_field<double>(c->g, fields_view<double>(c), E, B, c->stream);
+  grpic_status s = cuda_check(c, cudaGetLastError(), "set_uniform_field");
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_uniform_field sync");
+  return s;
+}
+
+grpic_status grpic_set_j(grpic_ctx* c, const double* J3, int mem) {
+  if (!c || !J3) return GRPIC_ERR_INVALID;
+  const size_t bytes = sizeof(double) * 3 * c->g.ncell;
+  grpic_status s = cuda_check(c,
+                              cudaMemcpyAsync(c->J, J3, bytes,
+                                              mem == GRPIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyHostToDevice,
+                                              c->stream),
+                              "set_j");
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_j sync");
+  return s;
+}
+
+grpic_status grpic_load_particles(grpic_ctx* c, int species, double q_over_m, double q_macro, int64_t n,
+                                  const double* x4, const double* u4, const uint32_t* ids, int flags) {
+  if (!c || species < 0 || species >= kMaxSpecies || n < 0) return GRPIC_ERR_INVALID;
+  if (n > 0 && (!x4 || !u4 || !ids)) return GRPIC_ERR_INVALID;
+  if (n >= (1ll << 31) - 1) return fail(c, GRPIC_ERR_CAPACITY, "at most 2^31-2 particles per species");
+  const int umode = flags & 3;
+  if (umode == 3) return GRPIC_ERR_INVALID;
+  const int mem = (flags & GRPIC_LOAD_DEVICE) ? GRPIC_MEM_DEVICE : GRPIC_MEM_HOST;
+  grpic_status s = ensure_capacity(c, species, n);
+  if (s != GRPIC_OK) return s;
+  SpeciesStore& S = c->sp[species];
+  const void *xd, *ud, *idd;
+  void *tx = nullptr, *tu = nullptr, *ti = nullptr;
+  s = stage_in(c, x4, sizeof(double) * 4 * (size_t)n, mem, &xd, &tx);
+  if (s == GRPIC_OK) s = stage_in(c, u4, sizeof(double) * 4 * (size_t)n, mem, &ud, &tu);
+  if (s == GRPIC_OK) s = stage_in(c, ids, sizeof(uint32_t) * (size_t)n, mem, &idd, &ti);
+  if (s != GRPIC_OK) {
+    release_tmp(c, tx);
+    release_tmp(c, tu);
+    release_tmp(c, ti);
+    return s;
+  }
+  S.qm = q_over_m;
+  S.qmacro = q_macro;
+  S.cur = 0;
+  S.n = n;
+  S.loaded = true;
+  S.shadow_pending = false;
+  const double ct_now = c->g.c * c->g.dt * (double)c->steps;
+  const int ni = (int)n;
+  cudaMemcpyAsync(S.n_dev, &ni, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  if (c->mixed)
+    launch_load_particles<float>(c->g, particles_view<float>(c, species, 0), n, static_cast<const double*>(xd),
+                                 static_cast<const double*>(ud), static_cast<const uint32_t*>(idd), umode, ct_now,
+                                 c->st, c->stream);
+  else
+    launch_load_particles<double>(c->g, particles_view<double>(c, species, 0), n, static_cast<const double*>(xd),
+                                  static_cast<const double*>(ud), static_cast<const uint32_t*>(idd), umode, ct_now,
+                                  c->st, c->stream);
+  s = cuda_check(c, cudaGetLastError(), "load_particles");
+  // sort once so the store starts cell-ordered
+  if (s == GRPIC_OK) {
+    if (c->mixed)
+      launch_sort<float>(c->g, particles_view<float>(c, species, 0), particles_view<float>(c, species, 1), c->sort,
+                         S.n_dev, c->stream);
+    else
+      launch_sort<double>(c->g, particles_view<double>(c, species, 0), particles_view<double>(c, species, 1),
+                          c->sort, S.n_dev, c->stream);
+    S.cur = 1;
+  }
+  if (s == GRPIC_OK) s = read_status(c);
+  release_tmp(c, tx);
+  release_tmp(c, tu);
+  release_tmp(c, ti);
+  if (s != GRPIC_OK) {
+    S.loaded = false;
+    S.n = 0;
+  }
+  return s;
+}
+
+grpic_status grpic_step_async(grpic_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return GRPIC_ERR_INVALID;
+  for (int i = 0; i < nsteps; ++i) enqueue_step(c);
+  return cuda_check(c, cudaGetLastError(), "step launch");
+}
+
+grpic_status grpic_sync(grpic_ctx* c) {
+  if (!c) return GRPIC_ERR_INVALID;
+  return read_status(c);
+}
+
+grpic_status grpic_step(grpic_ctx* c, int nsteps) {
+  grpic_status s = grpic_step_async(c, nsteps);
+  if (s != GRPIC_OK) return s;
+  return read_status(c);
+}
+
+grpic_status grpic_stage(grpic_ctx* c, int stage) {
+  if (!c || stage < GRPIC_STAGE_B_HALF || stage > GRPIC_STAGE_SORT) return GRPIC_ERR_INVALID;
+  enqueue_stage_any(c, stage);
+  grpic_status s = cuda_check(c, cudaGetLastError(), "stage launch");
+  if (s != GRPIC_OK) return s;
+  return read_status(c);
+}
+
+grpic_status grpic_get_fields(grpic_ctx* c, double* d3, double* b3, double* J3, int mem) {
+  if (!c) return GRPIC_ERR_INVALID;
+  const long long n3 = 3 * c->g.ncell;
+  const size_t bytes = sizeof(double) * n3;
+  const cudaMemcpyKind kind = mem == GRPIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* tmp = nullptr;
+  if (c->mixed && (d3 || b3)) {
+    tmp = static_cast<double*>(dev_alloc(c, bytes));
+    if (!tmp) return fail(c, GRPIC_ERR_OOM, "staging allocation failed");
+  }
+  double* outs[2] = {d3, b3};
+  for (int w = 0; w < 2; ++w) {
+    if (!outs[w]) continue;
+    if (c->mixed) {
+      launch_convert_out<float>(tmp, static_cast<float*>(c->fields) + w * n3, n3, c->stream);
+      cudaMemcpyAsync(outs[w], tmp, bytes, kind, c->stream);
+    } else {
+      cudaMemcpyAsync(outs[w], static_cast<double*>(c->fields) + w * n3, bytes, kind, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+  }
+  if (J3) cudaMemcpyAsync(J3, c->J, bytes, kind, c->stream);
+  grpic_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "get_fields");
+  if (tmp) dev_free(c, tmp);
+  return s;
+}
+
+grpic_status grpic_num_particles(grpic_ctx* c, int species, int64_t* n) {
+  if (!c || !n || species < 0 || species >= kMaxSpecies) return GRPIC_ERR_INVALID;
+  SpeciesStore& S = c->sp[species];
+  if (!S.loaded) {
+    *n = 0;
+    return GRPIC_OK;
+  }
+  int v = 0;
+  grpic_status s = cuda_check(c, cudaMemcpyAsync(&v, S.n_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                              "count copy");
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "count sync");
+  if (s != GRPIC_OK) return s;
+  // entries after the last sort may include particles flagged since; sort if needed
+  if (c->since_sort != 0) {
+    enqueue_stage_any(c, GRPIC_STAGE_SORT);
+    c->since_sort = 0;
+    s = cuda_check(c, cudaMemcpyAsync(&v, S.n_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "count copy");
+    if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "count sync");
+    if (s != GRPIC_OK) return s;
+  }
+  S.n = v;
+  S.shadow_pending = false;
+  *n = v;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_get_particles(grpic_ctx* c, int species, int64_t* n_inout, double* x4, double* u4,
+                                 uint32_t* ids, int mem) {
+  if (!c || !n_inout || species < 0 || species >= kMaxSpecies) return GRPIC_ERR_INVALID;
+  int64_t n = 0;
+  grpic_status s = grpic_num_particles(c, species, &n);
+  if (s != GRPIC_OK) return s;
+  if (*n_inout < n) {
+    *n_inout = n;
+    return fail(c, GRPIC_ERR_CAPACITY, "output arrays too small");
+  }
+  *n_inout = n;
+  if (n == 0) return GRPIC_OK;
+  const double ct_now = c->g.c * c->g.dt * (double)c->steps;
+  SpeciesStore& S = c->sp[species];
+  double *dx = x4, *du = u4;
+  uint32_t* di = ids;
+  void *tx = nullptr, *tu = nullptr, *ti = nullptr;
+  if (mem != GRPIC_MEM_DEVICE) {
+    if (x4) dx = static_cast<double*>(tx = dev_alloc(c, sizeof(double) * 4 * n));
+    if (u4) du = static_cast<double*>(tu = dev_alloc(c, sizeof(double) * 4 * n));
+    if (ids) di = static_cast<uint32_t*>(ti = dev_alloc(c, sizeof(uint32_t) * n));
+    if ((x4 && !tx) || (u4 && !tu) || (ids && !ti)) {
+      dev_free(c, tx);
+      dev_free(c, tu);
+      dev_free(c, ti);
+      return fail(c, GRPIC_ERR_OOM, "staging allocation failed");
+    }
+  }
+  if (c->mixed)
+    launch_unload_particles<float>(particles_view<float>(c, species, S.cur), n, dx, du, di, ct_now, c->stream);
+  else
+    launch_unload_particles<double>(particles_view<double>(c, species, S.cur), n, dx, du, di, ct_now, c->stream);
+  if (mem != GRPIC_MEM_DEVICE) {
+    if (x4) cudaMemcpyAsync(x4, dx, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (u4) cudaMemcpyAsync(u4, du, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (ids) cudaMemcpyAsync(ids, di, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, c->stream);
+  }
+  s = cuda_check(c, cudaStreamSynchronize(c->stream), "get_particles");
+  dev_free(c, tx);
+  dev_free(c, tu);
+  dev_free(c, ti);
+  return s;
+}
+
+grpic_status grpic_get_stats(grpic_ctx* c, grpic_stats* out) {
+  if (!c || !out) return GRPIC_ERR_INVALID;
+  grpic_status s = read_status(c);
+  if (s != GRPIC_OK && s != GRPIC_ERR_CFL && s != GRPIC_ERR_NONFINITE) return s;
+  *out = c->totals;
+  out->steps = c->steps;
+  for (int q = 0; q < kMaxSpecies; ++q) {
+    int v = 0;
+    if (c->sp[q].loaded) {
+      cudaMemcpy(&v, c->sp[q].n_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    }
+    out->n_alive[q] = v;
+  }
+  return GRPIC_OK;
+}
+
+grpic_status grpic_set_profiling(grpic_ctx* c, int on) {
+  if (!c) return GRPIC_ERR_INVALID;
+  c->profiling = on != 0;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_get_profile(grpic_ctx* c, double times_ms[5], int64_t counts[5], int64_t* kernel_launches,
+                               int reset) {
+  if (!c) return GRPIC_ERR_INVALID;
+  grpic_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+  if (s != GRPIC_OK) return s;
+  collect_profile(c);
+  for (int q = 0; q < 5; ++q) {
+    if (times_ms) times_ms[q] = c->prof_ms[q];
+    if (counts) counts[q] = c->prof_cnt[q];
+  }
+  if (kernel_launches) *kernel_launches = c->launches;
+  if (reset) {
+    for (int q = 0; q < 5; ++q) {
+      c->prof_ms[q] = 0.0;
+      c->prof_cnt[q] = 0;
+    }
+    c->launches = 0;
+  }
+  return GRPIC_OK;
+}
+
+// ---- batched engine (stage-interleaved over contexts) ----------------------------------
+struct grpic_batch {
+  std::vector<grpic_ctx*> ctxs;
+};
+
+grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grpic_batch** out) {
+  (void)stream;
+  if (!ctxs || n <= 0 || !out) return GRPIC_ERR_INVALID;
+  grpic_batch* b = new grpic_batch();
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) {
+      delete b;
+      return GRPIC_ERR_INVALID;
+    }
+    b->ctxs.push_back(ctxs[i]);
+  }
+  *out = b;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return GRPIC_ERR_INVALID;
+  for (int s = 0; s < nsteps; ++s)
+    for (grpic_ctx* c : b->ctxs) enqueue_step(c);
+  for (grpic_ctx* c : b->ctxs) {
+    grpic_status st = read_status(c);
+    if (st != GRPIC_OK) return st;
+  }
+  return GRPIC_OK;
+}
+
+grpic_status grpic_batch_destroy(grpic_batch* b) {
+  if (!b) return GRPIC_ERR_INVALID;
+  delete b;
+  return GRPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// Device metric module for the Cartesian Kerr-Schild form of the Kerr metric.
+//
+//   g_mn = eta_mn + f k_m k_n,   f = 2 m r^3 / (r^4 + a^2 z^2)                 (Eq. 4)
+//   k = ((r x - a y)/(r^2 + a^2), (r y + a x)/(r^2 + a^2), z / r, 1)          (Eq. 5, dt -> dx^4)
+//   r^4 - (R^2 - a^2) r^2 - a^2 z^2 = 0                                        (Eq. 6)
+//
+// k is null for eta (that is Eq. 6), so |k_spatial| = 1, det g = -1 and
+// g^mn = eta^mn - f k^m k^n with k^m = (k_x, k_y, k_z, -1).  Everything below uses those
+// closed forms; the gradients of r, f and k are written out by the chain rule.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace grpic {
+
+template <typename S>
+struct Kerr {
+  S r, f;        // r of Eq. 6, f of Eq. 4
+  S k0, k1, k2;  // spatial k_m (k_3 = 1)
+  S D;           // sqrt((R^2 - a^2)^2 + 4 a^2 z^2) = d(quartic)/d(r^2)
+  bool flat;     // r = 0 (the disk z = 0, R <= a): metric taken flat, its limit there
+};
+
+template <typename S>
+__device__ __forceinline__ Kerr<S> kerr_eval(S x, S y, S z, S m, S a) {
+  Kerr<S> K;
+  const S a2 = a * a;
+  const S q = a2 * z * z;
+  const S p = x * x + y * y + z * z - a2;
+  K.D = sqrt(p * p + S(4) * q);
+  // Non-negative root of Eq. 6 in r^2, written so that neither branch cancels.
+  const S r2 = (p >= S(0)) ? S(0.5) * (p + K.D) : (S(2) * q) / (K.D - p);
+  if (!(r2 > S(0))) {
+    K.flat = true;
+    K.r = S(0);
+    K.f = S(0);
+    K.k0 = S(0);
+    K.k1 = S(0);
+    K.k2 = S(1);
+    return K;
+  }
+  K.flat = false;
+  K.r = sqrt(r2);
+  const S inv_rho2 = S(1) / (r2 + a2);
+  K.f = S(2) * m * K.r * r2 / (r2 * r2 + q);
+  K.k0 = (K.r * x - a * y) * inv_rho2;
+  K.k1 = (K.r * y + a * x) * inv_rho2;
+  K.k2 = z / K.r;
+  return K;
+}
+
+// Gamma^a_mn u^m u^n = g^ab (u^m d_m g_bn u^n - 1/2 d_b g_mn u^m u^n) for g = eta + f k k.
+// With s = k.u, D_b = u^m d_m k_b, E_b = u^n d_b k_n and d_4 = 0:
+//   w_b = (u.df) s k_b + f s D_b + f (u.D) k_b - 1/2 s^2 d_b f - f s E_b
+//   Gamma u u = eta^ab w_b - f k^a (k^b w_b)
+template <typename S>
+__device__ __forceinline__ void christoffel_uu(const Kerr<S>& K, S x, S y, S z, S a, const S u[4], S out[4]) {
+  if (K.flat) {
+    out[0] = out[1] = out[2] = out[3] = S(0);
+    return;
+  }
+  const S r = K.r, f = K.f;
+  const S k0 = K.k0, k1 = K.k1, k2 = K.k2;
+  const S r2 = r * r, a2 = a * a;
+  const S inv_rho2 = S(1) / (r2 + a2);
+  const S inv_D = S(1) / K.D;
+  const S inv_r = S(1) / r;
+  // grad r from the implicit quartic: r_x = x r / D, r_y = y r / D, r_z = z (r^2 + a^2) / (r D)
+  const S rx = x * r * inv_D;
+  const S ry = y * r * inv_D;
+  const S rz = z * (r2 + a2) * inv_D * inv_r;
+  // grad f: df/dr = f (3/r - 4 r^3/Sigma), df/dz|_r = -2 a^2 z f / Sigma, Sigma = r^4 + a^2 z^2
+  const S inv_sig = S(1) / (r2 * r2 + a2 * z * z);
+  const S fr = f * (S(3) * inv_r - S(4) * r2 * r * inv_sig);
+  const S fx = fr * rx;
+  const S fy = fr * ry;
+  const S fz = fr * rz - S(2) * a2 * z * f * inv_sig;
+  // Jacobian J[i][j] = d_i k_j
+  const S ri[3] = {rx, ry, rz};
+  S Jk[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const S tr = S(2) * r * ri[i];
+    Jk[i][0] = (x * ri[i] + (i == 0 ? r : S(0)) - (i == 1 ? a : S(0)) - tr * k0) * inv_rho2;
+    Jk[i][1] = (y * ri[i] + (i == 1 ? r : S(0)) + (i == 0 ? a : S(0)) - tr * k1) * inv_rho2;
+    Jk[i][2] = ((i == 2 ? S(1) : S(0)) - k2 * ri[i]) * inv_r;
+  }
+  const S s = k0 * u[0] + k1 * u[1] + k2 * u[2] + u[3];
+  const S uf = u[0] * fx + u[1] * fy + u[2] * fz;
+  S Dv[3], Ev[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    Dv[j] = u[0] * Jk[0][j] + u[1] * Jk[1][j] + u[2] * Jk[2][j];
+    Ev[j] = u[0] * Jk[j][0] + u[1] * Jk[j][1] + u[2] * Jk[j][2];
+  }
+  const S uD = u[0] * Dv[0] + u[1] * Dv[1] + u[2] * Dv[2];
+  const S fg[3] = {fx, fy, fz};
+  const S kv[3] = {k0, k1, k2};
+  const S c1 = uf * s + f * uD;  // coefficient of k_b in w_b (and w_4 itself)
+  const S fs = f * s;
+  const S hs2 = S(0.5) * s * s;
+  S w[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) w[j] = c1 * kv[j] + fs * (Dv[j] - Ev[j]) - hs2 * fg[j];
+  const S w3 = c1;
+  const S kw = k0 * w[0] + k1 * w[1] + k2 * w[2] - w3;
+  out[0] = w[0] - f * k0 * kw;
+  out[1] = w[1] - f * k1 * kw;
+  out[2] = w[2] - f * k2 * kw;
+  out[3] = -w3 + f * kw;
+}
+
+// Field tensor at a point from the prognostic pair: covariant b = (F_yz, F_zx, F_xy) and
+// contravariant d = (F^x4, F^y4, F^z4).  Lowering F with g = eta + f k k gives, for the
+// spatial block, F_cov = M F^sp M + f (d k^T - k d^T) with M = I + f k k^T, so
+//   alpha = b - f (d x k),  h = (F^yz, F^zx, F^xy) = [alpha + f k (k.alpha)] / (1 + f),
+// and the covariant electric part e_i = F_i4 = f (k x h)_i + (f - 1) d_i - f k_i (k.d).
+template <typename S>
+__device__ __forceinline__ void contra_spatial(S f, S k0, S k1, S k2, const S b[3], const S d[3], S h[3]) {
+  const S al0 = b[0] - f * (d[1] * k2 - d[2] * k1);
+  const S al1 = b[1] - f * (d[2] * k0 - d[0] * k2);
+  const S al2 = b[2] - f * (d[0] * k1 - d[1] * k0);
+  const S ka = f * (k0 * al0 + k1 * al1 + k2 * al2);
+  const S inv = S(1) / (S(1) + f);
+  h[0] = (al0 + ka * k0) * inv;
+  h[1] = (al1 + ka * k1) * inv;
+  h[2] = (al2 + ka * k2) * inv;
+}
+
+template <typename S>
+__device__ __forceinline__ void cov_electric(S f, S k0, S k1, S k2, const S h[3], const S d[3], S e[3]) {
+  const S kd = k0 * d[0] + k1 * d[1] + k2 * d[2];
+  const S fm1 = f - S(1);
+  e[0] = f * (k1 * h[2] - k2 * h[1]) + fm1 * d[0] - f * k0 * kd;
+  e[1] = f * (k2 * h[0] - k0 * h[2]) + fm1 * d[1] - f * k1 * kd;
+  e[2] = f * (k0 * h[1] - k1 * h[0]) + fm1 * d[2] - f * k2 * kd;
+}
+
+// Lorentz part of Eq. 15, (q/m) F^a_b u^b = (q/m) F^ac u_c, with u_c = g_cb u^b:
+//   u_i = u^i + f s k_i, u_4 = -u^4 + f s;  (q/m)[(u_cov x h)_i + d_i u_4],  -(q/m) d.u_cov
+template <typename S>
+__device__ __forceinline__ void lorentz(S qm, S f, S k0, S k1, S k2, const S h[3], const S d[3], const S u[4],
+                                        S out[4]) {
+  const S s = k0 * u[0] + k1 * u[1] + k2 * u[2] + u[3];
+  const S fs = f * s;
+  const S c0 = u[0] + fs * k0, c1 = u[1] + fs * k1, c2 = u[2] + fs * k2;
+  const S c3 = fs - u[3];
+  out[0] = qm * (c1 * h[2] - c2 * h[1] + d[0] * c3);
+  out[1] = qm * (c2 * h[0] - c0 * h[2] + d[1] * c3);
+  out[2] = qm * (c0 * h[1] - c1 * h[0] + d[2] * c3);
+  out[3] = -qm * (d[0] * c0 + d[1] * c1 + d[2] * c2);
+}
+
+// Covariant spatial block of a contravariant tensor given as (h, d): with v_i = F^{i b} k_b,
+// (g F g)_ij = F^ij + f (v_i k_j - k_i v_j).  Returns (F_yz, F_zx, F_xy).
+template <typename S>
+__device__ __forceinline__ void lower_spatial(S f, S k0, S k1, S k2, const S h[3], const S d[3], S b[3]) {
+  // F^{ij} k_j = (k x h) components with sign: F^{il} k_l = eps_ilm k_l h_m = (k x h)_i
+  const S v0 = (k1 * h[2] - k2 * h[1]) + d[0];
+  const S v1 = (k2 * h[0] - k0 * h[2]) + d[1];
+  const S v2 = (k0 * h[1] - k1 * h[0]) + d[2];
+  b[0] = h[0] + f * (v1 * k2 - k1 * v2);
+  b[1] = h[1] + f * (v2 * k0 - k2 * v0);
+  b[2] = h[2] + f * (v0 * k1 - k0 * v1);
+}
+
+// Eq. 16: gamma = [u^4/c + sqrt((u^4/c)^2 + 4 a^4 dt / (2c))] / 2; a negative argument or a
+// non-positive result falls back to u^4/c (the caller counts it).
+template <typename S>
+__device__ __forceinline__ S gamma_step(S u4, S a4, S inv_c, S dt, bool* fallback) {
+  const S w = u4 * inv_c;
+  const S arg = w * w + S(2) * a4 * dt * inv_c;
+  S g = S(-1);
+  if (arg >= S(0)) g = S(0.5) * (w + sqrt(arg));
+  if (!(g > S(0))) {
+    *fallback = true;
+    return w;
+  }
+  *fallback = false;
+  return g;
+}
+
+}  // namespace grpic

@@ -1,0 +1,469 @@
+// Fused gather + GR-RK4 push + curved-metric current deposit (Sec. 3.3 and Sec. 4).
+//
+// Per particle and step:
+//   1. RK4 in proper time (Eqs. 13-16): y = (x^a, u^a), dy/dtau = (u, a~(x, u)),
+//      a~ = (q/m) F^a_b u^b - Gamma^a_mn u^m u^n, one step h = dt / gamma_1 with gamma_1 from
+//      Eq. 16 at (x_n, u_n); classical stage offsets 0, h/2, h/2, h.
+//   2. At each stage: CIC gather of the six prognostic components, each from its own staggered
+//      lattice (the sqrt(-det g) sub-volumes of Sec. 3.3 are exactly trilinear since
+//      det g = -1), conversion with g at the particle, Lorentz + Christoffel terms.
+//   3. Umeda zig-zag split of x_n -> x_{n+1} into two segments; the flux of each segment
+//      through the faces of its cell, weighted by the four sub-areas of Eq. 18
+//      (integrand sqrt(g_II g_JJ - g_IJ^2) = sqrt(1 + f (k_I^2 + k_J^2)), Q x Q Gauss-Legendre
+//      per sub-rectangle, plane at the segment midpoint), times gamma_bar = (u^4_n+u^4_{n+1})/2c
+//      (J = rho gamma v).
+//   4. Removal flag: r <= r_+ or a coordinate outside [1, n-2]; sort key = cell or kDead.
+//
+// Precision: T = double runs everything in FP64.  T = float (FP32-mixed) keeps positions,
+// velocities, fields and arithmetic in FP32 except where R^2 < 16 m^2 + a^2 (which contains
+// r < 4m): there the quartic, the metric and the Christoffel contraction run in FP64.  The
+// global J accumulators are FP64 in both modes.
+#include <cmath>
+
+#include "common.cuh"
+#include "metric.cuh"
+
+namespace grpic {
+
+namespace {
+
+template <int Q>
+struct Gauss;
+template <>
+struct Gauss<1> {
+  __device__ static constexpr double x(int) { return 0.0; }
+  __device__ static constexpr double w(int) { return 2.0; }
+};
+template <>
+struct Gauss<2> {
+  __device__ static constexpr double x(int i) { return i == 0 ? -0.57735026918962576451 : 0.57735026918962576451; }
+  __device__ static constexpr double w(int) { return 1.0; }
+};
+template <>
+struct Gauss<3> {
+  __device__ static constexpr double x(int i) {
+    return i == 0 ? -0.77459666924148337704 : (i == 1 ? 0.0 : 0.77459666924148337704);
+  }
+  __device__ static constexpr double w(int i) { return i == 1 ? 8.0 / 9.0 : 5.0 / 9.0; }
+};
+
+struct Consts {
+  double m, a, xc, yc, zc;
+  double promote_r2;  // FP32-mixed: evaluate in FP64 where R^2 < promote_r2
+};
+
+// a~ at (x, u): gather, convert, Lorentz - Christoffel.
+template <typename T, bool MIXED>
+__device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const Consts& C, T qm, const T x[3],
+                                      const T u[4], T out[4], unsigned& flags, unsigned& n64) {
+  // --- CIC gather: integer lattice (floor x) and half lattice (floor(x - 1/2)) per axis
+  int ii[3], ih[3];
+  T wi[3], wh[3];
+  const int nn[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T s0 = x[ax];
+    const T s1 = x[ax] - T(0.5);
+    if (!(s1 >= T(0)) || !(s0 <= T(nn[ax] - 1))) flags |= ST_RANGE;
+    int a0 = (int)floor(s0), a1 = (int)floor(s1);
+    a0 = min(max(a0, 0), nn[ax] - 2);
+    a1 = min(max(a1, 0), nn[ax] - 2);
+    ii[ax] = a0;
+    ih[ax] = a1;
+    wi[ax] = s0 - T(a0);
+    wh[ax] = s1 - T(a1);
+  }
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  T val[6];
+#pragma unroll
+  for (int comp = 0; comp < 6; ++comp) {
+    // lattice offsets: d^x (1,0,0) d^y (0,1,0) d^z (0,0,1) b_x (0,1,1) b_y (1,0,1) b_z (1,1,0)
+    const bool hx = (comp == 0) || (comp == 4) || (comp == 5);
+    const bool hy = (comp == 1) || (comp == 3) || (comp == 5);
+    const bool hz = (comp == 2) || (comp == 3) || (comp == 4);
+    const int i0 = hx ? ih[0] : ii[0], j0 = hy ? ih[1] : ii[1], k0 = hz ? ih[2] : ii[2];
+    const T w0 = hx ? wh[0] : wi[0], w1 = hy ? wh[1] : wi[1], w2 = hz ? wh[2] : wi[2];
+    const T* arr = comp < 3 ? F.d[comp] : F.b[comp - 3];
+    const long long base = ((long long)k0 * g.ny + j0) * g.nx + i0;
+    T s = T(0);
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+          const T W = (di ? w0 : T(1) - w0) * (dj ? w1 : T(1) - w1) * (dk ? w2 : T(1) - w2);
+          s += W * __ldg(arr + base + dk * sz + dj * sy + di);
+        }
+    val[comp] = s;
+  }
+  const T d[3] = {val[0], val[1], val[2]};
+  const T b[3] = {val[3], val[4], val[5]};
+
+  // --- metric and Christoffel contraction at the particle
+  T f, k0, k1, k2, gam[4];
+  const T X = x[0] - (T)C.xc, Y = x[1] - (T)C.yc, Z = x[2] - (T)C.zc;
+  if (MIXED && (double)(X * X + Y * Y + Z * Z) < C.promote_r2) {
+    const double Xd = (double)x[0] - C.xc, Yd = (double)x[1] - C.yc, Zd = (double)x[2] - C.zc;
+    const Kerr<double> K = kerr_eval<double>(Xd, Yd, Zd, C.m, C.a);
+    const double ud[4] = {(double)u[0], (double)u[1], (double)u[2], (double)u[3]};
+    double gd[4];
+    christoffel_uu<double>(K, Xd, Yd, Zd, C.a, ud, gd);
+    f = (T)K.f;
+    k0 = (T)K.k0;
+    k1 = (T)K.k1;
+    k2 = (T)K.k2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) gam[q] = (T)gd[q];
+    ++n64;
+  } else {
+    const Kerr<T> K = kerr_eval<T>(X, Y, Z, (T)C.m, (T)C.a);
+    christoffel_uu<T>(K, X, Y, Z, (T)C.a, u, gam);
+    f = K.f;
+    k0 = K.k0;
+    k1 = K.k1;
+    k2 = K.k2;
+  }
+  T h[3], lor[4];
+  contra_spatial(f, k0, k1, k2, b, d, h);
+  lorentz(qm, f, k0, k1, k2, h, d, u, lor);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = lor[q] - gam[q];
+}
+
+// Integrand of Eq. 18 at a grid position.
+template <typename T, bool MIXED>
+__device__ __forceinline__ T area_integrand(const Consts& C, T px, T py, T pz, int I, int J, unsigned& n64) {
+  const T X = px - (T)C.xc, Y = py - (T)C.yc, Z = pz - (T)C.zc;
+  if (MIXED && (double)(X * X + Y * Y + Z * Z) < C.promote_r2) {
+    const Kerr<double> K =
+        kerr_eval<double>((double)px - C.xc, (double)py - C.yc, (double)pz - C.zc, C.m, C.a);
+    const double kv[3] = {K.k0, K.k1, K.k2};
+    ++n64;
+    return (T)sqrt(1.0 + K.f * (kv[I] * kv[I] + kv[J] * kv[J]));
+  }
+  const Kerr<T> K = kerr_eval<T>(X, Y, Z, (T)C.m, (T)C.a);
+  const T kv[3] = {K.k0, K.k1, K.k2};
+  return sqrt(T(1) + K.f * (kv[I] * kv[I] + kv[J] * kv[J]));
+}
+
+// AREA(Is..If, Js..Jf) of Eq. 18 in the plane x^K = xK.
+template <typename T, int Q, bool MIXED>
+__device__ __forceinline__ T area(const Consts& C, int K, T xK, int I, T Is, T If, int J, T Js, T Jf, unsigned& n64) {
+  T s = T(0);
+  const T ci = T(0.5) * (Is + If), hi = T(0.5) * (If - Is);
+  const T cj = T(0.5) * (Js + Jf), hj = T(0.5) * (Jf - Js);
+#pragma unroll
+  for (int p = 0; p < Q; ++p)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      T pos[3];
+      pos[K] = xK;
+      pos[I] = ci + hi * (T)Gauss<Q>::x(p);
+      pos[J] = cj + hj * (T)Gauss<Q>::x(q);
+      s += (T)Gauss<Q>::w(p) * (T)Gauss<Q>::w(q) * area_integrand<T, MIXED>(C, pos[0], pos[1], pos[2], I, J, n64);
+    }
+  return s * T(0.25) * (If - Is) * (Jf - Js);
+}
+
+template <typename T, int Q, bool MIXED>
+__device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const Consts& C, const T x1[3],
+                                        const T x2[3], T qg, T inv_dt, unsigned& flags, unsigned& n64) {
+  const int nn[3] = {g.nx, g.ny, g.nz};
+  int c1[3], c2[3];
+  T xr[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int a = (int)floor(x1[ax]), b = (int)floor(x2[ax]);
+    if (a < 0 || b < 0 || a > nn[ax] - 2 || b > nn[ax] - 2) flags |= ST_RANGE;
+    a = min(max(a, 0), nn[ax] - 2);
+    b = min(max(b, 0), nn[ax] - 2);
+    c1[ax] = a;
+    c2[ax] = b;
+    const T mid = T(0.5) * (x1[ax] + x2[ax]);
+    xr[ax] = fmin((T)(min(a, b) + 1), fmax((T)max(a, b), mid));
+  }
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+#pragma unroll
+  for (int seg = 0; seg < 2; ++seg) {
+    const T* a = seg ? xr : x1;
+    const T* b = seg ? x2 : xr;
+    const int* cell = seg ? c2 : c1;
+    T P[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) P[ax] = T(0.5) * (a[ax] + b[ax]);
+#pragma unroll
+    for (int K = 0; K < 3; ++K) {
+      const T dK = b[K] - a[K];
+      if (dK == T(0)) continue;
+      const T flux = qg * dK * inv_dt;
+      const int I = (K + 1) % 3, J = (K + 2) % 3;
+      const T i0 = (T)cell[I], j0 = (T)cell[J];
+      const T A00 = area<T, Q, MIXED>(C, K, P[K], I, P[I], i0 + T(1), J, P[J], j0 + T(1), n64);
+      const T A10 = area<T, Q, MIXED>(C, K, P[K], I, i0, P[I], J, P[J], j0 + T(1), n64);
+      const T A01 = area<T, Q, MIXED>(C, K, P[K], I, P[I], i0 + T(1), J, j0, P[J], n64);
+      const T A11 = area<T, Q, MIXED>(C, K, P[K], I, i0, P[I], J, j0, P[J], n64);
+      const T FA = A00 + A10 + A01 + A11;
+      const T W[4] = {A00 / FA, A10 / FA, A01 / FA, A11 / FA};
+      const long long st[3] = {1, sy, sz};
+      const long long base = ((long long)cell[2] * g.ny + cell[1]) * g.nx + cell[0];
+      double* JK = F.J[K];
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) atomicAdd(JK + base + di * st[I] + dj * st[J], (double)(flux * W[dj * 2 + di]));
+    }
+  }
+}
+
+template <typename T, int Q, bool MIXED>
+__global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields<T> F, const Particles<T> P,
+                                                        const Species sp, DevStatus* st) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned flags = 0, n64 = 0;
+  bool active = i < P.n && i < (long long)(*P.n_dev);
+  if (active) active = P.key[i] != kDead;
+  if (active) {
+    Consts C;
+    C.m = g.m;
+    C.a = g.a;
+    C.xc = g.xc;
+    C.yc = g.yc;
+    C.zc = g.zc;
+    C.promote_r2 = 16.0 * g.m * g.m + g.a * g.a;
+    const T qm = (T)sp.qm;
+    const T dt = (T)g.dt;
+    T x0[4], u0[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x0[q] = P.x[q][i];
+      u0[q] = P.u[q][i];
+    }
+    // stage 1 and Eq. 16
+    T a[4], sx[4], su[4], xs[4], us[4];
+    accel<T, MIXED>(g, F, C, qm, x0, u0, a, flags, n64);
+    bool fb = false;
+    const T g1 = gamma_step<T>(u0[3], a[3], T(1) / (T)g.c, dt, &fb);
+    const T h = dt / g1;
+    const T h2 = T(0.5) * h;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sx[q] = u0[q];
+      su[q] = a[q];
+      xs[q] = x0[q] + h2 * u0[q];
+      us[q] = u0[q] + h2 * a[q];
+    }
+    // stage 2
+    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sx[q] += T(2) * us[q];
+      su[q] += T(2) * a[q];
+      xs[q] = x0[q] + h2 * us[q];
+      us[q] = u0[q] + h2 * a[q];
+    }
+    // stage 3
+    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sx[q] += T(2) * us[q];
+      su[q] += T(2) * a[q];
+      xs[q] = x0[q] + h * us[q];
+      us[q] = u0[q] + h * a[q];
+    }
+    // stage 4
+    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
+    T x1[4], u1[4];
+    const T h6 = h / T(6);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sx[q] += us[q];
+      su[q] += a[q];
+      x1[q] = x0[q] + h6 * sx[q];
+      u1[q] = u0[q] + h6 * su[q];
+    }
+    x1[3] -= (T)(g.c * g.dt);  // x^4 is stored relative to c t
+    bool finite = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) finite = finite && isfinite(x1[q]) && isfinite(u1[q]);
+    if (!finite) flags |= ST_NONFINITE;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (!(fabs(x1[q] - x0[q]) < T(1))) flags |= ST_CFL;
+    // deposit, J = rho gamma v
+    if (finite && sp.qmacro != 0.0) {
+      const T gbar = (g.flags & 1u) ? T(1) : (u0[3] + u1[3]) / (T(2) * (T)g.c);
+      const T qg = (T)sp.qmacro * gbar;
+      deposit<T, (Q > 0 ? Q : 2), MIXED>(g, F, C, x0, x1, qg, T(1) / dt, flags, n64);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      P.x[q][i] = x1[q];
+      P.u[q][i] = u1[q];
+    }
+    // removal (r <= r_+ or outside [1, n-2]) and the sort key
+    bool outer = !finite;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (!(x1[q] >= T(1) && x1[q] <= T(nn[q] - 2))) outer = true;
+    bool horizon = false;
+    if (finite && g.m > 0.0) {
+      const Kerr<double> K =
+          kerr_eval<double>((double)x1[0] - g.xc, (double)x1[1] - g.yc, (double)x1[2] - g.zc, g.m, g.a);
+      horizon = K.flat || K.r <= g.r_plus;
+    }
+    if (horizon || outer) {
+      P.key[i] = kDead;
+      atomicAdd(horizon ? &st->removed_horizon : &st->removed_outer, 1ull);
+    } else {
+      const int ci = (int)floor(x1[0]), cj = (int)floor(x1[1]), ck = (int)floor(x1[2]);
+      P.key[i] = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
+    }
+    if (fb) atomicAdd(&st->fallbacks, 1ull);
+  }
+  // one status update per warp
+  const unsigned any_flags = __reduce_or_sync(0xffffffffu, flags);
+  const unsigned sum64 = __reduce_add_sync(0xffffffffu, n64);
+  const unsigned npush = __popc(__ballot_sync(0xffffffffu, active));
+  if ((threadIdx.x & 31) == 0) {
+    if (any_flags) atomicOr(&st->flags, any_flags);
+    if (sum64) atomicAdd(&st->fp64_evals, (unsigned long long)sum64);
+    if (npush) atomicAdd(&st->pushed, (unsigned long long)npush);
+  }
+}
+
+// ---- load / unload ---------------------------------------------------------------------
+template <typename T>
+__global__ void k_load(const Grid g, const Particles<T> P, long long n, const double* __restrict__ x4,
+                       const double* __restrict__ u4, const uint32_t* __restrict__ ids, int umode, double ct_now,
+                       DevStatus* st) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x[3] = {x4[i], x4[n + i], x4[2 * n + i]};
+  unsigned bad = 0;
+  const int nn[3] = {g.nx, g.ny, g.nz};
+  for (int q = 0; q < 3; ++q)
+    if (!(x[q] >= 1.0 && x[q] <= nn[q] - 2)) bad |= ST_LOAD_INVALID;
+  double u[4] = {u4[i], u4[n + i], u4[2 * n + i], umode == 0 ? u4[3 * n + i] : 0.0};
+  if (!bad && umode != 0) {
+    const Kerr<double> K = kerr_eval<double>(x[0] - g.xc, x[1] - g.yc, x[2] - g.zc, g.m, g.a);
+    const double f = K.f, kk[4] = {K.k0, K.k1, K.k2, 1.0};
+    const double c2 = g.c * g.c;
+    if (umode == 1) {
+      // covariant u_i given: g^mn u_m u_n = -c^2 with g^mn = eta^mn - f k^m k^n, k^m = (k_i, -1)
+      // (-1 - f) u_4^2 + 2 (f k.u) u_4 + (|u|^2 - f (k.u)^2 + c^2) = 0, u^4 = g^{4n} u_n > 0
+      const double ku = kk[0] * u[0] + kk[1] * u[1] + kk[2] * u[2];
+      const double A = -1.0 - f, B = 2.0 * f * ku;
+      const double Cc = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] - f * ku * ku + c2;
+      const double disc = B * B - 4.0 * A * Cc;
+      if (disc < 0.0) {
+        bad |= ST_LOAD_INVALID;
+      } else {
+        // u^4 = g^{4n} u_n = -u_4 + f (k.u - u_4)  (k^4 = -1); pick the root with u^4 > 0
+        const double sq = sqrt(disc);
+        const double r1 = (-B + sq) / (2.0 * A), r2 = (-B - sq) / (2.0 * A);
+        const double up1 = -r1 + f * (ku - r1), up2 = -r2 + f * (ku - r2);
+        const double ul4 = (up1 > 0.0) ? r1 : r2;
+        if (!(up1 > 0.0) && !(up2 > 0.0)) bad |= ST_LOAD_INVALID;
+        // raise: u^i = u_i - f k_i (k.u - u_4), u^4 = -u_4 + f (k.u - u_4)
+        const double kul = ku - ul4;
+        const double ucov[3] = {u[0], u[1], u[2]};
+        for (int q = 0; q < 3; ++q) u[q] = ucov[q] - f * kk[q] * kul;
+        u[3] = -ul4 + f * kul;
+      }
+    } else {
+      // contravariant u^i given: g_44 (u^4)^2 + 2 g_4i u^i u^4 + g_ij u^i u^j + c^2 = 0
+      const double ku = kk[0] * u[0] + kk[1] * u[1] + kk[2] * u[2];
+      const double A = -1.0 + f, B = 2.0 * f * ku;
+      const double Cc = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + f * ku * ku + c2;
+      const double disc = B * B - 4.0 * A * Cc;
+      if (!(A < 0.0)) {
+        bad |= ST_LOAD_ERGO;
+      } else if (disc < 0.0) {
+        bad |= ST_LOAD_INVALID;
+      } else {
+        const double sq = sqrt(disc);
+        u[3] = fmax((-B + sq) / (2.0 * A), (-B - sq) / (2.0 * A));
+        if (!(u[3] > 0.0)) bad |= ST_LOAD_INVALID;
+      }
+    }
+  }
+  if (bad) atomicOr(&st->flags, bad);
+  for (int q = 0; q < 3; ++q) P.x[q][i] = (T)x[q];
+  P.x[3][i] = (T)(x4[3 * n + i] - ct_now);
+  for (int q = 0; q < 4; ++q) P.u[q][i] = (T)u[q];
+  P.id[i] = ids[i];
+  const int ci = min(max((int)floor(x[0]), 0), g.nx - 2);
+  const int cj = min(max((int)floor(x[1]), 0), g.ny - 2);
+  const int ck = min(max((int)floor(x[2]), 0), g.nz - 2);
+  P.key[i] = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
+}
+
+template <typename T>
+__global__ void k_unload(const Particles<T> P, long long n, double* __restrict__ x4, double* __restrict__ u4,
+                         uint32_t* __restrict__ ids, double ct_now) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < 3; ++q) {
+    if (x4) x4[q * n + i] = (double)P.x[q][i];
+  }
+  if (x4) x4[3 * n + i] = (double)P.x[3][i] + ct_now;
+  for (int q = 0; q < 4; ++q)
+    if (u4) u4[q * n + i] = (double)P.u[q][i];
+  if (ids) ids[i] = P.id[i];
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+template <typename T, bool MIXED>
+void launch_push_q(const Grid& g, const Fields<T>& F, const Particles<T>& P, const Species& sp, DevStatus* st,
+                   cudaStream_t stream) {
+  const unsigned nb = blocks_for(P.n, 128);
+  if (g.quad_order == 1)
+    k_push_deposit<T, 1, MIXED><<<nb, 128, 0, stream>>>(g, F, P, sp, st);
+  else if (g.quad_order == 3)
+    k_push_deposit<T, 3, MIXED><<<nb, 128, 0, stream>>>(g, F, P, sp, st);
+  else
+    k_push_deposit<T, 2, MIXED><<<nb, 128, 0, stream>>>(g, F, P, sp, st);
+}
+
+// FP64 runs pure double; FP32 runs the mixed policy.
+template <>
+void launch_push_deposit<double>(const Grid& g, const Fields<double>& F, const Particles<double>& P,
+                                 const Species& sp, DevStatus* st, bool, double, cudaStream_t stream) {
+  if (P.n > 0) launch_push_q<double, false>(g, F, P, sp, st, stream);
+}
+template <>
+void launch_push_deposit<float>(const Grid& g, const Fields<float>& F, const Particles<float>& P,
+                                const Species& sp, DevStatus* st, bool, double, cudaStream_t stream) {
+  if (P.n > 0) launch_push_q<float, true>(g, F, P, sp, st, stream);
+}
+
+template <typename T>
+void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,
+                           const uint32_t* ids, int umode, double ct_now, DevStatus* st, cudaStream_t stream) {
+  if (n <= 0) return;
+  k_load<T><<<blocks_for(n, 256), 256, 0, stream>>>(g, P, n, x4, u4, ids, umode, ct_now, st);
+}
+
+template <typename T>
+void launch_unload_particles(const Particles<T>& P, long long n, double* x4, double* u4, uint32_t* ids,
+                             double ct_now, cudaStream_t stream) {
+  if (n <= 0) return;
+  k_unload<T><<<blocks_for(n, 256), 256, 0, stream>>>(P, n, x4, u4, ids, ct_now);
+}
+
+template void launch_load_particles<float>(const Grid&, const Particles<float>&, long long, const double*,
+                                           const double*, const uint32_t*, int, double, DevStatus*, cudaStream_t);
+template void launch_load_particles<double>(const Grid&, const Particles<double>&, long long, const double*,
+                                            const double*, const uint32_t*, int, double, DevStatus*,
+                                            cudaStream_t);
+template void launch_unload_particles<float>(const Particles<float>&, long long, double*, double*, uint32_t*,
+                                             double, cudaStream_t);
+template void launch_unload_particles<double>(const Particles<double>&, long long, double*, double*, uint32_t*,
+                                              double, cudaStream_t);
+
+}  // namespace grpic

@@ -1,0 +1,358 @@
+"""ctypes binding of the GRPIC C ABI (include/grpic.h): the same entry points under the same
+names, plus a small ``Simulation`` convenience wrapper.  Argument marshalling only -- every
+step of the timestep runs in the CUDA library.  Device memory comes from PyTorch's caching
+allocator through the ABI's allocator callbacks, and work runs on PyTorch's current stream.
+
+The library must be built first (``paper_0904_0232_gb300.build.build()``); loading fails
+loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrpic.so")
+
+GRPIC_OK = 0
+STATUS_NAMES = {0: "GRPIC_OK", 1: "GRPIC_ERR_INVALID", 2: "GRPIC_ERR_OOM", 3: "GRPIC_ERR_CUDA", 4: "GRPIC_ERR_CFL",
+                5: "GRPIC_ERR_NONFINITE", 6: "GRPIC_ERR_TIMEOUT", 7: "GRPIC_ERR_AGAIN", 8: "GRPIC_ERR_CAPACITY"}
+GRPIC_FP64, GRPIC_FP32_MIXED = 0, 1
+GRPIC_NO_GAMMA_IN_J = 1
+GRPIC_MEM_HOST, GRPIC_MEM_DEVICE = 0, 1
+GRPIC_U_FULL, GRPIC_U_COV_SPATIAL, GRPIC_U_CONTRA_SPATIAL, GRPIC_LOAD_DEVICE = 0, 1, 2, 16
+GRPIC_STAGE_B_HALF, GRPIC_STAGE_ZERO_J, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_E, GRPIC_STAGE_SORT = range(5)
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class grpic_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("m", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double), ("dt", ctypes.c_double),
+                ("precision", ctypes.c_int), ("quad_order", ctypes.c_int), ("r_excise", ctypes.c_double),
+                ("flags", ctypes.c_uint), ("sort_interval", ctypes.c_int), ("max_particles", ctypes.c_int64),
+                ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+
+
+class grpic_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("removed_horizon", ctypes.c_int64), ("removed_outer", ctypes.c_int64),
+                ("gamma_fallbacks", ctypes.c_int64), ("fp64_evals", ctypes.c_int64),
+                ("particle_steps", ctypes.c_int64), ("n_alive", ctypes.c_int64 * 4)]
+
+
+EXPORTS = {
+    "grpic_create": (ctypes.c_int, [ctypes.POINTER(grpic_config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "grpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "grpic_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_set_uniform_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]),
+    "grpic_set_j": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_load_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int]),
+    "grpic_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_step_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_stage": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "grpic_get_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int]),
+    "grpic_num_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "grpic_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_stats)]),
+    "grpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "grpic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "grpic_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.c_int]),
+    "grpic_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "grpic_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgrpic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_0904_0232_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GrpicError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} {msg}".strip())
+        self.code = code
+
+
+# ---- PyTorch-backed device allocator --------------------------------------------------------
+def _torch():
+    import torch
+
+    return torch
+
+
+@ALLOC_FN
+def _torch_alloc(nbytes, user):
+    torch = _torch()
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                  torch.cuda.current_stream())
+    except Exception:  # out of memory -> NULL -> GRPIC_ERR_OOM
+        return None
+
+
+@FREE_FN
+def _torch_free(ptr, user):
+    if ptr:
+        _torch().cuda.caching_allocator_delete(ptr)
+
+
+# ---- thin wrappers with the ABI's names ------------------------------------------------------
+def _check(ctx, code, where):
+    if code != GRPIC_OK:
+        msg = load_library().grpic_last_error(ctx).decode() if ctx else ""
+        raise GrpicError(code, where, msg)
+
+
+def grpic_create(cfg: grpic_config, stream=None):
+    h = ctypes.c_void_p()
+    code = load_library().grpic_create(ctypes.byref(cfg), stream, ctypes.byref(h))
+    if code != GRPIC_OK:
+        raise GrpicError(code, "grpic_create")
+    return h.value
+
+
+def grpic_destroy(ctx):
+    _check(None, load_library().grpic_destroy(ctx), "grpic_destroy")
+
+
+def grpic_step(ctx, nsteps):
+    _check(ctx, load_library().grpic_step(ctx, int(nsteps)), "grpic_step")
+
+
+def grpic_step_async(ctx, nsteps):
+    _check(ctx, load_library().grpic_step_async(ctx, int(nsteps)), "grpic_step_async")
+
+
+def grpic_sync(ctx):
+    _check(ctx, load_library().grpic_sync(ctx), "grpic_sync")
+
+
+def grpic_stage(ctx, stage):
+    _check(ctx, load_library().grpic_stage(ctx, int(stage)), "grpic_stage")
+
+
+def _is_cuda_tensor(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _as_arg(a, dtype):
+    """(pointer, mem, keepalive) for a numpy array or a CUDA tensor."""
+    if _is_cuda_tensor(a):
+        t = a.contiguous().double() if dtype is np.float64 else a.contiguous()
+        return ctypes.c_void_p(t.data_ptr()), GRPIC_MEM_DEVICE, t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST, arr
+
+
+def grpic_set_fields(ctx, d3, b3):
+    pd, md, kd = _as_arg(d3, np.float64)
+    pb, mb, kb = _as_arg(b3, np.float64)
+    assert md == mb
+    _check(ctx, load_library().grpic_set_fields(ctx, pd, pb, md), "grpic_set_fields")
+
+
+def grpic_set_uniform_field(ctx, E, B):
+    e = (ctypes.c_double * 3)(*[float(v) for v in E])
+    b = (ctypes.c_double * 3)(*[float(v) for v in B])
+    _check(ctx, load_library().grpic_set_uniform_field(ctx, e, b), "grpic_set_uniform_field")
+
+
+def grpic_set_j(ctx, J3):
+    pj, mj, kj = _as_arg(J3, np.float64)
+    _check(ctx, load_library().grpic_set_j(ctx, pj, mj), "grpic_set_j")
+
+
+def grpic_load_particles(ctx, species, q_over_m, q_macro, x4, u4, ids, umode=GRPIC_U_FULL):
+    n = int(x4.shape[1])
+    px, mx, kx = _as_arg(x4, np.float64)
+    pu, mu, ku = _as_arg(u4, np.float64)
+    if _is_cuda_tensor(ids):
+        ti = ids.contiguous()
+        pi, mi, ki = ctypes.c_void_p(ti.data_ptr()), GRPIC_MEM_DEVICE, ti
+    else:
+        pi, mi, ki = _as_arg(ids, np.uint32)
+    assert mx == mu == mi
+    flags = int(umode) | (GRPIC_LOAD_DEVICE if mx == GRPIC_MEM_DEVICE else 0)
+    _check(ctx, load_library().grpic_load_particles(ctx, int(species), float(q_over_m), float(q_macro), n, px, pu, pi,
+                                                    flags), "grpic_load_particles")
+
+
+def grpic_num_particles(ctx, species):
+    n = ctypes.c_int64(0)
+    _check(ctx, load_library().grpic_num_particles(ctx, int(species), ctypes.byref(n)), "grpic_num_particles")
+    return n.value
+
+
+def grpic_get_particles(ctx, species):
+    n = grpic_num_particles(ctx, species)
+    x4 = np.zeros((4, n))
+    u4 = np.zeros((4, n))
+    ids = np.zeros(n, dtype=np.uint32)
+    nn = ctypes.c_int64(n)
+    _check(ctx, load_library().grpic_get_particles(ctx, int(species), ctypes.byref(nn),
+                                                   x4.ctypes.data_as(ctypes.c_void_p),
+                                                   u4.ctypes.data_as(ctypes.c_void_p),
+                                                   ids.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST),
+           "grpic_get_particles")
+    return x4[:, :nn.value], u4[:, :nn.value], ids[:nn.value]
+
+
+def grpic_get_fields(ctx, shape):
+    d = np.zeros((3,) + tuple(shape))
+    b = np.zeros((3,) + tuple(shape))
+    J = np.zeros((3,) + tuple(shape))
+    _check(ctx, load_library().grpic_get_fields(ctx, d.ctypes.data_as(ctypes.c_void_p),
+                                                b.ctypes.data_as(ctypes.c_void_p),
+                                                J.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST),
+           "grpic_get_fields")
+    return d, b, J
+
+
+def grpic_get_stats(ctx):
+    s = grpic_stats()
+    _check(ctx, load_library().grpic_get_stats(ctx, ctypes.byref(s)), "grpic_get_stats")
+    return dict(steps=s.steps, removed_horizon=s.removed_horizon, removed_outer=s.removed_outer,
+                gamma_fallbacks=s.gamma_fallbacks, fp64_evals=s.fp64_evals, particle_steps=s.particle_steps,
+                n_alive=list(s.n_alive))
+
+
+def grpic_set_profiling(ctx, on):
+    _check(ctx, load_library().grpic_set_profiling(ctx, int(bool(on))), "grpic_set_profiling")
+
+
+STAGE_NAMES = ("b_half", "zero_j", "push_deposit", "e_step", "sort")
+
+
+def grpic_get_profile(ctx, reset=False):
+    ms = (ctypes.c_double * 5)()
+    cnt = (ctypes.c_int64 * 5)()
+    nl = ctypes.c_int64(0)
+    _check(ctx, load_library().grpic_get_profile(ctx, ms, cnt, ctypes.byref(nl), int(bool(reset))),
+           "grpic_get_profile")
+    return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(5)}, nl.value
+
+
+def grpic_probe_fma_peak(precision):
+    v = ctypes.c_double(0.0)
+    _check(None, load_library().grpic_probe_fma_peak(int(precision), ctypes.byref(v)), "grpic_probe_fma_peak")
+    return v.value
+
+
+def grpic_batch_create(ctxs, stream=None):
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    h = ctypes.c_void_p()
+    _check(None, load_library().grpic_batch_create(arr, len(ctxs), stream, ctypes.byref(h)), "grpic_batch_create")
+    return h.value
+
+
+def grpic_batch_step(b, nsteps):
+    _check(None, load_library().grpic_batch_step(b, int(nsteps)), "grpic_batch_step")
+
+
+def grpic_batch_destroy(b):
+    _check(None, load_library().grpic_batch_destroy(b), "grpic_batch_destroy")
+
+
+# ---- convenience wrapper -----------------------------------------------------------------------
+class Simulation:
+    """One GRPIC context on the current CUDA device and PyTorch's current stream."""
+
+    def __init__(self, nx, ny, nz, m, a, c, dt, precision="fp64", quad_order=2, r_excise=0.0, flags=0,
+                 sort_interval=1, max_particles=0, stream=None, torch_allocator=True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("GRPIC needs a CUDA device")
+        load_library()
+        self.shape = (nz, ny, nx)
+        prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
+        cfg = grpic_config(nx, ny, nz, m, a, c, dt, prec, quad_order, r_excise, flags, sort_interval, max_particles)
+        if torch_allocator:
+            cfg.alloc = _torch_alloc
+            cfg.free_fn = _torch_free
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.handle = grpic_create(cfg, ctypes.c_void_p(stream))
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "handle", None):
+            grpic_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, d, b):
+        grpic_set_fields(self.handle, d, b)
+
+    def set_uniform_field(self, E=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0)):
+        grpic_set_uniform_field(self.handle, E, B)
+
+    def set_j(self, J):
+        grpic_set_j(self.handle, J)
+
+    def load_particles(self, species, q_over_m, q_macro, x4, u4, ids, umode=GRPIC_U_FULL):
+        if u4.shape[0] == 3:
+            u4 = np.vstack([np.asarray(u4), np.zeros((1, u4.shape[1]))])
+        grpic_load_particles(self.handle, species, q_over_m, q_macro, x4, u4, ids, umode)
+
+    def step(self, n=1):
+        grpic_step(self.handle, n)
+
+    def step_async(self, n=1):
+        grpic_step_async(self.handle, n)
+
+    def sync(self):
+        grpic_sync(self.handle)
+
+    def stage(self, s):
+        grpic_stage(self.handle, s)
+
+    def get_fields(self):
+        return grpic_get_fields(self.handle, self.shape)
+
+    def get_particles(self, species):
+        return grpic_get_particles(self.handle, species)
+
+    def num_particles(self, species):
+        return grpic_num_particles(self.handle, species)
+
+    def stats(self):
+        return grpic_get_stats(self.handle)
+
+    def set_profiling(self, on=True):
+        grpic_set_profiling(self.handle, on)
+
+    def profile(self, reset=False):
+        return grpic_get_profile(self.handle, reset)

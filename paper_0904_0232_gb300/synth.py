@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds none of the method's arithmetic (no metric, no field conversion): it draws
+positions and covariant spatial four-velocity components; each implementation completes u^4
+and converts the initial field itself.  Both the CUDA path and the oracle take these inputs.
+
+Recipe (stands in for the disk/corona set-ups of Sec. 6, which have no released data):
+  * positions uniform inside each cell of [1, n-3]^3 (so inside [1, n-2]), ``ppc`` per cell
+    and species, optionally skipping particles within Euclidean distance ``r_min`` of the
+    centre; pair plasmas are co-located (net charge density zero at start);
+  * covariant spatial momenta u_i / c isotropic with |u| drawn from the Maxwell-Juettner
+    distribution f(u) ~ u^2 exp(-(sqrt(1+u^2) - 1)/theta), theta = (u_th / c)^2, by inverse
+    transform of a tabulated CDF;
+  * macro-particle charge chosen so that the plasma frequency at the loaded density gives
+    omega_p dt = 0.25 (Sec. 5: omega_p dt < 2 with margin);
+  * the RNG is numpy's counter-based Philox keyed by (seed, species).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class SpeciesInput:
+    q_over_m: float
+    q_macro: float
+    x4: np.ndarray   # (4, n) grid coordinates, x^4 = 0
+    usp: np.ndarray  # (3, n) covariant spatial u_i (complete u^a with mode "covariant spatial")
+    ids: np.ndarray  # (n,) uint32
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    m: float
+    a: float
+    c: float
+    dt: float
+    B0: float
+    nsteps: int
+    species: list
+
+    @property
+    def n_particles(self) -> int:
+        return sum(s.ids.size for s in self.species)
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[int(seed), int(stream)]))
+
+
+def maxwell_juettner(rng: np.random.Generator, n: int, theta: float) -> np.ndarray:
+    """(3, n) isotropic momenta per unit mass (units of c) with |u| ~ u^2 exp(-(gamma-1)/theta)."""
+    if n == 0:
+        return np.zeros((3, 0))
+    umax = np.sqrt((1.0 + 40.0 * theta) ** 2 - 1.0)
+    u = np.linspace(0.0, umax, 20001)
+    pdf = u * u * np.exp(-(np.sqrt(1.0 + u * u) - 1.0) / theta)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(u))])
+    cdf /= cdf[-1]
+    mag = np.interp(rng.random(n), cdf, u)
+    d = rng.standard_normal((3, n))
+    d /= np.linalg.norm(d, axis=0, keepdims=True)
+    return d * mag
+
+
+def uniform_positions(rng, nx, ny, nz, ppc, r_min=0.0, cells=None):
+    """(3, n) positions, ppc per cell in cells [1, n-3]^3 (or the given (i, j, k) cell list)."""
+    if cells is None:
+        ci, cj, ck = np.meshgrid(np.arange(1, nx - 2), np.arange(1, ny - 2), np.arange(1, nz - 2), indexing="ij")
+        cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()])
+        order = np.lexsort((cells[0], cells[1], cells[2]))
+        cells = cells[:, order]
+    base = np.repeat(cells, ppc, axis=1).astype(np.float64)
+    x = base + rng.random(base.shape)
+    if r_min > 0.0:
+        cen = np.array([(nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2]).reshape(3, 1)
+        keep = ((x - cen) ** 2).sum(0) >= r_min * r_min
+        x = x[:, keep]
+    return x
+
+
+def charge_for(dt, ppc, q_over_m_list, wp_dt=0.25):
+    """|q_macro| with sum_s 4 pi ppc |q_macro| |q/m|_s = (wp_dt / dt)^2."""
+    return (wp_dt / dt) ** 2 / (4.0 * np.pi * ppc * sum(abs(q) for q in q_over_m_list))
+
+
+def plasma(name, n, m, a, c, dt, B0, nsteps, ppc, qms, u_th, seed, r_min=0.0, max_particles=None, cells=None):
+    rng = _rng(seed, 0)
+    x = uniform_positions(rng, n, n, n, ppc, r_min=r_min, cells=cells)
+    if max_particles is not None and x.shape[1] > max_particles:
+        x = x[:, :max_particles]
+    npart = x.shape[1]
+    x4 = np.vstack([x, np.zeros((1, npart))])
+    q = charge_for(dt, ppc, qms)
+    theta = (u_th / c) ** 2
+    species = []
+    for s, qm in enumerate(qms):
+        usp = maxwell_juettner(_rng(seed, 1 + s), npart, theta) * c
+        species.append(SpeciesInput(q_over_m=qm, q_macro=float(np.sign(qm) * q), x4=x4.copy(), usp=usp,
+                                    ids=np.arange(npart, dtype=np.uint32)))
+    return Workload(name, n, n, n, m, a, c, dt, B0, nsteps, species)
+
+
+def schwarzschild_pairs_32(seed=1, max_particles=None):
+    """a = 0, m = 2 cells, 32^3, e-/e+ pairs (q/m = -1, +1), 2 per cell per species outside
+    R = 3m, Maxwell-Juettner u_th = 0.1 c, uniform B_z = 0.05, dt = 0.4, 20 steps."""
+    return plasma("schwarzschild_pairs_32", 32, 2.0, 0.0, 1.0, 0.4, 0.05, 20, 2, (-1.0, 1.0), 0.1, seed,
+                  r_min=6.0, max_particles=max_particles)
+
+
+def kerr_ion_electron_128(seed=2, max_particles=None, n=128, cells=None):
+    """a = 0.9 m, m = 4 cells, 128^3, electrons (q/m = -1) and ions (q/m = +1/20), 8 per cell
+    per species, u_th = 0.05 c, uniform B_z = 0.1, dt = 0.4, 200 steps."""
+    return plasma(f"kerr_ion_electron_{n}", n, 4.0, 3.6, 1.0, 0.4, 0.1, 200, 8, (-1.0, 1.0 / 20.0), 0.05, seed,
+                  max_particles=max_particles, cells=cells)
+
+
+def random_fields(shape, seed, scale=0.05):
+    """Smooth-ish random prognostic fields (d, b), each (3, nz, ny, nx)."""
+    rng = _rng(seed, 99)
+    d = rng.standard_normal((3,) + tuple(shape)) * scale
+    b = rng.standard_normal((3,) + tuple(shape)) * scale
+    return d, b

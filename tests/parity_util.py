@@ -1,0 +1,82 @@
+"""Helpers for the GPU-vs-oracle parity tests: identical seeded starts and comparisons by id.
+
+Tolerances (per step, from identical state):
+  FP64 path         particles 1e-12 (relative to the state's max norm), J and fields 1e-12 (relative L2)
+  FP32-mixed path   particles 2e-6, J 1e-5 (relative L2), fields 1e-6 (relative L2; FP32 rounding
+                    of a stencil of O(10) terms)
+"""
+import numpy as np
+
+import oracle as O
+from paper_0904_0232_gb300 import synth
+from paper_0904_0232_gb300.grpic import Simulation
+
+TOL = {
+    "fp64": dict(particles=1e-12, J=1e-12, fields=1e-12),
+    "fp32_mixed": dict(particles=2e-6, J=1e-5, fields=1e-6),
+}
+
+
+def oracle_start(wl, threads=0, quad_order=2, flags=0, fields=None, r_excise=0.0):
+    """Oracle context loaded with the workload (u^4 completed by the oracle)."""
+    ref = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, quad_order=quad_order, threads=threads,
+                   flags=flags, r_excise=r_excise)
+    if fields is None:
+        ref.init_uniform_field(B=(0.0, 0.0, wl.B0))
+    else:
+        ref.set_fields(*fields)
+    for s, sp in enumerate(wl.species):
+        ref.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=1)
+    return ref
+
+
+def gpu_from_oracle(ref, wl, precision, quad_order=2, flags=0, sort_interval=1, r_excise=0.0):
+    """GPU context holding exactly the oracle's current state."""
+    sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=quad_order,
+                     flags=flags, sort_interval=sort_interval, r_excise=r_excise)
+    d, b, J = ref.get_fields()
+    sim.set_fields(d, b)
+    sim.set_j(J)
+    for s, sp in enumerate(wl.species):
+        x, u, ids = ref.get_particles(s)
+        sim.load_particles(s, sp.q_over_m, sp.q_macro, x, u, ids)
+    return sim
+
+
+def particle_errors(sim, ref, species, x4_scale=None):
+    """Max relative errors (x spatial, x^4, u) over particles matched by id; survivors must match."""
+    xr, ur, ir = ref.get_particles(species)
+    x, u, ids = sim.get_particles(species)
+    o = np.argsort(ids, kind="stable")
+    assert np.array_equal(ids[o], ir), f"survivor sets differ: {ids.size} vs {ir.size}"
+    if ir.size == 0:
+        return 0.0, 0.0, 0.0
+    x, u = x[:, o], u[:, o]
+    ex = (np.abs(x[:3] - xr[:3]).max(0) / np.abs(xr[:3]).max(0)).max()
+    s4 = np.maximum(np.abs(xr[3]), x4_scale if x4_scale is not None else 1.0)
+    e4 = (np.abs(x[3] - xr[3]) / s4).max()
+    eu = (np.abs(u - ur).max(0) / np.abs(ur).max(0)).max()
+    return ex, e4, eu
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def small_kerr(n=24, ppc=1, seed=5, r_min=None, nxyz=None, m=2.0, a=1.6):
+    """A small Kerr plasma spanning several cells and a ragged particle count."""
+    wl = synth.plasma("small_kerr", n, m, a, 1.0, 0.4, 0.08, 3, ppc, (-1.0, 0.05), 0.1, seed,
+                      r_min=(2.2 * m if r_min is None else r_min))
+    if nxyz is not None:
+        nx, ny, nz = nxyz
+        rng = np.random.default_rng(seed)
+        wl.nx, wl.ny, wl.nz = nx, ny, nz
+        for sp in wl.species:
+            n0 = sp.ids.size
+            x = np.vstack([rng.uniform(1.0, nx - 2.0, n0), rng.uniform(1.0, ny - 2.0, n0),
+                           rng.uniform(1.0, nz - 2.0, n0), np.zeros(n0)])
+            cen = np.array([(nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2]).reshape(3, 1)
+            keep = np.sqrt(((x[:3] - cen) ** 2).sum(0)) > 2.2 * m
+            sp.x4, sp.usp, sp.ids = x[:, keep], sp.usp[:, keep], sp.ids[keep]
+    return wl
