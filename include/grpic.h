@@ -90,7 +90,7 @@ typedef struct {
   double dt;             /* time step; c dt < 1/sqrt(3) is required */
   int precision;         /* GRPIC_FP64 or GRPIC_FP32_MIXED */
   int quad_order;        /* Q of the Q x Q Gauss-Legendre rule of Eq. 18: 1, 2 or 3 (0 -> 2) */
-  double r_excise;       /* fields at r < r_excise are frozen; <= 0 -> 0.5 r_+ */
+  double r_excise;       /* fields at r < r_excise are frozen; <= 0 -> r_+ (the inside of the horizon) */
   unsigned flags;        /* GRPIC_NO_GAMMA_IN_J */
   int sort_interval;     /* counting sort every k steps (<= 0 -> 1) */
   int64_t max_particles; /* capacity per species (0 -> set by the first load) */

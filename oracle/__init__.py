@@ -98,6 +98,7 @@ def lib():
                 "orc_deposit": (ctypes.c_int, [_V, _D, _D, ctypes.c_double, ctypes.c_double]),
                 "orc_face_weights": (None, [_V, ctypes.c_int, _D, _I, _D]),
                 "orc_get_stats": (None, [_V, _LL]),
+                "orc_last_moves": (ctypes.c_int, [_V, ctypes.c_int, _LL, _D, _D, _U32]),
                 "orc_gamma_terms": (None, [_V, _D]),
                 "orc_max_threads": (ctypes.c_int, []),
             }
@@ -341,6 +342,17 @@ class Oracle:
         c = np.ascontiguousarray(cell, dtype=np.int32)
         lib().orc_face_weights(self._h, int(K), _dp(_f64(P)), c.ctypes.data_as(_I), _dp(W))
         return W
+
+    def last_moves(self, species):
+        """(x0, x1, ids) of every particle of the last push, removed ones included."""
+        n = ctypes.c_longlong(0)
+        self._chk(lib().orc_last_moves(self._h, int(species), ctypes.byref(n), None, None, None), "last_moves")
+        x0 = np.zeros((3, n.value))
+        x1 = np.zeros((3, n.value))
+        ids = np.zeros(n.value, dtype=np.uint32)
+        self._chk(lib().orc_last_moves(self._h, int(species), ctypes.byref(n), _dp(x0), _dp(x1),
+                                       ids.ctypes.data_as(_U32)), "last_moves")
+        return x0, x1, ids
 
     def stats(self):
         out = (ctypes.c_longlong * 4)()

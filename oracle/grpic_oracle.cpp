@@ -43,8 +43,9 @@
  *   A13 J = rho u = rho gamma v: the Umeda flux is multiplied by gamma_bar =
  *       (u^4_n + u^4_{n+1}) / (2c) unless ORC_NO_GAMMA_IN_J is set.
  *   A15 Particles are removed when r <= r_+ or a coordinate leaves [1, N-2].  Field
- *       components on the outer two index layers, or at points with r < r_excise, are
- *       not advanced; field conversions at points with r < r_excise use the flat metric.
+ *       components on the outer two index layers, or at points with r < r_excise (default
+ *       r_+: the whole inside of the horizon), are not advanced; field conversions at points
+ *       with r < r_excise use the flat metric.
  *       A metric evaluated where r = 0 exactly (the disk z = 0, R <= a) is flat.
  *   A16 Particles are pushed with the fields present after the first B half-step;
  *       J is deposited from x_n -> x_{n+1}.
@@ -416,6 +417,9 @@ struct Species {
   double qm = 0.0, qmacro = 0.0;
   std::vector<double> x[4], u[4];
   std::vector<uint32_t> id;
+  // start and end positions of every particle of the last push (removed ones included)
+  std::vector<double> last_x0[3], last_x1[3];
+  std::vector<uint32_t> last_id;
 };
 
 }  // namespace
@@ -426,7 +430,7 @@ typedef struct {
   int nx, ny, nz;
   double m, a, c, dt;
   int quad_order;
-  double r_excise;  // <= 0: 0.5 r_+
+  double r_excise;  // <= 0: r_+
   unsigned flags;
   int threads;  // <= 0: all available
 } orc_config;
@@ -834,6 +838,8 @@ struct Ctx {
     int err = ORC_OK;
     for (auto& s : sp) {
       const size_t np = s.id.size();
+      for (int ax = 0; ax < 3; ++ax) s.last_x0[ax] = s.x[ax];
+      s.last_id = s.id;
       std::vector<char> rem(np, 0), hor(np, 0);
       std::vector<std::vector<double>> Jt((size_t)nthreads * 3);
       for (auto& v : Jt) v.assign(ncell, 0.0);
@@ -859,6 +865,7 @@ struct Ctx {
           hor[p] = hz;
         }
       }
+      for (int ax = 0; ax < 3; ++ax) s.last_x1[ax] = s.x[ax];
       for (int t = 0; t < nthreads; ++t) {
         if (terr[t] != ORC_OK && err == ORC_OK) err = terr[t];
         stat_fallback += tfb[t];
@@ -1151,7 +1158,7 @@ void* orc_create(const orc_config* cfg) {
   ctx->n[2] = cfg->nz;
   for (int ax = 0; ax < 3; ++ax) ctx->Xc[ax] = 0.5 * (ctx->n[ax] - 1);
   ctx->r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
-  ctx->r_exc = cfg->r_excise > 0 ? cfg->r_excise : 0.5 * ctx->r_plus;
+  ctx->r_exc = cfg->r_excise > 0 ? cfg->r_excise : ctx->r_plus;
   ctx->ncell = (size_t)cfg->nx * cfg->ny * cfg->nz;
   for (auto& f : ctx->F) f.assign(ctx->ncell, 0.0);
   for (auto& j : ctx->J) j.assign(ctx->ncell, 0.0);
@@ -1248,12 +1255,23 @@ int orc_load_particles(void* p, int species, double qm, double qmacro, long long
     s.u[al].assign(n, 0.0);
   }
   s.id.assign(n, 0);
-  for (long long w = 0; w < n; ++w) {
-    const size_t i = order[w];
+  long long w = 0;
+  for (long long o = 0; o < n; ++o) {
+    const size_t i = order[o];
     double x[4], u[4];
     for (int al = 0; al < 4; ++al) x[al] = x4[al * n + i];
     for (int ax = 0; ax < 3; ++ax)
       if (!(x[ax] >= 1.0 && x[ax] <= ctx->n[ax] - 2)) return ORC_ERR_INVALID;
+    // removal rule r <= r_+ (A15) applies from the start
+    if (ctx->cfg.m > 0.0) {
+      double X[3];
+      ctx->rel(x, X);
+      const KerrFK<double> kf = kerr_fk<double>(X, ctx->cfg.m, ctx->cfg.a);
+      if (kf.flat || kf.r <= ctx->r_plus) {
+        ++ctx->stat_removed_horizon;
+        continue;
+      }
+    }
     if (umode == 0) {
       for (int al = 0; al < 4; ++al) u[al] = u4[al * n + i];
     } else {
@@ -1267,7 +1285,13 @@ int orc_load_particles(void* p, int species, double qm, double qmacro, long long
       s.u[al][w] = u[al];
     }
     s.id[w] = ids[i];
+    ++w;
   }
+  for (int al = 0; al < 4; ++al) {
+    s.x[al].resize(w);
+    s.u[al].resize(w);
+  }
+  s.id.resize(w);
   return ORC_OK;
 }
 
@@ -1328,6 +1352,27 @@ int orc_deposit(void* p, const double* x1, const double* x2, double qmacro, doub
 
 void orc_face_weights(void* p, int K, const double* P, const int* cell, double* W4) {
   static_cast<Ctx*>(p)->face_weights(K, P, cell, W4);
+}
+
+// Moves of the last push of a species: n_out in/out, x0/x1 planar (3, n).
+int orc_last_moves(void* p, int species, long long* n_inout, double* x0, double* x1, uint32_t* ids) {
+  Ctx* ctx = static_cast<Ctx*>(p);
+  if (species < 0 || species >= (int)ctx->sp.size()) return ORC_ERR_INVALID;
+  const Species& s = ctx->sp[species];
+  const long long n = (long long)s.last_id.size();
+  if (!x0) {
+    *n_inout = n;
+    return ORC_OK;
+  }
+  if (*n_inout < n) return ORC_ERR_INVALID;
+  for (int ax = 0; ax < 3; ++ax)
+    for (long long i = 0; i < n; ++i) {
+      x0[ax * n + i] = s.last_x0[ax][i];
+      x1[ax * n + i] = s.last_x1[ax][i];
+    }
+  for (long long i = 0; i < n; ++i) ids[i] = s.last_id[i];
+  *n_inout = n;
+  return ORC_OK;
 }
 
 // stats: removed_horizon, removed_outer, f_fallbacks, steps

@@ -51,6 +51,7 @@ struct grpic_ctx {
   SortScratch sort{};
   SpeciesStore sp[kMaxSpecies];
   long long steps = 0;
+  long long pushes = 0;  // push stages run: particle x^4 is stored relative to c dt * pushes
   int since_sort = 0;
   grpic_stats totals{};
   // tracing
@@ -160,6 +161,7 @@ void enqueue_stage(grpic_ctx* c, int stage) {
         launch_push_deposit<T>(c->g, F, particles_view<T>(c, s, S.cur), spc, c->st, c->mixed, 0.0, c->stream);
         c->launches += 1;
       }
+      c->pushes += 1;
       break;
     case GRPIC_STAGE_E:
       launch_e_step<T>(c->g, F, c->stream);
@@ -344,7 +346,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.yc = 0.5 * (cfg->ny - 1);
   g.zc = 0.5 * (cfg->nz - 1);
   g.r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
-  g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : 0.5 * g.r_plus;
+  g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : g.r_plus;
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
 
@@ -512,7 +514,7 @@ grpic_status grpic_load_particles(grpic_ctx* c, int species, double q_over_m, do
   S.n = n;
   S.loaded = true;
   S.shadow_pending = false;
-  const double ct_now = c->g.c * c->g.dt * (double)c->steps;
+  const double ct_now = c->g.c * c->g.dt * (double)c->pushes;
   const int ni = (int)n;
   cudaMemcpyAsync(S.n_dev, &ni, sizeof(int), cudaMemcpyHostToDevice, c->stream);
   if (c->mixed)
@@ -635,7 +637,7 @@ grpic_status grpic_get_particles(grpic_ctx* c, int species, int64_t* n_inout, do
   }
   *n_inout = n;
   if (n == 0) return GRPIC_OK;
-  const double ct_now = c->g.c * c->g.dt * (double)c->steps;
+  const double ct_now = c->g.c * c->g.dt * (double)c->pushes;
   SpeciesStore& S = c->sp[species];
   double *dx = x4, *du = u4;
   uint32_t* di = ids;

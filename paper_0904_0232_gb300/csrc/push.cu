@@ -166,35 +166,41 @@ __device__ __forceinline__ T area(const Consts& C, int K, T xK, int I, T Is, T I
   return s * T(0.25) * (If - Is) * (Jf - Js);
 }
 
+// Umeda zig-zag deposit of the move x0 -> x0 + dx.  The segment displacements are carried
+// as offsets from x0 (s1 = relay - x0, s2 = dx - s1), so the flux keeps the accuracy of the RK4
+// increment instead of inheriting the rounding of the stored positions.  With |dx| < 1 the
+// relay point min(min(a,b)+1, max(max(a,b), mid)) is the midpoint when the cell does not
+// change along an axis and the shared face otherwise.
 template <typename T, int Q, bool MIXED>
-__device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const Consts& C, const T x1[3],
-                                        const T x2[3], T qg, T inv_dt, unsigned& flags, unsigned& n64) {
+__device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const Consts& C, const T x0[3],
+                                        const T dx[3], T qg, T inv_dt, unsigned& flags, unsigned& n64) {
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
-  T xr[3];
+  T s1[3], s2[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    int a = (int)floor(x1[ax]), b = (int)floor(x2[ax]);
+    int a = (int)floor(x0[ax]), b = (int)floor(x0[ax] + dx[ax]);
     if (a < 0 || b < 0 || a > nn[ax] - 2 || b > nn[ax] - 2) flags |= ST_RANGE;
     a = min(max(a, 0), nn[ax] - 2);
     b = min(max(b, 0), nn[ax] - 2);
     c1[ax] = a;
     c2[ax] = b;
-    const T mid = T(0.5) * (x1[ax] + x2[ax]);
-    xr[ax] = fmin((T)(min(a, b) + 1), fmax((T)max(a, b), mid));
+    s1[ax] = (a == b) ? T(0.5) * dx[ax] : (T)max(a, b) - x0[ax];
+    s2[ax] = dx[ax] - s1[ax];
   }
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
 #pragma unroll
   for (int seg = 0; seg < 2; ++seg) {
-    const T* a = seg ? xr : x1;
-    const T* b = seg ? x2 : xr;
     const int* cell = seg ? c2 : c1;
-    T P[3];
+    T P[3], dseg[3];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) P[ax] = T(0.5) * (a[ax] + b[ax]);
+    for (int ax = 0; ax < 3; ++ax) {
+      dseg[ax] = seg ? s2[ax] : s1[ax];
+      P[ax] = seg ? x0[ax] + (s1[ax] + T(0.5) * s2[ax]) : x0[ax] + T(0.5) * s1[ax];
+    }
 #pragma unroll
     for (int K = 0; K < 3; ++K) {
-      const T dK = b[K] - a[K];
+      const T dK = dseg[K];
       if (dK == T(0)) continue;
       const T flux = qg * dK * inv_dt;
       const int I = (K + 1) % 3, J = (K + 2) % 3;
@@ -273,13 +279,14 @@ __global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields
     }
     // stage 4
     accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
-    T x1[4], u1[4];
+    T x1[4], u1[4], dx[4];
     const T h6 = h / T(6);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       sx[q] += us[q];
       su[q] += a[q];
-      x1[q] = x0[q] + h6 * sx[q];
+      dx[q] = h6 * sx[q];
+      x1[q] = x0[q] + dx[q];
       u1[q] = u0[q] + h6 * su[q];
     }
     x1[3] -= (T)(g.c * g.dt);  // x^4 is stored relative to c t
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields
     if (finite && sp.qmacro != 0.0) {
       const T gbar = (g.flags & 1u) ? T(1) : (u0[3] + u1[3]) / (T(2) * (T)g.c);
       const T qg = (T)sp.qmacro * gbar;
-      deposit<T, (Q > 0 ? Q : 2), MIXED>(g, F, C, x0, x1, qg, T(1) / dt, flags, n64);
+      deposit<T, Q, MIXED>(g, F, C, x0, dx, qg, T(1) / dt, flags, n64);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -346,7 +353,14 @@ __global__ void k_load(const Grid g, const Particles<T> P, long long n, const do
   for (int q = 0; q < 3; ++q)
     if (!(x[q] >= 1.0 && x[q] <= nn[q] - 2)) bad |= ST_LOAD_INVALID;
   double u[4] = {u4[i], u4[n + i], u4[2 * n + i], umode == 0 ? u4[3 * n + i] : 0.0};
-  if (!bad && umode != 0) {
+  // the removal rule (r <= r_+) applies from the start: such particles are dropped at load
+  bool inside = false;
+  if (!bad && g.m > 0.0) {
+    const Kerr<double> K = kerr_eval<double>(x[0] - g.xc, x[1] - g.yc, x[2] - g.zc, g.m, g.a);
+    inside = K.flat || K.r <= g.r_plus;
+    if (inside) atomicAdd(&st->removed_horizon, 1ull);
+  }
+  if (!bad && !inside && umode != 0) {
     const Kerr<double> K = kerr_eval<double>(x[0] - g.xc, x[1] - g.yc, x[2] - g.zc, g.m, g.a);
     const double f = K.f, kk[4] = {K.k0, K.k1, K.k2, 1.0};
     const double c2 = g.c * g.c;
@@ -397,7 +411,7 @@ __global__ void k_load(const Grid g, const Particles<T> P, long long n, const do
   const int ci = min(max((int)floor(x[0]), 0), g.nx - 2);
   const int cj = min(max((int)floor(x[1]), 0), g.ny - 2);
   const int ck = min(max((int)floor(x[2]), 0), g.nz - 2);
-  P.key[i] = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
+  P.key[i] = inside ? kDead : (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
 }
 
 template <typename T>

@@ -24,7 +24,7 @@ __global__ void k_hist(const uint32_t* __restrict__ key, long long n, const int*
   atomicAdd(counts + (k == kDead ? dead_bin : (long long)k), 1);
 }
 
-// Inclusive scan of one value per thread across the block; returns the block total.
+// Inclusive scan of one value per thread across the block.
 __device__ __forceinline__ int block_inclusive_scan(int v, int* warp_sums) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -45,10 +45,8 @@ __device__ __forceinline__ int block_inclusive_scan(int v, int* warp_sums) {
   }
   __syncthreads();
   if (wid > 0) v += warp_sums[wid - 1];
-  const int total = warp_sums[kScanThreads / 32 - 1];
   __syncthreads();
   return v;
-  (void)total;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const int* __restrict__ in, long long n,
@@ -140,8 +138,10 @@ void launch_sort(const Grid& g, const Particles<T>& src, const Particles<T>& dst
   k_tile_sums<<<ntiles, kScanThreads, 0, stream>>>(s.counts, nbins, s.blocks);
   k_scan_tile_sums<<<1, kScanThreads, 0, stream>>>(s.blocks, ntiles);
   k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(s.counts, nbins, s.blocks, s.offsets);
-  k_live_count<<<1, 1, 0, stream>>>(s.offsets, dead_bin, n_out);
+  // scatter first: it reads the old count through src.n_dev, which may alias n_out.  Removed
+  // particles never take a slot, so the cursor of the removed bin still holds the live count.
   if (src.n > 0) k_scatter<T><<<blocks_for(src.n, 256), 256, 0, stream>>>(src, dst, s.offsets, dead_bin);
+  k_live_count<<<1, 1, 0, stream>>>(s.offsets, dead_bin, n_out);
 }
 
 template void launch_sort<float>(const Grid&, const Particles<float>&, const Particles<float>&, const SortScratch&,

@@ -59,6 +59,43 @@ def particle_errors(sim, ref, species, x4_scale=None):
     return ex, e4, eu
 
 
+def face_ambiguity_mask(ref, shape, nspecies, delta=2e-5):
+    """Grid nodes whose J depends on a floating-point-decided cell index: the zig-zag split of
+    a move changes discontinuously when an endpoint crosses a cell face, so a particle whose
+    start or end lies within `delta` of a face (per the oracle) can be split differently by an
+    FP32 kernel.  Returns a boolean (nz, ny, nx) mask of the nodes its deposit can touch."""
+    nz, ny, nx = shape
+    mask = np.zeros(shape, dtype=bool)
+    for s in range(nspecies):
+        x0, x1, _ = ref.last_moves(s)
+        if x0.size == 0:
+            continue
+        near = np.zeros(x0.shape[1], dtype=bool)
+        for x in (x0, x1):
+            fr = x - np.floor(x)
+            near |= (np.minimum(fr, 1.0 - fr) < delta).any(0)
+        for p in np.nonzero(near)[0]:
+            lo = np.floor(np.minimum(x0[:, p], x1[:, p])).astype(int) - 1
+            hi = np.floor(np.maximum(x0[:, p], x1[:, p])).astype(int) + 3
+            lo = np.maximum(lo, 0)
+            mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
+    return mask
+
+
+def dilate(mask, r):
+    out = mask.copy()
+    for ax in range(3):
+        for _ in range(r):
+            out |= np.roll(out, 1, axis=ax) | np.roll(out, -1, axis=ax)
+    return out
+
+
+def rel_l2_masked(a, b, mask):
+    """Relative L2 over the (3, nz, ny, nx) arrays, ignoring nodes where mask is set."""
+    keep = ~np.broadcast_to(mask, a.shape)
+    return rel_l2(a[keep], b[keep])
+
+
 def rel_l2(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)

@@ -1,0 +1,104 @@
+"""Parity at the benchmark's full size and launch configuration: Kerr a = 0.9 m, m = 4, 128^3,
+electron-ion plasma with 8 particles per cell per species (31.25 M particles), loaded from the
+same seeded generator into the CUDA library and (a sample of it) into the oracle.
+
+* the first B half-step on the whole grid, element by element;
+* the push of sampled particles (random ones plus the ones closest to the hole), one by one;
+* J through a property that holds at any size: the Umeda split conserves the total flux, so
+  sum_nodes J^K = sum_p q gamma_bar dx^K / dt over all pushed particles (computed here from the
+  GPU's own before/after particle states in FP64).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from parity_util import TOL, rel_l2
+from paper_0904_0232_gb300 import synth
+from paper_0904_0232_gb300.grpic import (GRPIC_STAGE_B_HALF, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_ZERO_J,
+                                         GRPIC_U_COV_SPATIAL, Simulation)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def workload():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return synth.kerr_ion_electron_128(seed=2)
+
+
+@pytest.fixture(scope="module")
+def oracle_fields(workload):
+    wl = workload
+    ref = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=0, flags=O.NO_GAMMA_TERMS)
+    ref.init_uniform_field(B=(0.0, 0.0, wl.B0))
+    ref.b_half()
+    return ref
+
+
+def _by_id(x, u, ids):
+    o = np.argsort(ids, kind="stable")
+    return x[:, o], u[:, o], ids[o]
+
+
+@pytest.mark.parametrize("prec", ["fp32_mixed", "fp64"])
+def test_full_size_step(workload, oracle_fields, prec):
+    import torch
+
+    wl = workload
+    ref = oracle_fields
+    sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=prec)
+    sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
+    for s, sp in enumerate(wl.species):
+        x = torch.from_numpy(sp.x4).cuda()
+        u = torch.from_numpy(np.vstack([sp.usp, np.zeros((1, sp.usp.shape[1]))])).cuda()
+        i = torch.from_numpy(sp.ids.view(np.int32)).cuda()
+        sim.load_particles(s, sp.q_over_m, sp.q_macro, x, u, i, umode=GRPIC_U_COV_SPATIAL)
+        del x, u, i
+    before = [_by_id(*sim.get_particles(s)) for s in range(2)]
+    sim.stage(GRPIC_STAGE_B_HALF)
+    d, b, _ = sim.get_fields()
+    dr, br, _ = ref.get_fields()
+    assert rel_l2(b, br) <= TOL[prec]["fields"]
+    assert rel_l2(d, dr) <= (1e-15 if prec == "fp64" else 1e-7)
+    sim.stage(GRPIC_STAGE_ZERO_J)
+    sim.stage(GRPIC_STAGE_PUSH_DEPOSIT)
+    _, _, J = sim.get_fields()
+    after = [_by_id(*sim.get_particles(s)) for s in range(2)]  # flagged particles stay listed until the sort
+
+    cen = np.array([(wl.nx - 1) / 2] * 3).reshape(3, 1)
+    rng = np.random.default_rng(0)
+    flux_total = np.zeros(3)
+    flux_abs = np.zeros(3)
+    for s, sp in enumerate(wl.species):
+        x0, u0, i0 = before[s]
+        x1, u1, i1 = after[s]
+        assert np.array_equal(i0, i1)
+        gbar = (u0[3] + u1[3]) / (2.0 * wl.c)
+        dxs = x1[:3] - x0[:3]
+        contrib = sp.q_macro * gbar * dxs / wl.dt
+        flux_total += contrib.sum(1)
+        flux_abs += np.abs(contrib).sum(1)
+        # sampled particles: random ones and the 300 closest to the hole
+        R = np.sqrt(((x0[:3] - cen) ** 2).sum(0))
+        pick = np.unique(np.concatenate([rng.choice(i0.size, 1500, replace=False), np.argsort(R)[:300]]))
+        o = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=0, flags=O.NO_GAMMA_TERMS)
+        o.set_fields(dr, br)
+        gen_ids = sp.ids
+        sel = np.searchsorted(gen_ids, i0[pick])
+        o.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4[:, sel], sp.usp[:, sel], gen_ids[sel], umode=1)
+        o.push_deposit()
+        xr0, xr1, ir = o.last_moves(s)
+        assert np.array_equal(ir, i0[pick])
+        # positions after the push (removed ones included) and velocities of the survivors
+        ex = np.abs(x1[:3, pick] - xr1).max(0) / np.abs(xr1).max(0)
+        assert ex.max() <= TOL[prec]["particles"], ex.max()
+        xs, us, ids_s = o.get_particles(s)
+        keep = np.searchsorted(i0[pick], ids_s)
+        eu = np.abs(u1[:, pick][:, keep] - us).max(0) / np.abs(us).max(0)
+        assert eu.max() <= TOL[prec]["particles"], eu.max()
+    jsum = J.reshape(3, -1).sum(1)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.all(np.abs(jsum - flux_total) <= tol * flux_abs), (jsum, flux_total, flux_abs)
+    sim.close()

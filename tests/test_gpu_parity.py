@@ -4,7 +4,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from parity_util import TOL, gpu_from_oracle, oracle_start, particle_errors, rel_l2, small_kerr
+from parity_util import (TOL, dilate, face_ambiguity_mask, gpu_from_oracle, oracle_start, particle_errors, rel_l2,
+                         rel_l2_masked, small_kerr)
 from paper_0904_0232_gb300 import synth
 from paper_0904_0232_gb300.grpic import (GRPIC_STAGE_B_HALF, GRPIC_STAGE_E, GRPIC_STAGE_PUSH_DEPOSIT,
                                          GRPIC_STAGE_ZERO_J, GRPIC_U_CONTRA_SPATIAL, GRPIC_U_COV_SPATIAL,
@@ -23,6 +24,22 @@ def _cuda():
 
 def _rand_fields(shape, seed, scale=0.05):
     return synth.random_fields(shape, seed, scale)
+
+
+def check_j(J, Jr, ref, nspecies, prec, factor=1.0):
+    """J parity.  FP32: nodes touched by a particle whose cell index is decided within rounding
+    of a face are compared only through the split-independent total flux per component.
+    Returns the mask used (all False for FP64)."""
+    tol = TOL[prec]["J"] * factor
+    if prec == "fp64":
+        assert rel_l2(J, Jr) <= tol, rel_l2(J, Jr)
+        return np.zeros(J.shape[1:], dtype=bool)
+    mask = face_ambiguity_mask(ref, J.shape[1:], nspecies)
+    assert mask.mean() < 0.05, mask.mean()
+    assert rel_l2_masked(J, Jr, mask) <= tol, rel_l2_masked(J, Jr, mask)
+    for K in range(3):
+        assert abs(J[K].sum() - Jr[K].sum()) <= tol * max(np.abs(Jr[K]).sum(), 1e-300)
+    return mask
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -98,8 +115,9 @@ def test_load_rejects_bad_input():
     with pytest.raises(GrpicError) as ei:
         sim.load_particles(0, -1.0, 0.0, x4, u4, np.array([0], np.uint32))
     assert ei.value.code == 1
-    # contravariant completion inside the ergoregion is ambiguous and refused
-    x4 = np.array([[7.5 + 1.6], [7.5], [7.5], [0.0]])
+    # contravariant completion inside the ergoregion (outside the horizon) is ambiguous and refused:
+    # m = 1, a = 0.5, equatorial plane: horizon at R = 1.93, ergosurface at R = 2.06
+    x4 = np.array([[7.5 + 2.0], [7.5], [7.5], [0.0]])
     with pytest.raises(GrpicError):
         sim.load_particles(0, -1.0, 0.0, x4, np.zeros((4, 1)), np.array([0], np.uint32), umode=GRPIC_U_CONTRA_SPATIAL)
 
@@ -122,7 +140,7 @@ def test_push_deposit_stage(prec, Q):
         assert e4 <= tol["particles"]
     _, _, J = sim.get_fields()
     _, _, Jr = ref.get_fields()
-    assert rel_l2(J, Jr) <= tol["J"], rel_l2(J, Jr)
+    check_j(J, Jr, ref, 2, prec)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -133,18 +151,20 @@ def test_full_steps(prec, dims):
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, prec)
     tol = TOL[prec]
+    seen = np.zeros((wl.nz, wl.ny, wl.nx), dtype=bool)
     for step in range(3):
         ref.step(1)
         sim.step(1)
         for s in range(2):
             ex, e4, eu = particle_errors(sim, ref, s)
-            # errors compound over steps: allow the per-step bound times the step count
+            # errors compound over steps: allow the per-step bound times 4^step
             assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
         d, b, J = sim.get_fields()
         dr, br, Jr = ref.get_fields()
-        assert rel_l2(J, Jr) <= tol["J"] * 4 ** step
-        assert rel_l2(b, br) <= tol["fields"] * 4 ** step
-        assert rel_l2(d, dr) <= max(tol["fields"], tol["J"]) * 4 ** step
+        # fields downstream of an ambiguous split differ there; the stencils spread it by 3/step
+        seen = dilate(seen, 3) | check_j(J, Jr, ref, 2, prec, 4 ** step)
+        assert rel_l2_masked(b, br, seen) <= tol["fields"] * 4 ** step
+        assert rel_l2_masked(d, dr, seen) <= max(tol["fields"], tol["J"]) * 4 ** step
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -190,6 +210,43 @@ def test_removal_matches_oracle(prec):
     assert st["removed_outer"] == rs["removed_outer"] > 0
 
 
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_load_drops_particles_inside_horizon(prec):
+    wl = small_kerr(n=24, ppc=2, seed=12, r_min=0.0)
+    ref = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt)
+    sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=prec)
+    sp = wl.species[1]
+    ref.load_particles(0, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=1)
+    sim.load_particles(0, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=GRPIC_U_COV_SPATIAL)
+    assert ref.stats()["removed_horizon"] > 0
+    assert sim.stats()["removed_horizon"] == ref.stats()["removed_horizon"]
+    ex, e4, eu = particle_errors(sim, ref, 0)
+    assert max(ex, eu) <= (1e-13 if prec == "fp64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_near_horizon_full_density(prec):
+    """Every cell filled (8 per cell per species), Kerr a = 0.9 m, m = 4 on a 32^3 grid: particles
+    start just outside the horizon, fall in and are removed; two whole steps against the oracle."""
+    wl = synth.kerr_ion_electron_128(seed=3, n=32)
+    ref = oracle_start(wl)
+    loaded_inside = ref.stats()["removed_horizon"]
+    sim = gpu_from_oracle(ref, wl, prec)
+    tol = TOL[prec]
+    seen = np.zeros((wl.nz, wl.ny, wl.nx), dtype=bool)
+    for step in range(2):
+        ref.step(1)
+        sim.step(1)
+        for s in range(2):
+            ex, e4, eu = particle_errors(sim, ref, s)
+            assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
+        d, b, J = sim.get_fields()
+        dr, br, Jr = ref.get_fields()
+        seen = dilate(seen, 3) | check_j(J, Jr, ref, 2, prec, 4 ** step)
+        assert rel_l2_masked(b, br, seen) <= tol["fields"] * 4 ** step
+    assert sim.stats()["removed_horizon"] == ref.stats()["removed_horizon"] - loaded_inside > 0
+
+
 def test_empty_species_and_zero_particles():
     sim = Simulation(16, 16, 16, 1.0, 0.5, 1.0, 0.4, precision="fp32_mixed")
     sim.set_uniform_field(B=(0, 0, 0.1))
@@ -221,4 +278,4 @@ def test_no_gamma_flag(prec):
     ref.push_deposit()
     sim.stage(GRPIC_STAGE_ZERO_J)
     sim.stage(GRPIC_STAGE_PUSH_DEPOSIT)
-    assert rel_l2(sim.get_fields()[2], ref.get_fields()[2]) <= TOL[prec]["J"]
+    check_j(sim.get_fields()[2], ref.get_fields()[2], ref, 2, prec)

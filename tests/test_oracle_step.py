@@ -76,3 +76,14 @@ def test_regression_snapshot():
     for k in gold.files:
         assert out[k].shape == gold[k].shape
         assert np.allclose(out[k], gold[k], rtol=1e-13, atol=1e-15), k
+
+
+def test_particles_inside_horizon_are_dropped_at_load():
+    """The removal rule r <= r_+ (A15) applies from the start."""
+    N, m, a = 20, 2.0, 1.0
+    o = O.Oracle(N, N, N, m, a, 1.0, 0.4)
+    Xc = o.centre
+    x4 = np.array([[Xc[0] + 0.3, Xc[0] + 7.0], [Xc[1], Xc[1]], [Xc[2] + 0.2, Xc[2]], [0.0, 0.0]])
+    o.load_particles(0, -1.0, 0.0, x4, np.zeros((3, 2)), [5, 6], umode=1)
+    assert list(o.get_particles(0)[2]) == [6]
+    assert o.stats()["removed_horizon"] == 1
