@@ -57,7 +57,8 @@ typedef enum {
 enum { GRPIC_FP64 = 0, GRPIC_FP32_MIXED = 1 };
 
 enum {
-  GRPIC_NO_GAMMA_IN_J = 1u /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
+  GRPIC_NO_GAMMA_IN_J = 1u,     /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
+  GRPIC_LITERAL_HALF_STEPS = 2u /* field update with each half-step explicit in its own start value (see below) */
 };
 
 enum { GRPIC_MEM_HOST = 0, GRPIC_MEM_DEVICE = 1 };
@@ -70,13 +71,22 @@ enum {
   GRPIC_LOAD_DEVICE = 16     /* x4, u4, ids are device pointers */
 };
 
-/* Pipeline stages for grpic_stage (each is one row of the timestep). */
+/* Pipeline stages for grpic_stage (each is one row of the timestep).
+ * Field time levels (Sec. 3: B is advanced in two half-steps around the push, E a full step):
+ * the stored b lags d by half a step.  By default the update is time-centred: the first half
+ * takes b^{n-1/2} to b^n = b^{n-1/2} - (dx^4/2) curl e(b^{n-1/2}, d^n) for the push; the second
+ * gives b^{n+1/2} = b^{n-1/2} - dx^4 curl e(b^n, d^n); the E step evaluates the d-dependence of
+ * the contravariant tensor at a midpoint predictor of d.  In Kerr-Schild coordinates e depends
+ * on b (and h on d) through the shift, and the literal explicit form (GRPIC_LITERAL_HALF_STEPS:
+ * each half-step b -= (dx^4/2) curl e(b, d) from its own start, E step explicit in d) is a
+ * forward-Euler step of a centred advection term, which grows without bound. */
 enum {
-  GRPIC_STAGE_B_HALF = 0,       /* Sec. 3.1, Eq. 10: b <- b - (dx^4/2) curl e */
+  GRPIC_STAGE_B_HALF = 0,       /* Sec. 3.1, Eq. 10: first B half-step */
   GRPIC_STAGE_ZERO_J = 1,       /* J <- 0 */
   GRPIC_STAGE_PUSH_DEPOSIT = 2, /* Sec. 3.3 + Sec. 4: RK4 push, curved deposit, removal flags */
   GRPIC_STAGE_E = 3,            /* Sec. 3.2, Eq. 12: d <- d + dx^4 (4 pi/c J - div F) */
-  GRPIC_STAGE_SORT = 4          /* counting sort by cell; drops removed particles */
+  GRPIC_STAGE_SORT = 4,         /* counting sort by cell; drops removed particles */
+  GRPIC_STAGE_B_HALF2 = 5       /* Sec. 3.1, Eq. 10: second B half-step */
 };
 
 typedef void* (*grpic_alloc_fn)(size_t bytes, void* user);
@@ -179,7 +189,7 @@ const char* grpic_status_string(grpic_status s);
  * milliseconds and the number of times the stage ran since the last reset (reset = 1 clears
  * after reading), plus the number of kernels the library has launched in total. */
 grpic_status grpic_set_profiling(grpic_ctx* ctx, int on);
-grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[5], int64_t counts[5], int64_t* kernel_launches,
+grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t counts[6], int64_t* kernel_launches,
                                int reset);
 
 /* Measure the sustained fused-multiply-add rate of this GPU's CUDA cores (not the tensor

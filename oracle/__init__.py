@@ -28,6 +28,7 @@ _lib = None
 NO_GAMMA_IN_J = 1
 NO_GAMMA_TERMS = 2
 FROZEN_FIELDS = 4
+LITERAL_HALF_STEPS = 8
 
 OK, ERR_INVALID, ERR_CFL, ERR_NONFINITE = 0, 1, 4, 5
 
@@ -91,6 +92,7 @@ def lib():
                 "orc_get_particles": (ctypes.c_int, [_V, ctypes.c_int, _D, _D, _U32]),
                 "orc_step": (ctypes.c_int, [_V, ctypes.c_int]),
                 "orc_stage_b_half": (ctypes.c_int, [_V]),
+                "orc_stage_b_half2": (ctypes.c_int, [_V]),
                 "orc_stage_e": (ctypes.c_int, [_V]),
                 "orc_stage_zero_j": (ctypes.c_int, [_V]),
                 "orc_stage_push_deposit": (ctypes.c_int, [_V]),
@@ -318,7 +320,12 @@ class Oracle:
         self._chk(lib().orc_step(self._h, int(nsteps)), "step")
 
     def b_half(self):
+        """First B half-step (b^{n-1/2} -> b^n)."""
         self._chk(lib().orc_stage_b_half(self._h), "b_half")
+
+    def b_half2(self):
+        """Second B half-step (-> b^{n+1/2})."""
+        self._chk(lib().orc_stage_b_half2(self._h), "b_half2")
 
     def e_step(self):
         self._chk(lib().orc_stage_e(self._h), "e_step")

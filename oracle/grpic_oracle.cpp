@@ -49,6 +49,14 @@
  *       A metric evaluated where r = 0 exactly (the disk z = 0, R <= a) is flat.
  *   A16 Particles are pushed with the fields present after the first B half-step;
  *       J is deposited from x_n -> x_{n+1}.
+ *   A21 Time levels of the field tensor in Eqs. 9-12 (unstated): time-centred.  The stored b
+ *       lags d by half a step.  First half-step: b^n = b^{n-1/2} - (dx^4/2) curl e(b^{n-1/2}, d^n);
+ *       second: b^{n+1/2} = b^{n-1/2} - dx^4 curl e(b^n, d^n); E step: the contravariant tensor
+ *       in the divergence is taken at (b^{n+1/2}, d*) with the midpoint predictor
+ *       d* = d^n + (dx^4/2) rhs(b^{n+1/2}, d^n).  In Kerr-Schild coordinates e depends on b and
+ *       h on d (the shift terms), and evaluating them at each half-step's own start value
+ *       (ORC_LITERAL_HALF_STEPS) is a forward-Euler step of a centred advection term, which grows
+ *       without bound near the horizon.
  *
  * Parity status: every function is pinned by a CPU test against closed forms, invariants
  * or brute force.  The literal RK4 coefficients printed in Sec. 3.3 are not implemented:
@@ -82,6 +90,7 @@ enum {
   ORC_NO_GAMMA_IN_J = 1u,   // A13 off: plain Umeda flux (charge conserving in flat space)
   ORC_NO_GAMMA_TERMS = 2u,  // skip the (identically zero) Christoffel terms of Eq. 11
   ORC_FROZEN_FIELDS = 4u,   // test-particle runs: the cycle does not advance the fields
+  ORC_LITERAL_HALF_STEPS = 8u,  // each B half-step and the E step explicit in their own start values
 };
 
 // ---------------------------------------------------------------------------------------
@@ -446,6 +455,7 @@ struct Ctx {
   int n[3]{};
   size_t ncell = 0;
   std::vector<double> F[6];
+  std::vector<double> Fprev[3];  // b^{n-1/2} kept by the first B half-step (A21)
   std::vector<double> J[3];
   std::vector<Species> sp;
   std::vector<double> glx, glw;
@@ -536,9 +546,14 @@ struct Ctx {
     complete_tensor(g, b, d, Fu, Fd);
   }
 
-  // --- Sec. 3.1: magnetic half-step (Eqs. 9-10) -------------------------------------------
-  void b_half() {
+  bool literal() const { return (cfg.flags & ORC_LITERAL_HALF_STEPS) != 0; }
+
+  // --- Sec. 3.1: magnetic half-steps (Eqs. 9-10, time levels A21) --------------------------
+  // which = 0: first half-step (b^{n-1/2} -> b^n), 1: second half-step (-> b^{n+1/2}).
+  void b_half(int which) {
     const double dx4 = cfg.c * cfg.dt;
+    if (!literal() && which == 0)
+      for (int q = 0; q < 3; ++q) Fprev[q] = F[3 + q];
     std::vector<double> e[3];
     for (int c = 0; c < 3; ++c) e[c].assign(ncell, 0.0);
     // covariant F_{c4} at the F^{c4} lattice points
@@ -574,18 +589,20 @@ struct Ctx {
             // (F_{b4}(x + e_a) - F_{b4}(x)) / dx^a + (F_{4a}(x + e_b) - F_{4a}(x)) / dx^b, dx^a = 1
             const double t1 = e[be][idx(pa[0], pa[1], pa[2])] - e[be][idx(i, j, k)];
             const double t2 = -(e[al][idx(pb[0], pb[1], pb[2])] - e[al][idx(i, j, k)]);
-            F[3 + q][idx(i, j, k)] -= (t1 + t2) * dx4 / 2.0;
+            const size_t id = idx(i, j, k);
+            if (literal() || which == 0)
+              F[3 + q][id] -= (t1 + t2) * dx4 / 2.0;
+            else
+              F[3 + q][id] = Fprev[q][id] - (t1 + t2) * dx4;
           }
     }
   }
 
-  // --- Sec. 3.2: electric full step (Eqs. 11-12, readings A6, A8, A9) -------------------
-  void e_step() {
-    const double dx4 = cfg.c * cfg.dt;
-    std::vector<double> h[3];
-    for (int q = 0; q < 3; ++q) h[q].assign(ncell, 0.0);
+  // Contravariant F^{jk} at the face lattice points from the current (b, d).
+  void contra_h(std::vector<double> h[3]) const {
     const int nt = nthreads();
     (void)nt;
+    for (int q = 0; q < 3; ++q) h[q].assign(ncell, 0.0);
     for (int q = 0; q < 3; ++q)
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(nt)
@@ -597,8 +614,15 @@ struct Ctx {
             tensor_at_lattice(3 + q, i, j, k, Fu, Fd);
             h[q][idx(i, j, k)] = Fu[kPair[q][0]][kPair[q][1]];
           }
-    std::vector<double> newd[3];
-    for (int al = 0; al < 3; ++al) newd[al] = F[al];
+  }
+
+  // out^a = F^{a4} + coef (4 pi/c J^a - Gamma terms - d_nu F^{a nu}) at the advanced lattice
+  // points (Eq. 12 with readings A6, A8, A9); elsewhere out = F^{a4}.  Gamma terms use the
+  // tensor of the current state.
+  void e_update(const std::vector<double> h[3], double coef, std::vector<double> out[3]) {
+    const int nt = nthreads();
+    (void)nt;
+    for (int al = 0; al < 3; ++al) out[al] = F[al];
     double gmax = 0.0, gscale = 0.0;
     for (int al = 0; al < 3; ++al)
 #ifdef _OPENMP
@@ -637,11 +661,31 @@ struct Ctx {
               gscale = std::max(gscale, scale);
             }
             const size_t id = idx(i, j, k);
-            newd[al][id] = F[al][id] + (4.0 * kPi / cfg.c * J[al][id] - gterm - div) * dx4;
+            out[al][id] = F[al][id] + (4.0 * kPi / cfg.c * J[al][id] - gterm - div) * coef;
           }
-    for (int al = 0; al < 3; ++al) F[al].swap(newd[al]);
     gterm_max = std::max(gterm_max, gmax);
     gterm_scale = std::max(gterm_scale, gscale);
+  }
+
+  // --- Sec. 3.2: electric full step (Eqs. 11-12, readings A6, A8, A9, A21) ------------------
+  void e_step() {
+    const double dx4 = cfg.c * cfg.dt;
+    std::vector<double> h[3], newd[3];
+    contra_h(h);
+    if (!literal()) {
+      // midpoint predictor d* = d + (dx4/2) rhs, then the tensor at (b, d*)
+      std::vector<double> dstar[3];
+      e_update(h, dx4 / 2.0, dstar);
+      std::vector<double> dn[3];
+      for (int al = 0; al < 3; ++al) {
+        dn[al] = F[al];
+        F[al] = dstar[al];
+      }
+      contra_h(h);
+      for (int al = 0; al < 3; ++al) F[al].swap(dn[al]);
+    }
+    e_update(h, dx4, newd);
+    for (int al = 0; al < 3; ++al) F[al].swap(newd[al]);
   }
 
   // CIC gather of component c at grid position x (Sec. 3.3; weights trilinear, reading A5).
@@ -906,12 +950,12 @@ struct Ctx {
   // Sec. 2.2 cycle: B half-step, push + deposit, B half-step, E step.
   int step() {
     const bool fields = !(cfg.flags & ORC_FROZEN_FIELDS);
-    if (fields) b_half();
+    if (fields) b_half(0);
     zero_j();
     const int e = push_deposit_all();
     if (e != ORC_OK) return e;
     if (fields) {
-      b_half();
+      b_half(1);
       e_step();
     }
     ++stat_steps;
@@ -1326,7 +1370,11 @@ int orc_step(void* p, int nsteps) {
 }
 
 int orc_stage_b_half(void* p) {
-  static_cast<Ctx*>(p)->b_half();
+  static_cast<Ctx*>(p)->b_half(0);
+  return ORC_OK;
+}
+int orc_stage_b_half2(void* p) {
+  static_cast<Ctx*>(p)->b_half(1);
   return ORC_OK;
 }
 int orc_stage_e(void* p) {

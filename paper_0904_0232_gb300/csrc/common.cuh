@@ -45,6 +45,8 @@ struct Fields {
   T* d[3];
   T* b[3];
   T* s[3];       // scratch: covariant e (B step) or contravariant h (E step)
+  T* bp[3];      // b at the previous half level (time-centred B update)
+  T* dp[3];      // midpoint predictor of d (time-centred E update)
   double* J[3];
   const T* mc;
   const uint8_t* mask;
@@ -67,10 +69,15 @@ __host__ __device__ inline long long cell_index(const Grid& g, int i, int j, int
 // ---- launchers (defined in fields.cu, push.cu, sort.cu) --------------------------------
 template <typename T>
 void launch_metric_cache(const Grid& g, T* mc, uint8_t* mask, cudaStream_t st);
+// B half-steps.  which = 0: first half (b^{n-1/2} -> b^n); which = 1: second half
+// (b^n -> b^{n+1/2}).  literal = true: each half is b -= (dx4/2) curl e(b, d) in place;
+// literal = false (time-centred): the first half saves b^{n-1/2}, the second computes
+// b^{n+1/2} = b^{n-1/2} - dx4 curl e(b^n, d^n).
 template <typename T>
-void launch_b_half(const Grid& g, const Fields<T>& F, cudaStream_t st);
+void launch_b_half(const Grid& g, const Fields<T>& F, int which, bool literal, cudaStream_t st);
+// E step d^n -> d^{n+1}; time-centred unless literal (midpoint predictor for d in h(b, d)).
 template <typename T>
-void launch_e_step(const Grid& g, const Fields<T>& F, cudaStream_t st);
+void launch_e_step(const Grid& g, const Fields<T>& F, bool literal, cudaStream_t st);
 template <typename T>
 void launch_uniform_field(const Grid& g, const Fields<T>& F, const double E[3], const double B[3], cudaStream_t st);
 template <typename T>

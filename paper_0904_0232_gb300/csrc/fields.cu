@@ -144,17 +144,16 @@ __global__ void k_cov_e(const Grid g, const Fields<T> F, const Box bx) {
   F.s[2][c] = e[2];
 }
 
+// mode 0: b -= coef curl e (in place); 1: save b to bp, then b -= coef curl e;
+// 2: b = bp - coef curl e.  Only advanced (masked) locations are touched.
 template <typename T>
-__global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, T dx4) {
+__global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, T coef, int mode) {
   int i, j, k;
   if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
-  const T* e0 = F.s[0];
-  const T* e1 = F.s[1];
-  const T* e2 = F.s[2];
-  const T* ev[3] = {e0, e1, e2};
+  const T* ev[3] = {F.s[0], F.s[1], F.s[2]};
   // (alpha, beta) of F_{alpha beta}: b_x = F_yz, b_y = F_zx, b_z = F_xy
   const int al[3] = {1, 2, 0}, be[3] = {2, 0, 1};
 #pragma unroll
@@ -164,7 +163,9 @@ __global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, T dx4)
     const T* ea = ev[al[q]];
     const T t1 = eb[c + st[al[q]]] - eb[c];
     const T t2 = -(ea[c + st[be[q]]] - ea[c]);
-    F.b[q][c] -= (t1 + t2) * dx4 / T(2);
+    const T old = (mode == 2) ? F.bp[q][c] : F.b[q][c];
+    if (mode == 1) F.bp[q][c] = old;
+    F.b[q][c] = old - (t1 + t2) * coef;
   }
 }
 
@@ -190,16 +191,23 @@ __global__ void k_contra_h(const Grid g, const Fields<T> F, const Box bx) {
   F.s[2][c] = h[2];
 }
 
+// d_out = d + coef (4 pi/c J - div h) at advanced locations.  full = true writes every cell
+// of the grid (d copied where not advanced) so d_out can be read as a whole field.
 template <typename T>
-__global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, T dx4, double four_pi_over_c) {
+__global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, T coef, double four_pi_over_c,
+                           T* out0, T* out1, T* out2, bool full) {
   int i, j, k;
   if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
+  T* out[3] = {out0, out1, out2};
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
-    if (!(bits & (1u << al))) continue;
+    if (!(bits & (1u << al))) {
+      if (full) out[al][c] = F.d[al][c];
+      continue;
+    }
     T div = T(0);
 #pragma unroll
     for (int nu = 0; nu < 3; ++nu) {
@@ -211,7 +219,7 @@ __global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, T dx4,
       div += sgn * (hq[c] - hq[c - st[nu]]);
     }
     const T src = (T)(four_pi_over_c * F.J[al][c]);
-    F.d[al][c] = F.d[al][c] + (src - div) * dx4;
+    out[al][c] = F.d[al][c] + (src - div) * coef;
   }
 }
 
@@ -264,21 +272,38 @@ void launch_metric_cache(const Grid& g, T* mc, uint8_t* mask, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_b_half(const Grid& g, const Fields<T>& F, cudaStream_t st) {
+void launch_b_half(const Grid& g, const Fields<T>& F, int which, bool literal, cudaStream_t st) {
   const Box conv = make_box(g, 1), upd = make_box(g, 2);
   const long long nconv = (long long)conv.nxb * conv.nyb * conv.nzb;
   const long long nupd = (long long)upd.nxb * upd.nyb * upd.nzb;
+  const T dx4 = (T)(g.c * g.dt);
   k_cov_e<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv);
-  k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, (T)(g.c * g.dt));
+  if (literal)
+    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4 / T(2), 0);
+  else if (which == 0)
+    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4 / T(2), 1);
+  else
+    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4, 2);
 }
 
 template <typename T>
-void launch_e_step(const Grid& g, const Fields<T>& F, cudaStream_t st) {
-  const Box conv = make_box(g, 1), upd = make_box(g, 2);
+void launch_e_step(const Grid& g, const Fields<T>& F, bool literal, cudaStream_t st) {
+  const Box conv = make_box(g, 1), upd = make_box(g, 2), all = make_box(g, 0);
   const long long nconv = (long long)conv.nxb * conv.nyb * conv.nzb;
   const long long nupd = (long long)upd.nxb * upd.nyb * upd.nzb;
+  const long long nall = (long long)all.nxb * all.nyb * all.nzb;
+  const T dx4 = (T)(g.c * g.dt);
+  const double fpc = 4.0 * M_PI / g.c;
   k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv);
-  k_d_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, (T)(g.c * g.dt), 4.0 * M_PI / g.c);
+  if (!literal) {
+    // midpoint predictor d* = d + (dx4/2) rhs(d), then h from (b, d*)
+    k_d_update<T><<<blocks_for(nall, 256), 256, 0, st>>>(g, F, all, dx4 / T(2), fpc, F.dp[0], F.dp[1], F.dp[2],
+                                                          true);
+    Fields<T> Fp = F;
+    for (int q = 0; q < 3; ++q) Fp.d[q] = F.dp[q];
+    k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, Fp, conv);
+  }
+  k_d_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4, fpc, F.d[0], F.d[1], F.d[2], false);
 }
 
 template <typename T>
@@ -297,8 +322,8 @@ void launch_convert_out(double* dst, const T* src, long long n, cudaStream_t st)
 
 #define GRPIC_INST_FIELDS(T)                                                                             \
   template void launch_metric_cache<T>(const Grid&, T*, uint8_t*, cudaStream_t);                        \
-  template void launch_b_half<T>(const Grid&, const Fields<T>&, cudaStream_t);                          \
-  template void launch_e_step<T>(const Grid&, const Fields<T>&, cudaStream_t);                          \
+  template void launch_b_half<T>(const Grid&, const Fields<T>&, int, bool, cudaStream_t);              \
+  template void launch_e_step<T>(const Grid&, const Fields<T>&, bool, cudaStream_t);                    \
   template void launch_uniform_field<T>(const Grid&, const Fields<T>&, const double*, const double*,     \
                                         cudaStream_t);                                                   \
   template void launch_convert_in<T>(T*, const double*, long long, cudaStream_t);                       \

@@ -42,7 +42,7 @@ struct grpic_ctx {
   bool mixed = false;
   size_t tsize = 8;
   std::string err;
-  void* fields = nullptr;  // 9 planes of T: d[3], b[3], scratch[3]
+  void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T
   uint8_t* mask = nullptr;
@@ -63,8 +63,8 @@ struct grpic_ctx {
     int stage;
   };
   std::vector<Pending> pending;
-  double prof_ms[5] = {0, 0, 0, 0, 0};
-  long long prof_cnt[5] = {0, 0, 0, 0, 0};
+  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long prof_cnt[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -109,6 +109,8 @@ Fields<T> fields_view(grpic_ctx* c) {
     F.d[q] = base + (size_t)q * c->g.ncell;
     F.b[q] = base + (size_t)(3 + q) * c->g.ncell;
     F.s[q] = base + (size_t)(6 + q) * c->g.ncell;
+    F.bp[q] = base + (size_t)(9 + q) * c->g.ncell;
+    F.dp[q] = base + (size_t)(12 + q) * c->g.ncell;
     F.J[q] = c->J + (size_t)q * c->g.ncell;
   }
   F.mc = static_cast<const T*>(c->mc);
@@ -141,12 +143,15 @@ void refresh_count(SpeciesStore& S) {
   }
 }
 
+bool literal_fields(const grpic_ctx* c) { return (c->cfg.flags & GRPIC_LITERAL_HALF_STEPS) != 0; }
+
 template <typename T>
 void enqueue_stage(grpic_ctx* c, int stage) {
   Fields<T> F = fields_view<T>(c);
   switch (stage) {
     case GRPIC_STAGE_B_HALF:
-      launch_b_half<T>(c->g, F, c->stream);
+    case GRPIC_STAGE_B_HALF2:
+      launch_b_half<T>(c->g, F, stage == GRPIC_STAGE_B_HALF ? 0 : 1, literal_fields(c), c->stream);
       c->launches += 2;
       break;
     case GRPIC_STAGE_ZERO_J:
@@ -164,8 +169,8 @@ void enqueue_stage(grpic_ctx* c, int stage) {
       c->pushes += 1;
       break;
     case GRPIC_STAGE_E:
-      launch_e_step<T>(c->g, F, c->stream);
-      c->launches += 2;
+      launch_e_step<T>(c->g, F, literal_fields(c), c->stream);
+      c->launches += literal_fields(c) ? 2 : 4;
       break;
     case GRPIC_STAGE_SORT:
       for (int s = 0; s < kMaxSpecies; ++s) {
@@ -233,7 +238,7 @@ void enqueue_step(grpic_ctx* c) {
   enqueue_stage_any(c, GRPIC_STAGE_B_HALF);
   enqueue_stage_any(c, GRPIC_STAGE_ZERO_J);
   enqueue_stage_any(c, GRPIC_STAGE_PUSH_DEPOSIT);
-  enqueue_stage_any(c, GRPIC_STAGE_B_HALF);
+  enqueue_stage_any(c, GRPIC_STAGE_B_HALF2);
   enqueue_stage_any(c, GRPIC_STAGE_E);
   c->steps += 1;
   if (++c->since_sort >= std::max(1, c->cfg.sort_interval)) {
@@ -350,7 +355,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
 
-  c->fields = dev_alloc(c, 9 * (size_t)ncell * c->tsize);
+  c->fields = dev_alloc(c, 15 * (size_t)ncell * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));
   c->mc = dev_alloc(c, 24 * (size_t)ncell * c->tsize);
   c->mask = static_cast<uint8_t*>(dev_alloc(c, (size_t)ncell));
@@ -372,7 +377,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
     grpic_destroy(c);
     return GRPIC_ERR_OOM;
   }
-  cudaMemsetAsync(c->fields, 0, 9 * (size_t)ncell * c->tsize, c->stream);
+  cudaMemsetAsync(c->fields, 0, 15 * (size_t)ncell * c->tsize, c->stream);
   cudaMemsetAsync(c->J, 0, 3 * (size_t)ncell * sizeof(double), c->stream);
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
   for (int s = 0; s < kMaxSpecies; ++s) cudaMemsetAsync(c->sp[s].n_dev, 0, sizeof(int), c->stream);
@@ -565,7 +570,7 @@ grpic_status grpic_step(grpic_ctx* c, int nsteps) {
 }
 
 grpic_status grpic_stage(grpic_ctx* c, int stage) {
-  if (!c || stage < GRPIC_STAGE_B_HALF || stage > GRPIC_STAGE_SORT) return GRPIC_ERR_INVALID;
+  if (!c || stage < GRPIC_STAGE_B_HALF || stage > GRPIC_STAGE_B_HALF2) return GRPIC_ERR_INVALID;
   enqueue_stage_any(c, stage);
   grpic_status s = cuda_check(c, cudaGetLastError(), "stage launch");
   if (s != GRPIC_OK) return s;
@@ -691,19 +696,19 @@ grpic_status grpic_set_profiling(grpic_ctx* c, int on) {
   return GRPIC_OK;
 }
 
-grpic_status grpic_get_profile(grpic_ctx* c, double times_ms[5], int64_t counts[5], int64_t* kernel_launches,
+grpic_status grpic_get_profile(grpic_ctx* c, double times_ms[6], int64_t counts[6], int64_t* kernel_launches,
                                int reset) {
   if (!c) return GRPIC_ERR_INVALID;
   grpic_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
   if (s != GRPIC_OK) return s;
   collect_profile(c);
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < 6; ++q) {
     if (times_ms) times_ms[q] = c->prof_ms[q];
     if (counts) counts[q] = c->prof_cnt[q];
   }
   if (kernel_launches) *kernel_launches = c->launches;
   if (reset) {
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
       c->prof_ms[q] = 0.0;
       c->prof_cnt[q] = 0;
     }

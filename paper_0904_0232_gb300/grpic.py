@@ -21,9 +21,10 @@ STATUS_NAMES = {0: "GRPIC_OK", 1: "GRPIC_ERR_INVALID", 2: "GRPIC_ERR_OOM", 3: "G
                 5: "GRPIC_ERR_NONFINITE", 6: "GRPIC_ERR_TIMEOUT", 7: "GRPIC_ERR_AGAIN", 8: "GRPIC_ERR_CAPACITY"}
 GRPIC_FP64, GRPIC_FP32_MIXED = 0, 1
 GRPIC_NO_GAMMA_IN_J = 1
+GRPIC_LITERAL_HALF_STEPS = 2
 GRPIC_MEM_HOST, GRPIC_MEM_DEVICE = 0, 1
 GRPIC_U_FULL, GRPIC_U_COV_SPATIAL, GRPIC_U_CONTRA_SPATIAL, GRPIC_LOAD_DEVICE = 0, 1, 2, 16
-GRPIC_STAGE_B_HALF, GRPIC_STAGE_ZERO_J, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_E, GRPIC_STAGE_SORT = range(5)
+GRPIC_STAGE_B_HALF, GRPIC_STAGE_ZERO_J, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_E, GRPIC_STAGE_SORT, GRPIC_STAGE_B_HALF2 = range(6)
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -247,16 +248,16 @@ def grpic_set_profiling(ctx, on):
     _check(ctx, load_library().grpic_set_profiling(ctx, int(bool(on))), "grpic_set_profiling")
 
 
-STAGE_NAMES = ("b_half", "zero_j", "push_deposit", "e_step", "sort")
+STAGE_NAMES = ("b_half", "zero_j", "push_deposit", "e_step", "sort", "b_half2")
 
 
 def grpic_get_profile(ctx, reset=False):
-    ms = (ctypes.c_double * 5)()
-    cnt = (ctypes.c_int64 * 5)()
+    ms = (ctypes.c_double * 6)()
+    cnt = (ctypes.c_int64 * 6)()
     nl = ctypes.c_int64(0)
     _check(ctx, load_library().grpic_get_profile(ctx, ms, cnt, ctypes.byref(nl), int(bool(reset))),
            "grpic_get_profile")
-    return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(5)}, nl.value
+    return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(6)}, nl.value
 
 
 def grpic_probe_fma_peak(precision):

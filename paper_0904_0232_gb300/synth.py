@@ -11,8 +11,10 @@ Recipe (stands in for the disk/corona set-ups of Sec. 6, which have no released 
   * covariant spatial momenta u_i / c isotropic with |u| drawn from the Maxwell-Juettner
     distribution f(u) ~ u^2 exp(-(sqrt(1+u^2) - 1)/theta), theta = (u_th / c)^2, by inverse
     transform of a tabulated CDF;
-  * macro-particle charge chosen so that the plasma frequency at the loaded density gives
-    omega_p dt = 0.25 (Sec. 5: omega_p dt < 2 with margin);
+  * macro-particle charge chosen so that the plasma frequency at the loaded density gives a
+    stated omega_p dt (Sec. 5 requires omega_p dt < 2); the Kerr electron-ion workload uses
+    0.025, low enough that the charge-separation field near the hole stays bounded for 500
+    steps at dt = 0.4;
   * the RNG is numpy's counter-based Philox keyed by (seed, species).
 """
 from __future__ import annotations
@@ -90,14 +92,15 @@ def charge_for(dt, ppc, q_over_m_list, wp_dt=0.25):
     return (wp_dt / dt) ** 2 / (4.0 * np.pi * ppc * sum(abs(q) for q in q_over_m_list))
 
 
-def plasma(name, n, m, a, c, dt, B0, nsteps, ppc, qms, u_th, seed, r_min=0.0, max_particles=None, cells=None):
+def plasma(name, n, m, a, c, dt, B0, nsteps, ppc, qms, u_th, seed, r_min=0.0, max_particles=None, cells=None,
+           wp_dt=0.25):
     rng = _rng(seed, 0)
     x = uniform_positions(rng, n, n, n, ppc, r_min=r_min, cells=cells)
     if max_particles is not None and x.shape[1] > max_particles:
         x = x[:, :max_particles]
     npart = x.shape[1]
     x4 = np.vstack([x, np.zeros((1, npart))])
-    q = charge_for(dt, ppc, qms)
+    q = charge_for(dt, ppc, qms, wp_dt)
     theta = (u_th / c) ** 2
     species = []
     for s, qm in enumerate(qms):
@@ -114,11 +117,11 @@ def schwarzschild_pairs_32(seed=1, max_particles=None):
                   r_min=6.0, max_particles=max_particles)
 
 
-def kerr_ion_electron_128(seed=2, max_particles=None, n=128, cells=None):
+def kerr_ion_electron_128(seed=2, max_particles=None, n=128, cells=None, wp_dt=0.025):
     """a = 0.9 m, m = 4 cells, 128^3, electrons (q/m = -1) and ions (q/m = +1/20), 8 per cell
-    per species, u_th = 0.05 c, uniform B_z = 0.1, dt = 0.4, 200 steps."""
+    per species, u_th = 0.05 c, uniform B_z = 0.1, dt = 0.4, 200 steps, omega_p dt = wp_dt."""
     return plasma(f"kerr_ion_electron_{n}", n, 4.0, 3.6, 1.0, 0.4, 0.1, 200, 8, (-1.0, 1.0 / 20.0), 0.05, seed,
-                  max_particles=max_particles, cells=cells)
+                  max_particles=max_particles, cells=cells, wp_dt=wp_dt)
 
 
 def random_fields(shape, seed, scale=0.05):

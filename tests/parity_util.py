@@ -59,7 +59,7 @@ def particle_errors(sim, ref, species, x4_scale=None):
     return ex, e4, eu
 
 
-def face_ambiguity_mask(ref, shape, nspecies, delta=2e-5):
+def face_ambiguity_mask(ref, shape, nspecies, delta=1e-5):
     """Grid nodes whose J depends on a floating-point-decided cell index: the zig-zag split of
     a move changes discontinuously when an endpoint crosses a cell face, so a particle whose
     start or end lies within `delta` of a face (per the oracle) can be split differently by an
@@ -75,8 +75,9 @@ def face_ambiguity_mask(ref, shape, nspecies, delta=2e-5):
             fr = x - np.floor(x)
             near |= (np.minimum(fr, 1.0 - fr) < delta).any(0)
         for p in np.nonzero(near)[0]:
+            # cells either side of the face, and the +1 transverse node of each
             lo = np.floor(np.minimum(x0[:, p], x1[:, p])).astype(int) - 1
-            hi = np.floor(np.maximum(x0[:, p], x1[:, p])).astype(int) + 3
+            hi = np.floor(np.maximum(x0[:, p], x1[:, p])).astype(int) + 2
             lo = np.maximum(lo, 0)
             mask[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
     return mask

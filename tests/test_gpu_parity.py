@@ -7,9 +7,9 @@ import oracle as O
 from parity_util import (TOL, dilate, face_ambiguity_mask, gpu_from_oracle, oracle_start, particle_errors, rel_l2,
                          rel_l2_masked, small_kerr)
 from paper_0904_0232_gb300 import synth
-from paper_0904_0232_gb300.grpic import (GRPIC_STAGE_B_HALF, GRPIC_STAGE_E, GRPIC_STAGE_PUSH_DEPOSIT,
-                                         GRPIC_STAGE_ZERO_J, GRPIC_U_CONTRA_SPATIAL, GRPIC_U_COV_SPATIAL,
-                                         GrpicError, Simulation)
+from paper_0904_0232_gb300.grpic import (GRPIC_LITERAL_HALF_STEPS, GRPIC_STAGE_B_HALF, GRPIC_STAGE_B_HALF2,
+                                         GRPIC_STAGE_E, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_ZERO_J,
+                                         GRPIC_U_CONTRA_SPATIAL, GRPIC_U_COV_SPATIAL, GrpicError, Simulation)
 
 pytestmark = pytest.mark.gpu
 PRECISIONS = ["fp64", "fp32_mixed"]
@@ -35,7 +35,7 @@ def check_j(J, Jr, ref, nspecies, prec, factor=1.0):
         assert rel_l2(J, Jr) <= tol, rel_l2(J, Jr)
         return np.zeros(J.shape[1:], dtype=bool)
     mask = face_ambiguity_mask(ref, J.shape[1:], nspecies)
-    assert mask.mean() < 0.05, mask.mean()
+    assert mask.mean() < 0.25, mask.mean()  # at 16 particles per cell a few % of particles are near a face
     assert rel_l2_masked(J, Jr, mask) <= tol, rel_l2_masked(J, Jr, mask)
     for K in range(3):
         assert abs(J[K].sum() - Jr[K].sum()) <= tol * max(np.abs(Jr[K]).sum(), 1e-300)
@@ -73,6 +73,46 @@ def test_b_half_step(prec, dims):
     assert rel_l2(b1, br) <= TOL[prec]["fields"]
     assert rel_l2(b1 - b, br - b) <= (1e-11 if prec == "fp64" else 2e-4)  # the update itself
     assert np.array_equal(d1, dr) if prec == "fp64" else rel_l2(d1, dr) <= 1e-7
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("literal", [False, True])
+def test_both_b_half_steps(prec, literal):
+    """First and second B half-steps, time-centred (default) and literal explicit."""
+    nx, ny, nz = 22, 25, 28
+    ref = O.Oracle(nx, ny, nz, 2.0, 1.6, 1.0, 0.4, threads=0, flags=O.LITERAL_HALF_STEPS if literal else 0)
+    d, b = _rand_fields((nz, ny, nx), 13)
+    ref.set_fields(d, b)
+    sim = Simulation(nx, ny, nz, 2.0, 1.6, 1.0, 0.4, precision=prec, flags=GRPIC_LITERAL_HALF_STEPS if literal else 0)
+    sim.set_fields(d, b)
+    ref.b_half()
+    ref.b_half2()
+    sim.stage(GRPIC_STAGE_B_HALF)
+    sim.stage(GRPIC_STAGE_B_HALF2)
+    _, b1, _ = sim.get_fields()
+    _, br, _ = ref.get_fields()
+    assert rel_l2(b1, br) <= TOL[prec]["fields"]
+    assert rel_l2(b1 - b, br - b) <= (1e-11 if prec == "fp64" else 2e-4)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("literal", [False, True])
+def test_e_step_variants(prec, literal):
+    nx, ny, nz = 21, 24, 27
+    ref = O.Oracle(nx, ny, nz, 2.0, 1.6, 1.0, 0.4, threads=0, flags=O.LITERAL_HALF_STEPS if literal else 0)
+    d, b = _rand_fields((nz, ny, nx), 14)
+    J = np.random.default_rng(15).standard_normal((3, nz, ny, nx)) * 1e-3
+    ref.set_fields(d, b)
+    ref.set_j(J)
+    sim = Simulation(nx, ny, nz, 2.0, 1.6, 1.0, 0.4, precision=prec, flags=GRPIC_LITERAL_HALF_STEPS if literal else 0)
+    sim.set_fields(d, b)
+    sim.set_j(J)
+    ref.e_step()
+    sim.stage(GRPIC_STAGE_E)
+    d1, _, _ = sim.get_fields()
+    dr, _, _ = ref.get_fields()
+    assert rel_l2(d1, dr) <= TOL[prec]["fields"]
+    assert rel_l2(d1 - d, dr - d) <= (1e-11 if prec == "fp64" else 2e-4)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -279,3 +319,22 @@ def test_no_gamma_flag(prec):
     sim.stage(GRPIC_STAGE_ZERO_J)
     sim.stage(GRPIC_STAGE_PUSH_DEPOSIT)
     check_j(sim.get_fields()[2], ref.get_fields()[2], ref, 2, prec)
+
+
+def test_schwarzschild_pairs_full_run():
+    """The small workload end to end in FP64: a = 0, m = 2, 32^3, e-/e+ pairs outside R = 3m,
+    20 whole steps; particles, J and fields against the oracle after steps 1, 5 and 20."""
+    wl = synth.schwarzschild_pairs_32(seed=1)
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, "fp64")
+    done = 0
+    for upto, tol in ((1, 1e-12), (5, 1e-11), (20, 1e-9)):
+        ref.step(upto - done)
+        sim.step(upto - done)
+        done = upto
+        for s in range(2):
+            ex, e4, eu = particle_errors(sim, ref, s)
+            assert max(ex, eu) <= tol, (upto, s, ex, eu)
+        d, b, J = sim.get_fields()
+        dr, br, Jr = ref.get_fields()
+        assert rel_l2(J, Jr) <= tol and rel_l2(b, br) <= tol and rel_l2(d, dr) <= tol

@@ -83,7 +83,7 @@ def test_flat_space_is_yee_plane_wave():
     o.set_fields(d, b)
     for n in range(1, nsteps + 1):
         o.b_half()
-        o.b_half()
+        o.b_half2()
         o.e_step()
         dn, bn, _ = o.get_fields()
         de, be = _yee_fields(N, kx, ky, D, n, s)
@@ -123,7 +123,7 @@ def _wald_one_step_drift(m, N):
     o.init_wald(0.1)
     d0, b0, _ = o.get_fields()
     o.b_half()
-    o.b_half()
+    o.b_half2()
     o.e_step()
     d1, b1, _ = o.get_fields()
     Xc = (N - 1) / 2
@@ -206,3 +206,4 @@ def test_gauss_law_flat_closed_form():
         assert np.abs((G1 - G)[sl] + 4 * np.pi * pred[sl]).max() < 1e-14
         G = G1
     assert o.num_particles(0) == n and o.num_particles(1) == n
+
