@@ -43,8 +43,9 @@ def gpu_from_oracle(ref, wl, precision, quad_order=2, flags=0, sort_interval=1, 
     return sim
 
 
-def particle_errors(sim, ref, species, x4_scale=None):
-    """Max relative errors (x spatial, x^4, u) over particles matched by id; survivors must match."""
+def particle_errors(sim, ref, species, x4_scale=None, mask=None):
+    """Max relative errors (x spatial, x^4, u) over particles matched by id; survivors must match.
+    mask: optional (nz, ny, nx) boolean grid; particles whose cell is masked are not compared."""
     xr, ur, ir = ref.get_particles(species)
     x, u, ids = sim.get_particles(species)
     o = np.argsort(ids, kind="stable")
@@ -52,6 +53,12 @@ def particle_errors(sim, ref, species, x4_scale=None):
     if ir.size == 0:
         return 0.0, 0.0, 0.0
     x, u = x[:, o], u[:, o]
+    if mask is not None:
+        c = np.floor(xr[:3]).astype(int)
+        keep = ~mask[c[2], c[1], c[0]]
+        x, u, xr, ur = x[:, keep], u[:, keep], xr[:, keep], ur[:, keep]
+        if xr.shape[1] == 0:
+            return 0.0, 0.0, 0.0
     ex = (np.abs(x[:3] - xr[:3]).max(0) / np.abs(xr[:3]).max(0)).max()
     s4 = np.maximum(np.abs(xr[3]), x4_scale if x4_scale is not None else 1.0)
     e4 = (np.abs(x[3] - xr[3]) / s4).max()

@@ -196,8 +196,9 @@ def test_full_steps(prec, dims):
         ref.step(1)
         sim.step(1)
         for s in range(2):
-            ex, e4, eu = particle_errors(sim, ref, s)
-            # errors compound over steps: allow the per-step bound times 4^step
+            # errors compound over steps: allow the per-step bound times 4^step; particles in
+            # cells reached by an ambiguous split's field difference are compared through J only
+            ex, e4, eu = particle_errors(sim, ref, s, mask=dilate(seen, 1))
             assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
         d, b, J = sim.get_fields()
         dr, br, Jr = ref.get_fields()
@@ -278,7 +279,7 @@ def test_near_horizon_full_density(prec):
         ref.step(1)
         sim.step(1)
         for s in range(2):
-            ex, e4, eu = particle_errors(sim, ref, s)
+            ex, e4, eu = particle_errors(sim, ref, s, mask=dilate(seen, 1))
             assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
         d, b, J = sim.get_fields()
         dr, br, Jr = ref.get_fields()
