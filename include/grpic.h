@@ -198,6 +198,29 @@ grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t count
  * roofline denominator of the ALU-bound push. */
 grpic_status grpic_probe_fma_peak(int precision, double* flops_per_s);
 
+/* Sort a particle set by cell without allocating any device memory.  The paper has no
+ * counterpart: this is the library's counting sort offered to callers that cannot allocate at
+ * the point of the call -- code running under a fixed, pre-reserved device-memory budget,
+ * code called from inside an allocator or memory-pool callback (allocating would re-enter the
+ * allocator), or loops that must never block in cudaMalloc/cudaFree.
+ * x4, u4, ids: n particles on the current device, planar as elsewhere in this header (plane q
+ * of x4 starts at x4 + q*n).  Outputs (caller-owned device memory of the same sizes, same plane
+ * stride n): the particles whose position lies in [0, n_axis - 1) on every axis, ordered by
+ * cell index (k*ny + j)*nx + i of floor(x), order within a cell unspecified; *n_out (a device
+ * int64) receives how many were kept.  All work is ordered on `stream` (a cudaStream_t, NULL =
+ * default stream); the call does not synchronise.
+ * Scratch: one file-scope device array sized for grids of at most 262,144 cells (64^3), about
+ * 2.1 MB, held by every GPU that loads this library until the process exits.  Larger grids
+ * (nx*ny*nz > 262144) or n >= 2^31 return GRPIC_ERR_CAPACITY without touching the GPU.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares
+ * the array and it keeps the last call's contents (each call clears the counts it uses), so
+ * calls whose GPU work overlaps -- on different streams or from different host threads -- race.
+ * The call makes no cudaMalloc/cudaFree or other allocating call. */
+grpic_status grpic_sort_particles_static(int nx, int ny, int nz, int64_t n, const double* x4, const double* u4,
+                                         const uint32_t* ids, double* x4_out, double* u4_out, uint32_t* ids_out,
+                                         int64_t* n_out, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batched engine: many independent contexts advanced together.  Each stage of the timestep
  * is one persistent launch over all (instance, work item) pairs read from a device table;

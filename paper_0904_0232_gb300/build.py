@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrpic.so")
-SOURCES = ["grpic.cu", "fields.cu", "push.cu", "sort.cu", "peak.cu"]
+SOURCES = ["grpic.cu", "fields.cu", "push.cu", "sort.cu", "peak.cu", "static_sort.cu"]
 HEADERS = ["common.cuh", "metric.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

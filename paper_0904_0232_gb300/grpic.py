@@ -71,6 +71,10 @@ EXPORTS = {
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int]),
     "grpic_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "grpic_sort_particles_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]),
     "grpic_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -264,6 +268,23 @@ def grpic_probe_fma_peak(precision):
     v = ctypes.c_double(0.0)
     _check(None, load_library().grpic_probe_fma_peak(int(precision), ctypes.byref(v)), "grpic_probe_fma_peak")
     return v.value
+
+
+def grpic_sort_particles_static(nx, ny, nz, x4, u4, ids, x4_out, u4_out, ids_out, n_out, stream=None):
+    """Cell sort that allocates nothing (see include/grpic.h).  All array arguments are CUDA
+    tensors: x4/u4 (4, n) float64, ids (n,) int32 or uint32, outputs of the same shapes, n_out a
+    one-element int64 tensor.  Runs on `stream` (default: PyTorch's current stream)."""
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    n = int(x4.shape[1])
+    for t in (x4, u4, ids, x4_out, u4_out, ids_out, n_out):
+        assert _is_cuda_tensor(t) and t.is_contiguous()
+    code = load_library().grpic_sort_particles_static(
+        int(nx), int(ny), int(nz), n, x4.data_ptr(), u4.data_ptr(), ids.data_ptr(), x4_out.data_ptr(),
+        u4_out.data_ptr(), ids_out.data_ptr(), n_out.data_ptr(), ctypes.c_void_p(stream))
+    if code != GRPIC_OK:
+        raise GrpicError(code, "grpic_sort_particles_static",
+                         "grid larger than 64^3 cells or n >= 2^31" if code == 8 else "")
 
 
 def grpic_batch_create(ctxs, stream=None):
