@@ -104,6 +104,9 @@ typedef struct {
   unsigned flags;        /* GRPIC_NO_GAMMA_IN_J */
   int sort_interval;     /* counting sort every k steps (<= 0 -> 1) */
   int64_t max_particles; /* capacity per species (0 -> set by the first load) */
+  double fp64_radius;    /* FP32_MIXED: where the FP32 estimate of r is below fp64_radius * m, the quartic,
+                            the metric and the Christoffel contraction are evaluated in FP64 (0 -> 4;
+                            negative -> never) */
   grpic_alloc_fn alloc;  /* device allocator (NULL -> cudaMalloc); e.g. a PyTorch caching allocator */
   grpic_free_fn free_fn; /* matching free */
   void* alloc_user;      /* passed to alloc / free_fn */

@@ -16,6 +16,10 @@ LIB = os.path.join(HERE, "libgrpic.so")
 SOURCES = ["grpic.cu", "fields.cu", "push.cu", "sort.cu", "peak.cu", "static_sort.cu"]
 HEADERS = ["common.cuh", "metric.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 path of the push tolerates the hardware's approximate single-precision divide and
+# square root (1-2 ulp): measured particle-state errors stay ~1e-7 against the FP64 oracle,
+# 20x inside the 2e-6 bound.  FP64 arithmetic is unaffected by these flags.
+PER_FILE_FLAGS = {"push.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def nvcc() -> str:
@@ -39,7 +43,7 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "grpic.h")]
+    headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "grpic.h"), __file__]
     cc = nvcc()
     jobs = []
     objs = []
@@ -48,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([cc] + _flags(extra_flags) + ["-c", s, "-o", o])
+            jobs.append([cc] + _flags(list(extra_flags) + PER_FILE_FLAGS.get(src, [])) + ["-c", s, "-o", o])
 
     def run(cmd):
         if verbose:

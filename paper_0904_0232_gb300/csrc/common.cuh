@@ -34,6 +34,7 @@ struct Grid {
   double m, a, c, dt;
   double xc, yc, zc;  // centre of mass in grid coordinates
   double r_plus, r_exc;
+  double r_fp64;  // FP32-mixed: promote metric evaluations to FP64 where r < r_fp64
   int quad_order;
   unsigned flags;
 };

@@ -354,6 +354,8 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : g.r_plus;
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
+  g.r_fp64 = (cfg->fp64_radius == 0.0 ? 4.0 : cfg->fp64_radius) * cfg->m;
+  if (cfg->fp64_radius < 0.0) g.r_fp64 = -1.0;
 
   c->fields = dev_alloc(c, 15 * (size_t)ncell * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));

@@ -21,15 +21,24 @@ struct Kerr {
   bool flat;     // r = 0 (the disk z = 0, R <= a): metric taken flat, its limit there
 };
 
+// Non-negative root of Eq. 6 as r^2, written so that neither branch cancels; *D receives
+// sqrt((R^2 - a^2)^2 + 4 a^2 z^2).
 template <typename S>
-__device__ __forceinline__ Kerr<S> kerr_eval(S x, S y, S z, S m, S a) {
-  Kerr<S> K;
+__device__ __forceinline__ S kerr_r2(S x, S y, S z, S a, S* D) {
   const S a2 = a * a;
   const S q = a2 * z * z;
   const S p = x * x + y * y + z * z - a2;
-  K.D = sqrt(p * p + S(4) * q);
-  // Non-negative root of Eq. 6 in r^2, written so that neither branch cancels.
-  const S r2 = (p >= S(0)) ? S(0.5) * (p + K.D) : (S(2) * q) / (K.D - p);
+  *D = sqrt(p * p + S(4) * q);
+  return (p >= S(0)) ? S(0.5) * (p + *D) : (S(2) * q) / (*D - p);
+}
+
+// f and k of Eqs. 4-5 at (x, y, z) given r^2 from Eq. 6.
+template <typename S>
+__device__ __forceinline__ Kerr<S> kerr_from_r2(S x, S y, S z, S m, S a, S r2, S D) {
+  Kerr<S> K;
+  const S a2 = a * a;
+  const S q = a2 * z * z;
+  K.D = D;
   if (!(r2 > S(0))) {
     K.flat = true;
     K.r = S(0);
@@ -47,6 +56,13 @@ __device__ __forceinline__ Kerr<S> kerr_eval(S x, S y, S z, S m, S a) {
   K.k1 = (K.r * y + a * x) * inv_rho2;
   K.k2 = z / K.r;
   return K;
+}
+
+template <typename S>
+__device__ __forceinline__ Kerr<S> kerr_eval(S x, S y, S z, S m, S a) {
+  S D;
+  const S r2 = kerr_r2<S>(x, y, z, a, &D);
+  return kerr_from_r2<S>(x, y, z, m, a, r2, D);
 }
 
 // Gamma^a_mn u^m u^n = g^ab (u^m d_m g_bn u^n - 1/2 d_b g_mn u^m u^n) for g = eta + f k k.

@@ -15,9 +15,9 @@
 //   4. Removal flag: r <= r_+ or a coordinate outside [1, n-2]; sort key = cell or kDead.
 //
 // Precision: T = double runs everything in FP64.  T = float (FP32-mixed) keeps positions,
-// velocities, fields and arithmetic in FP32 except where R^2 < 16 m^2 + a^2 (which contains
-// r < 4m): there the quartic, the metric and the Christoffel contraction run in FP64.  The
-// global J accumulators are FP64 in both modes.
+// velocities, fields and arithmetic in FP32 except where the FP32 estimate of r is below
+// r_fp64 (default 4m): there the quartic, the metric and the Christoffel contraction are
+// evaluated again in FP64.  The global J accumulators are FP64 in both modes.
 #include <cmath>
 
 #include "common.cuh"
@@ -49,8 +49,42 @@ struct Gauss<3> {
 
 struct Consts {
   double m, a, xc, yc, zc;
-  double promote_r2;  // FP32-mixed: evaluate in FP64 where R^2 < promote_r2
+  float r_fp64;  // FP32-mixed: evaluate in FP64 where the FP32 r is below this
 };
+
+template <typename T>
+__device__ __forceinline__ T sel3(int i, T a, T b, T c) {
+  return i == 0 ? a : (i == 1 ? b : c);
+}
+
+// FP64 metric and Christoffel contraction at a grid position (the FP32-mixed policy near the
+// hole); kept out of line: it runs for few particles and would otherwise bloat every call site.
+template <typename T>
+__device__ __noinline__ void metric_christoffel_fp64(const Consts& C, T x, T y, T z, T u0, T u1, T u2, T u3,
+                                                     T* out) {
+  const double Xd = (double)x - C.xc, Yd = (double)y - C.yc, Zd = (double)z - C.zc;
+  const Kerr<double> K = kerr_eval<double>(Xd, Yd, Zd, C.m, C.a);
+  const double ud[4] = {(double)u0, (double)u1, (double)u2, (double)u3};
+  double gd[4];
+  christoffel_uu<double>(K, Xd, Yd, Zd, C.a, ud, gd);
+  out[0] = (T)K.f;
+  out[1] = (T)K.k0;
+  out[2] = (T)K.k1;
+  out[3] = (T)K.k2;
+  out[4] = (T)gd[0];
+  out[5] = (T)gd[1];
+  out[6] = (T)gd[2];
+  out[7] = (T)gd[3];
+}
+
+// FP64 root of the quartic (Eq. 6) as r^2 and D, for quadrature nodes near the hole.
+template <typename T>
+__device__ __noinline__ void quartic_fp64(const Consts& C, T x, T y, T z, T* r2, T* D) {
+  double Dd;
+  const double r2d = kerr_r2<double>((double)x - C.xc, (double)y - C.yc, (double)z - C.zc, C.a, &Dd);
+  *r2 = (T)r2d;
+  *D = (T)Dd;
+}
 
 // a~ at (x, u): gather, convert, Lorentz - Christoffel.
 template <typename T, bool MIXED>
@@ -103,26 +137,25 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
   // --- metric and Christoffel contraction at the particle
   T f, k0, k1, k2, gam[4];
   const T X = x[0] - (T)C.xc, Y = x[1] - (T)C.yc, Z = x[2] - (T)C.zc;
-  if (MIXED && (double)(X * X + Y * Y + Z * Z) < C.promote_r2) {
-    const double Xd = (double)x[0] - C.xc, Yd = (double)x[1] - C.yc, Zd = (double)x[2] - C.zc;
-    const Kerr<double> K = kerr_eval<double>(Xd, Yd, Zd, C.m, C.a);
-    const double ud[4] = {(double)u[0], (double)u[1], (double)u[2], (double)u[3]};
-    double gd[4];
-    christoffel_uu<double>(K, Xd, Yd, Zd, C.a, ud, gd);
-    f = (T)K.f;
-    k0 = (T)K.k0;
-    k1 = (T)K.k1;
-    k2 = (T)K.k2;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) gam[q] = (T)gd[q];
+  const Kerr<T> Kt = kerr_eval<T>(X, Y, Z, (T)C.m, (T)C.a);
+  if (MIXED && (float)Kt.r < C.r_fp64) {
+    T o[8];
+    metric_christoffel_fp64<T>(C, x[0], x[1], x[2], u[0], u[1], u[2], u[3], o);
+    f = o[0];
+    k0 = o[1];
+    k1 = o[2];
+    k2 = o[3];
+    gam[0] = o[4];
+    gam[1] = o[5];
+    gam[2] = o[6];
+    gam[3] = o[7];
     ++n64;
   } else {
-    const Kerr<T> K = kerr_eval<T>(X, Y, Z, (T)C.m, (T)C.a);
-    christoffel_uu<T>(K, X, Y, Z, (T)C.a, u, gam);
-    f = K.f;
-    k0 = K.k0;
-    k1 = K.k1;
-    k2 = K.k2;
+    christoffel_uu<T>(Kt, X, Y, Z, (T)C.a, u, gam);
+    f = Kt.f;
+    k0 = Kt.k0;
+    k1 = Kt.k1;
+    k2 = Kt.k2;
   }
   T h[3], lor[4];
   contra_spatial(f, k0, k1, k2, b, d, h);
@@ -131,25 +164,27 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
   for (int q = 0; q < 4; ++q) out[q] = lor[q] - gam[q];
 }
 
-// Integrand of Eq. 18 at a grid position.
+// Integrand of Eq. 18, sqrt(g_II g_JJ - g_IJ^2) = sqrt(1 + f (k_I^2 + k_J^2)), at a grid
+// position.  FP32-mixed: near the hole the quartic root is taken in FP64.
 template <typename T, bool MIXED>
-__device__ __forceinline__ T area_integrand(const Consts& C, T px, T py, T pz, int I, int J, unsigned& n64) {
+__device__ __forceinline__ T area_integrand(const Consts& C, T px, T py, T pz, int K, unsigned& n64) {
   const T X = px - (T)C.xc, Y = py - (T)C.yc, Z = pz - (T)C.zc;
-  if (MIXED && (double)(X * X + Y * Y + Z * Z) < C.promote_r2) {
-    const Kerr<double> K =
-        kerr_eval<double>((double)px - C.xc, (double)py - C.yc, (double)pz - C.zc, C.m, C.a);
-    const double kv[3] = {K.k0, K.k1, K.k2};
+  T D;
+  T r2 = kerr_r2<T>(X, Y, Z, (T)C.a, &D);
+  if (MIXED && (float)r2 < C.r_fp64 * C.r_fp64) {
+    quartic_fp64<T>(C, px, py, pz, &r2, &D);
     ++n64;
-    return (T)sqrt(1.0 + K.f * (kv[I] * kv[I] + kv[J] * kv[J]));
   }
-  const Kerr<T> K = kerr_eval<T>(X, Y, Z, (T)C.m, (T)C.a);
-  const T kv[3] = {K.k0, K.k1, K.k2};
-  return sqrt(T(1) + K.f * (kv[I] * kv[I] + kv[J] * kv[J]));
+  const Kerr<T> Kt = kerr_from_r2<T>(X, Y, Z, (T)C.m, (T)C.a, r2, D);
+  // k_I^2 + k_J^2 = |k|^2 - k_K^2 with the transverse pair of direction K
+  const T kI = sel3(K, Kt.k1, Kt.k2, Kt.k0);
+  const T kJ = sel3(K, Kt.k2, Kt.k0, Kt.k1);
+  return sqrt(T(1) + Kt.f * (kI * kI + kJ * kJ));
 }
 
-// AREA(Is..If, Js..Jf) of Eq. 18 in the plane x^K = xK.
+// AREA of Eq. 18 over [Is, If] x [Js, Jf] in the plane x^K = xK.
 template <typename T, int Q, bool MIXED>
-__device__ __forceinline__ T area(const Consts& C, int K, T xK, int I, T Is, T If, int J, T Js, T Jf, unsigned& n64) {
+__device__ __forceinline__ T area(const Consts& C, int K, T xK, T Is, T If, T Js, T Jf, unsigned& n64) {
   T s = T(0);
   const T ci = T(0.5) * (Is + If), hi = T(0.5) * (If - Is);
   const T cj = T(0.5) * (Js + Jf), hj = T(0.5) * (Jf - Js);
@@ -157,11 +192,13 @@ __device__ __forceinline__ T area(const Consts& C, int K, T xK, int I, T Is, T I
   for (int p = 0; p < Q; ++p)
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      T pos[3];
-      pos[K] = xK;
-      pos[I] = ci + hi * (T)Gauss<Q>::x(p);
-      pos[J] = cj + hj * (T)Gauss<Q>::x(q);
-      s += (T)Gauss<Q>::w(p) * (T)Gauss<Q>::w(q) * area_integrand<T, MIXED>(C, pos[0], pos[1], pos[2], I, J, n64);
+      const T xi = ci + hi * (T)Gauss<Q>::x(p);
+      const T xj = cj + hj * (T)Gauss<Q>::x(q);
+      // (x^K, x^I, x^J) -> (x, y, z) with I = K+1, J = K+2 (mod 3)
+      const T px = sel3(K, xK, xj, xi);
+      const T py = sel3(K, xi, xK, xj);
+      const T pz = sel3(K, xj, xi, xK);
+      s += (T)Gauss<Q>::w(p) * (T)Gauss<Q>::w(q) * area_integrand<T, MIXED>(C, px, py, pz, K, n64);
     }
   return s * T(0.25) * (If - Is) * (Jf - Js);
 }
@@ -189,35 +226,37 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
     s2[ax] = dx[ax] - s1[ax];
   }
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-#pragma unroll
+#pragma unroll 1
   for (int seg = 0; seg < 2; ++seg) {
-    const int* cell = seg ? c2 : c1;
+    const int cx = seg ? c2[0] : c1[0], cy = seg ? c2[1] : c1[1], cz = seg ? c2[2] : c1[2];
     T P[3], dseg[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       dseg[ax] = seg ? s2[ax] : s1[ax];
       P[ax] = seg ? x0[ax] + (s1[ax] + T(0.5) * s2[ax]) : x0[ax] + T(0.5) * s1[ax];
     }
-#pragma unroll
+    const long long base = ((long long)cz * g.ny + cy) * g.nx + cx;
+#pragma unroll 1
     for (int K = 0; K < 3; ++K) {
-      const T dK = dseg[K];
+      const T dK = sel3(K, dseg[0], dseg[1], dseg[2]);
       if (dK == T(0)) continue;
       const T flux = qg * dK * inv_dt;
-      const int I = (K + 1) % 3, J = (K + 2) % 3;
-      const T i0 = (T)cell[I], j0 = (T)cell[J];
-      const T A00 = area<T, Q, MIXED>(C, K, P[K], I, P[I], i0 + T(1), J, P[J], j0 + T(1), n64);
-      const T A10 = area<T, Q, MIXED>(C, K, P[K], I, i0, P[I], J, P[J], j0 + T(1), n64);
-      const T A01 = area<T, Q, MIXED>(C, K, P[K], I, P[I], i0 + T(1), J, j0, P[J], n64);
-      const T A11 = area<T, Q, MIXED>(C, K, P[K], I, i0, P[I], J, j0, P[J], n64);
+      const T PK = sel3(K, P[0], P[1], P[2]);
+      const T PI = sel3(K, P[1], P[2], P[0]);
+      const T PJ = sel3(K, P[2], P[0], P[1]);
+      const T i0 = (T)sel3(K, cy, cz, cx), j0 = (T)sel3(K, cz, cx, cy);
+      const T A00 = area<T, Q, MIXED>(C, K, PK, PI, i0 + T(1), PJ, j0 + T(1), n64);
+      const T A10 = area<T, Q, MIXED>(C, K, PK, i0, PI, PJ, j0 + T(1), n64);
+      const T A01 = area<T, Q, MIXED>(C, K, PK, PI, i0 + T(1), j0, PJ, n64);
+      const T A11 = area<T, Q, MIXED>(C, K, PK, i0, PI, j0, PJ, n64);
       const T FA = A00 + A10 + A01 + A11;
-      const T W[4] = {A00 / FA, A10 / FA, A01 / FA, A11 / FA};
-      const long long st[3] = {1, sy, sz};
-      const long long base = ((long long)cell[2] * g.ny + cell[1]) * g.nx + cell[0];
-      double* JK = F.J[K];
-#pragma unroll
-      for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-        for (int di = 0; di < 2; ++di) atomicAdd(JK + base + di * st[I] + dj * st[J], (double)(flux * W[dj * 2 + di]));
+      const T W00 = A00 / FA, W10 = A10 / FA, W01 = A01 / FA, W11 = A11 / FA;
+      const long long stI = sel3(K, sy, sz, 1ll), stJ = sel3(K, sz, 1ll, sy);
+      double* JK = sel3(K, F.J[0], F.J[1], F.J[2]);
+      atomicAdd(JK + base, (double)(flux * W00));
+      atomicAdd(JK + base + stI, (double)(flux * W10));
+      atomicAdd(JK + base + stJ, (double)(flux * W01));
+      atomicAdd(JK + base + stI + stJ, (double)(flux * W11));
     }
   }
 }
@@ -236,7 +275,7 @@ __global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields
     C.xc = g.xc;
     C.yc = g.yc;
     C.zc = g.zc;
-    C.promote_r2 = 16.0 * g.m * g.m + g.a * g.a;
+    C.r_fp64 = (float)g.r_fp64;
     const T qm = (T)sp.qm;
     const T dt = (T)g.dt;
     T x0[4], u0[4];
@@ -245,46 +284,35 @@ __global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields
       x0[q] = P.x[q][i];
       u0[q] = P.u[q][i];
     }
-    // stage 1 and Eq. 16
-    T a[4], sx[4], su[4], xs[4], us[4];
-    accel<T, MIXED>(g, F, C, qm, x0, u0, a, flags, n64);
+    // RK4 in proper time (A1): stages at offsets 0, h/2, h/2, h; h = dt / gamma_1 (Eq. 16)
+    T xs[4], us[4], a[4], sx[4], su[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      xs[q] = x0[q];
+      us[q] = u0[q];
+      sx[q] = T(0);
+      su[q] = T(0);
+    }
+    T h = T(0);
     bool fb = false;
-    const T g1 = gamma_step<T>(u0[3], a[3], T(1) / (T)g.c, dt, &fb);
-    const T h = dt / g1;
-    const T h2 = T(0.5) * h;
+#pragma unroll 1
+    for (int stage = 0; stage < 4; ++stage) {
+      accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
+      if (stage == 0) h = dt / gamma_step<T>(u0[3], a[3], T(1) / (T)g.c, dt, &fb);
+      const T wgt = (stage == 0 || stage == 3) ? T(1) : T(2);
+      const T frac = (stage == 2) ? h : T(0.5) * h;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sx[q] = u0[q];
-      su[q] = a[q];
-      xs[q] = x0[q] + h2 * u0[q];
-      us[q] = u0[q] + h2 * a[q];
+      for (int q = 0; q < 4; ++q) {
+        sx[q] += wgt * us[q];
+        su[q] += wgt * a[q];
+        xs[q] = x0[q] + frac * us[q];
+        us[q] = u0[q] + frac * a[q];
+      }
     }
-    // stage 2
-    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sx[q] += T(2) * us[q];
-      su[q] += T(2) * a[q];
-      xs[q] = x0[q] + h2 * us[q];
-      us[q] = u0[q] + h2 * a[q];
-    }
-    // stage 3
-    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sx[q] += T(2) * us[q];
-      su[q] += T(2) * a[q];
-      xs[q] = x0[q] + h * us[q];
-      us[q] = u0[q] + h * a[q];
-    }
-    // stage 4
-    accel<T, MIXED>(g, F, C, qm, xs, us, a, flags, n64);
     T x1[4], u1[4], dx[4];
     const T h6 = h / T(6);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      sx[q] += us[q];
-      su[q] += a[q];
       dx[q] = h6 * sx[q];
       x1[q] = x0[q] + dx[q];
       u1[q] = u0[q] + h6 * su[q];
@@ -316,9 +344,16 @@ __global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields
       if (!(x1[q] >= T(1) && x1[q] <= T(nn[q] - 2))) outer = true;
     bool horizon = false;
     if (finite && g.m > 0.0) {
-      const Kerr<double> K =
-          kerr_eval<double>((double)x1[0] - g.xc, (double)x1[1] - g.yc, (double)x1[2] - g.zc, g.m, g.a);
-      horizon = K.flat || K.r <= g.r_plus;
+      // cheap FP32 screen, FP64 decision near r_+
+      const T X = x1[0] - (T)g.xc, Y = x1[1] - (T)g.yc, Z = x1[2] - (T)g.zc;
+      T D;
+      const T r2 = kerr_r2<T>(X, Y, Z, (T)g.a, &D);
+      if ((double)r2 < 1.2 * g.r_plus * g.r_plus + 1.0) {
+        double Dd;
+        const double r2d =
+            kerr_r2<double>((double)x1[0] - g.xc, (double)x1[1] - g.yc, (double)x1[2] - g.zc, g.a, &Dd);
+        horizon = !(r2d > 0.0) || sqrt(r2d) <= g.r_plus;
+      }
     }
     if (horizon || outer) {
       P.key[i] = kDead;

@@ -35,6 +35,7 @@ class grpic_config(ctypes.Structure):
                 ("m", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("quad_order", ctypes.c_int), ("r_excise", ctypes.c_double),
                 ("flags", ctypes.c_uint), ("sort_interval", ctypes.c_int), ("max_particles", ctypes.c_int64),
+                ("fp64_radius", ctypes.c_double),
                 ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
@@ -307,14 +308,15 @@ class Simulation:
     """One GRPIC context on the current CUDA device and PyTorch's current stream."""
 
     def __init__(self, nx, ny, nz, m, a, c, dt, precision="fp64", quad_order=2, r_excise=0.0, flags=0,
-                 sort_interval=1, max_particles=0, stream=None, torch_allocator=True):
+                 sort_interval=1, max_particles=0, stream=None, torch_allocator=True, fp64_radius=0.0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("GRPIC needs a CUDA device")
         load_library()
         self.shape = (nz, ny, nx)
         prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
-        cfg = grpic_config(nx, ny, nz, m, a, c, dt, prec, quad_order, r_excise, flags, sort_interval, max_particles)
+        cfg = grpic_config(nx, ny, nz, m, a, c, dt, prec, quad_order, r_excise, flags, sort_interval, max_particles,
+                           fp64_radius)
         if torch_allocator:
             cfg.alloc = _torch_alloc
             cfg.free_fn = _torch_free
