@@ -18,6 +18,7 @@ struct Kerr {
   S r, f;        // r of Eq. 6, f of Eq. 4
   S k0, k1, k2;  // spatial k_m (k_3 = 1)
   S D;           // sqrt((R^2 - a^2)^2 + 4 a^2 z^2) = d(quartic)/d(r^2)
+  S inv_r, inv_rho2, inv_sig;  // 1/r, 1/(r^2 + a^2), 1/(r^4 + a^2 z^2), shared with the derivatives
   bool flat;     // r = 0 (the disk z = 0, R <= a): metric taken flat, its limit there
 };
 
@@ -50,12 +51,33 @@ __device__ __forceinline__ Kerr<S> kerr_from_r2(S x, S y, S z, S m, S a, S r2, S
   }
   K.flat = false;
   K.r = sqrt(r2);
-  const S inv_rho2 = S(1) / (r2 + a2);
-  K.f = S(2) * m * K.r * r2 / (r2 * r2 + q);
-  K.k0 = (K.r * x - a * y) * inv_rho2;
-  K.k1 = (K.r * y + a * x) * inv_rho2;
-  K.k2 = z / K.r;
+  K.inv_r = S(1) / K.r;
+  K.inv_rho2 = S(1) / (r2 + a2);
+  K.inv_sig = S(1) / (r2 * r2 + q);
+  K.f = S(2) * m * K.r * r2 * K.inv_sig;
+  K.k0 = (K.r * x - a * y) * K.inv_rho2;
+  K.k1 = (K.r * y + a * x) * K.inv_rho2;
+  K.k2 = z * K.inv_r;
   return K;
+}
+
+// Integrand of Eq. 18 for the plane normal to axis K: g_II g_JJ - g_IJ^2 = 1 + f (k_I^2 + k_J^2)
+// and, k being null for eta (Eq. 6), k_I^2 + k_J^2 = 1 - k_K^2.  Given r^2 from Eq. 6.
+template <typename S>
+__device__ __forceinline__ S area_density(S x, S y, S z, S m, S a, S r2, int K) {
+  if (!(r2 > S(0))) return S(1);
+  const S r = sqrt(r2);
+  const S a2 = a * a;
+  const S sig = r2 * r2 + a2 * z * z;
+  if (K == 2) {
+    // f (1 - z^2/r^2) = 2 m r (r^2 - z^2) / Sigma
+    return sqrt(S(1) + S(2) * m * r * (r2 - z * z) / sig);
+  }
+  // f (1 - k_K^2) with k_x = (r x - a y)/(r^2+a^2), k_y = (r y + a x)/(r^2+a^2)
+  const S num = (K == 0) ? (r * x - a * y) : (r * y + a * x);
+  const S rho2 = r2 + a2;
+  const S kk = num * num / (rho2 * rho2);
+  return sqrt(S(1) + S(2) * m * r * r2 * (S(1) - kk) / sig);
 }
 
 template <typename S>
@@ -78,15 +100,15 @@ __device__ __forceinline__ void christoffel_uu(const Kerr<S>& K, S x, S y, S z, 
   const S r = K.r, f = K.f;
   const S k0 = K.k0, k1 = K.k1, k2 = K.k2;
   const S r2 = r * r, a2 = a * a;
-  const S inv_rho2 = S(1) / (r2 + a2);
+  const S inv_rho2 = K.inv_rho2;
   const S inv_D = S(1) / K.D;
-  const S inv_r = S(1) / r;
+  const S inv_r = K.inv_r;
   // grad r from the implicit quartic: r_x = x r / D, r_y = y r / D, r_z = z (r^2 + a^2) / (r D)
   const S rx = x * r * inv_D;
   const S ry = y * r * inv_D;
   const S rz = z * (r2 + a2) * inv_D * inv_r;
   // grad f: df/dr = f (3/r - 4 r^3/Sigma), df/dz|_r = -2 a^2 z f / Sigma, Sigma = r^4 + a^2 z^2
-  const S inv_sig = S(1) / (r2 * r2 + a2 * z * z);
+  const S inv_sig = K.inv_sig;
   const S fr = f * (S(3) * inv_r - S(4) * r2 * r * inv_sig);
   const S fx = fr * rx;
   const S fy = fr * ry;

@@ -175,11 +175,7 @@ __device__ __forceinline__ T area_integrand(const Consts& C, T px, T py, T pz, i
     quartic_fp64<T>(C, px, py, pz, &r2, &D);
     ++n64;
   }
-  const Kerr<T> Kt = kerr_from_r2<T>(X, Y, Z, (T)C.m, (T)C.a, r2, D);
-  // k_I^2 + k_J^2 = |k|^2 - k_K^2 with the transverse pair of direction K
-  const T kI = sel3(K, Kt.k1, Kt.k2, Kt.k0);
-  const T kJ = sel3(K, Kt.k2, Kt.k0, Kt.k1);
-  return sqrt(T(1) + Kt.f * (kI * kI + kJ * kJ));
+  return area_density<T>(X, Y, Z, (T)C.m, (T)C.a, r2, K);
 }
 
 // AREA of Eq. 18 over [Is, If] x [Js, Jf] in the plane x^K = xK.
@@ -262,7 +258,7 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
 }
 
 template <typename T, int Q, bool MIXED>
-__global__ void __launch_bounds__(128) k_push_deposit(const Grid g, const Fields<T> F, const Particles<T> P,
+__global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fields<T> F, const Particles<T> P,
                                                         const Species sp, DevStatus* st) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   unsigned flags = 0, n64 = 0;
