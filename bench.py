@@ -36,9 +36,11 @@ METRIC = "particle-steps/s (gather+RK4 Kerr push+deposit) FP32-mixed vs FP64; p5
 UNIT = "particle-steps/s"
 
 # Arithmetic operations per particle-step of the push + deposit formulation (FMA = 2,
-# add/mul/div/sqrt = 1; index arithmetic excluded), by Gauss-Legendre order Q of Eq. 18.
-# Derivation table in DESIGN.md ("Algorithmic work per particle-step").
-ALG_FLOPS = {1: 3230, 2: 6890, 3: 12990}
+# add/mul/div/sqrt = 1; index arithmetic excluded), by Gauss-Legendre order Q of Eq. 18:
+# RK4 push 2130 (4 x 492 per stage evaluation + stage algebra) + deposit 6 face weightings x
+# 4 sub-areas x Q^2 integrand evaluations (42 each) + split/weights/flux.  Derivation table
+# in DESIGN.md ("Algorithmic work per particle-step").
+ALG_FLOPS = {1: 3570, 2: 6600, 3: 11640}
 
 # Nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
@@ -66,6 +68,8 @@ def parse():
     p.add_argument("--quad", type=int, default=2)
     p.add_argument("--sort-interval", type=int, default=1)
     p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--fp32-compare-steps", type=int, default=50,
+                   help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -164,9 +168,11 @@ class Clocks:
 
 # ---- CPU baseline (the oracle, as it stands) ---------------------------------------------------
 def cpu_sample_workload():
+    """Bounded CPU sample: the Kerr electron-ion workload's parameters on a 40^3 window around
+    the hole, 20,000 evenly strided particles per species."""
     from paper_0904_0232_gb300 import synth
 
-    return synth.kerr_ion_electron_128(seed=2, n=40, max_particles=20000)
+    return synth.subsample(synth.kerr_ion_electron_128(seed=2, n=40), 20000)
 
 
 def run_oracle_steps(wl, steps, warmup=0):
@@ -193,7 +199,7 @@ def run_oracle_steps(wl, steps, warmup=0):
     return psteps, el, O.max_threads(), per_step
 
 
-def cpu_baseline(steps=6):
+def cpu_baseline(steps=20):
     wl = cpu_sample_workload()
     psteps, el, cores, _ = run_oracle_steps(wl, steps)
     return {"value": psteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -210,7 +216,8 @@ def run_reference(args, dist):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "kerr_ion_electron_128 (bounded CPU sample: 40^3 window, 40000 particles)",
+            "config": {"workload": "kerr_ion_electron_128 (bounded CPU sample: 40^3 window around the hole, "
+                                   "40000 strided particles)",
                        "grid": wl.nx, "particles": wl.n_particles, "m": wl.m, "a": wl.a, "dt": wl.dt},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} oracle steps of the 40^3 / 40000-particle sample"},
@@ -218,13 +225,13 @@ def run_reference(args, dist):
 
 
 # ---- GPU arm ------------------------------------------------------------------------------------
-def make_sim(wl, precision, args, device_inputs=True):
+def make_sim(wl, precision, args, device_inputs=True, fp64_radius=0.0):
     import torch
 
     from paper_0904_0232_gb300.grpic import GRPIC_U_COV_SPATIAL, Simulation
 
     sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=args.quad,
-                     sort_interval=args.sort_interval)
+                     sort_interval=args.sort_interval, fp64_radius=fp64_radius)
     sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
     for s, sp in enumerate(wl.species):
         if device_inputs:
@@ -314,6 +321,21 @@ def run_gpu(args, dist):
                 "ms_per_step": ms64 / args.fp64_steps,
                 "push_ms_per_step": prof64["push_deposit"][0] / args.fp64_steps}
 
+    # --- the same workload with the FP64 region switched off (all-FP32 metric evaluations)
+    fp32_all = None
+    if args.fp32_compare_steps > 0:
+        sim32 = make_sim(wl, "fp32_mixed", args, fp64_radius=-1.0)
+        sim32.set_profiling(True)
+        sim32.step(1)
+        ms32, ps32, prof32, _ = timed_steps(sim32, args.fp32_compare_steps, dist)
+        sim32.close()
+        del sim32
+        torch.cuda.empty_cache()
+        fp32_all = {"value": dist.sum(ps32) / (dist.max(ms32) * 1e-3), "unit": UNIT,
+                    "steps": args.fp32_compare_steps, "ms_per_step": ms32 / args.fp32_compare_steps,
+                    "push_ms_per_step": prof32["push_deposit"][0] / args.fp32_compare_steps,
+                    "note": "fp64_radius < 0: no FP64 metric evaluations (error vs oracle in DESIGN.md)"}
+
     # --- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -363,6 +385,7 @@ def run_gpu(args, dist):
                      "fma_probe_tflops": fp32_probe / 1e12,
                      "flops_per_particle_step": ALG_FLOPS[args.quad], "kernel_sha": sha},
         "fp64": fp64,
+        "fp32_no_fp64_region": fp32_all,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

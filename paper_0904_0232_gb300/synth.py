@@ -124,6 +124,19 @@ def kerr_ion_electron_128(seed=2, max_particles=None, n=128, cells=None, wp_dt=0
                   max_particles=max_particles, cells=cells, wp_dt=wp_dt)
 
 
+def subsample(wl, n_per_species):
+    """The same workload keeping n evenly strided particles per species (a bounded sample that
+    still spans the whole grid)."""
+    species = []
+    for sp in wl.species:
+        k = max(1, sp.ids.size // max(1, n_per_species))
+        sel = np.arange(0, sp.ids.size, k)[:n_per_species]
+        species.append(SpeciesInput(sp.q_over_m, sp.q_macro, sp.x4[:, sel].copy(), sp.usp[:, sel].copy(),
+                                    sp.ids[sel].copy()))
+    return Workload(wl.name + f"_sample{n_per_species}", wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, wl.B0,
+                    wl.nsteps, species)
+
+
 def random_fields(shape, seed, scale=0.05):
     """Smooth-ish random prognostic fields (d, b), each (3, nz, ny, nx)."""
     rng = _rng(seed, 99)
