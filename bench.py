@@ -47,7 +47,7 @@ FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 
 # DRAM traffic of one push_deposit launch per particle, from an ncu capture (profiles/),
 # valid for the kernel source whose hash is recorded with it.
-PUSH_TRAFFIC = {"sha": None, "bytes_per_particle": None}
+PUSH_TRAFFIC = {"sha": "b10997ac32049e48", "bytes_per_particle": 1223.29e6 / 15.6e6}
 
 
 def kernel_sha():
@@ -370,7 +370,7 @@ def run_gpu(args, dist):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (FP64 metric/Christoffel for R^2 < 16m^2 + a^2; FP64 J)",
+        "vs_baseline": None, "dtype": "f32 (FP64 quartic/metric/Christoffel where r < 4m; FP64 J)",
         "data": "synthetic (seeded generator; stands in for the paper's disk/corona plasma)",
         "config": {"workload": f"kerr_ion_electron_{args.grid}: Kerr a=0.9m, m=4 cells, {args.grid}^3 grid, "
                                "e-/ion (mass ratio 20), 8 ppc per species, u_th=0.05c, B_z=0.1, dt=0.4",
