@@ -70,6 +70,10 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=4)
     p.add_argument("--fp32-compare-steps", type=int, default=50,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
+    p.add_argument("--workload", choices=["kerr128", "batch"], default="kerr128",
+                   help="kerr128: the single-instance Kerr electron-ion workload; batch: many small "
+                        "instances advanced by the batched engine")
+    p.add_argument("--batch-n", type=int, default=64)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -394,11 +398,94 @@ def run_gpu(args, dist):
     return line
 
 
+def run_batch(args, dist):
+    """Batched workload: n instances (grids 32^3-96^3, 1-32 particles per cell per species,
+    m in [1, 4] cells, a in [0, 0.99] m, pair plasma, B_z = 0.05, dt = 0.4, FP32-mixed) advanced
+    by one persistent launch per stage from a CUDA graph; compared with the same instances
+    stepped one after another."""
+    import torch
+
+    from paper_0904_0232_gb300 import synth
+    from paper_0904_0232_gb300.build import build
+    from paper_0904_0232_gb300.grpic import (GRPIC_U_COV_SPATIAL, Simulation, grpic_batch_create,
+                                             grpic_batch_destroy, grpic_batch_info, grpic_batch_step)
+
+    torch.cuda.set_device(dist.local)
+    build()
+    specs = synth.batch_specs(args.batch_n)
+    dev = torch.device("cuda")
+    draws = {}
+    for g in sorted({sp.grid for sp in specs}):
+        x, u0, u1 = synth.cell_major_pairs(g, 32, 0.1, 1.0, seed=7)
+        draws[g] = tuple(torch.from_numpy(a).to(dev) for a in (x, u0, u1))
+    sims = []
+    npart = 0
+    for k, sp in enumerate(specs):
+        x, u0, u1 = draws[sp.grid]
+        xs = x[:, :, :sp.ppc].reshape(3, -1)
+        n = xs.shape[1]
+        x4 = torch.cat([xs, torch.zeros((1, n), dtype=torch.float64, device=dev)]).contiguous()
+        ids = torch.arange(n, dtype=torch.int32, device=dev)
+        q = synth.charge_for(0.4, sp.ppc, (-1.0, 1.0), 0.1)
+        sim = Simulation(sp.grid, sp.grid, sp.grid, sp.m, sp.a, 1.0, 0.4, precision="fp32_mixed",
+                         quad_order=args.quad)
+        sim.set_uniform_field(B=(0.0, 0.0, 0.05))
+        for s, (qm, u) in enumerate(((-1.0, u0), (1.0, u1))):
+            us = torch.cat([u[:, :, :sp.ppc].reshape(3, -1), torch.zeros((1, n), dtype=torch.float64, device=dev)])
+            sim.load_particles(s, qm, float(np.sign(qm) * q), x4, us.contiguous(), ids, umode=GRPIC_U_COV_SPATIAL)
+        npart += sum(sim.num_particles(s) for s in range(2))
+        sims.append(sim)
+    del draws
+    torch.cuda.empty_cache()
+
+    def psteps():
+        return sum(s.stats()["particle_steps"] for s in sims)
+
+    b = grpic_batch_create([s.handle for s in sims])
+    kps, blocks = grpic_batch_info(b)
+    grpic_batch_step(b, args.warmup)
+    p0 = psteps()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grpic_batch_step(b, args.steps)
+    el = time.perf_counter() - t0
+    batched = (psteps() - p0) / el
+    grpic_batch_destroy(b)
+    # the same instances one after another (one context's step sequence at a time)
+    seq_steps = max(1, min(args.steps, 10))
+    p0 = psteps()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step_async(seq_steps)
+    for s in sims:
+        s.sync()
+    el_seq = time.perf_counter() - t0
+    sequential = (psteps() - p0) / el_seq
+    value = dist.sum(batched)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 quartic/metric/Christoffel where r < 4m; FP64 J)",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": f"batch of {len(specs)} instances: grids 32^3-96^3, 1-32 ppc per species, "
+                                   "m 1-4 cells, a 0-0.99 m, pair plasma, B_z=0.05, dt=0.4, omega_p dt=0.1",
+                       "particles": npart, "kernels_per_step": kps, "work_blocks": blocks,
+                       "timing": "host wall clock around synchronising graph replays"},
+            "sequential": {"value": sequential, "unit": UNIT, "steps": seq_steps,
+                           "note": "the same contexts stepped one after another (non-batched launches)"},
+            "gpu_launches": int(kps * args.steps)}
+    for s in sims:
+        s.close()
+    return line
+
+
 def main():
     args = parse()
     dist = Dist()
     if args.impl == "reference":
         line = run_reference(args, dist)
+    elif args.workload == "batch":
+        line = run_batch(args, dist)
     else:
         line = run_gpu(args, dist)
     if dist.rank == 0 and line is not None:

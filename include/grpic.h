@@ -232,10 +232,22 @@ grpic_status grpic_sort_particles_static(int nx, int ny, int nz, int64_t n, cons
  * ------------------------------------------------------------------------------------- */
 typedef struct grpic_batch grpic_batch;
 
-/* Group n contexts, all FP32_MIXED or all FP64 and all on `stream`.  The contexts stay owned
- * by the caller and must outlive the batch. */
+/* Group n contexts with the same precision, quadrature order and field-update form.  The
+ * batch builds one device descriptor per instance and tables of (instance, work block) items
+ * for every stage; each batched stage is a persistent grid-stride launch over such a table,
+ * and one step's stage sequence is captured once in a CUDA graph on a stream the batch owns
+ * (`stream` is unused).  The contexts stay owned by the caller and must outlive the batch; the
+ * batch is built for the particle counts loaded at creation (re-create it after loading more).
+ * Every batched step sorts.  Returns GRPIC_ERR_INVALID for mismatched contexts. */
 grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grpic_batch** out);
+
+/* Advance every instance nsteps timesteps (graph replays), ordered after each context's pending
+ * work; then synchronise and check every context's status (first error returned). */
 grpic_status grpic_batch_step(grpic_batch* b, int nsteps);
+
+/* Kernels launched per batched step, and the total number of work blocks in the stage tables. */
+grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t* work_blocks);
+
 grpic_status grpic_batch_destroy(grpic_batch* b);
 
 #ifdef __cplusplus

@@ -113,4 +113,62 @@ template <typename T>
 void launch_sort(const Grid& g, const Particles<T>& src, const Particles<T>& dst, const SortScratch& s,
                  int* n_out, cudaStream_t stream);
 
+// ---- batched engine -------------------------------------------------------------------------
+// Every stage of a batched step is one launch over a device table of work blocks; each block
+// belongs to exactly one instance (work is padded to whole blocks), so per-instance state and
+// warp-level reductions stay block-uniform.  Kernels loop over the table grid-stride.
+struct BlockEntry {
+  int inst;   // instance (field stages) or instance * 4 + species (particle stages)
+  int block;  // block index within that instance's work
+};
+
+template <typename T>
+struct SpeciesDesc {
+  double qm, qmacro;
+  Particles<T> buf[2];  // the two ping-pong buffers (n = work upper bound, n_dev = live count)
+  int* cur;             // device int: index of the current buffer
+  long long bin_base;   // first sort bin of this (instance, species) in the batch's bin array
+  int active;
+};
+
+template <typename T>
+struct InstDesc {
+  Grid g;
+  Fields<T> F;
+  DevStatus* st;
+  SpeciesDesc<T> sp[4];
+};
+
+template <typename T>
+struct BatchTables {
+  const InstDesc<T>* desc;
+  const BlockEntry* conv;  // cells of [1, n-2]^3, 128 per block
+  int nconv;
+  const BlockEntry* upd;   // cells of [2, n-3]^3, 256 per block
+  int nupd;
+  const BlockEntry* all;   // all cells, 256 per block
+  int nall;
+  const BlockEntry* part;  // particles of (instance, species), 128 per block
+  int npart;
+  int* counts;             // sort bins of every (instance, species)
+  int* offsets;
+  int* tiles;
+  long long nbins;
+  const int* pairs;        // instance * 4 + species of every loaded species
+  int npairs;
+  int* pair_base;          // exclusive prefix at each pair's first bin (per step)
+  int persist_blocks;      // grid size of the persistent launches
+};
+
+template <typename T>
+void launch_batch_b_half(const BatchTables<T>& bt, int which, bool literal, cudaStream_t st);
+template <typename T>
+void launch_batch_e_step(const BatchTables<T>& bt, bool literal, cudaStream_t st);
+template <typename T>
+void launch_batch_zero_j(const BatchTables<T>& bt, cudaStream_t st);
+template <typename T>
+void launch_batch_push(const BatchTables<T>& bt, int quad_order, cudaStream_t st);
+template <typename T>
+void launch_batch_sort(const BatchTables<T>& bt, cudaStream_t st);
+
 }  // namespace grpic

@@ -9,6 +9,7 @@
 // their own lattice; the conversion uses the metric at that point (cached at create).  Each
 // pass is two launches: a conversion pass into a scratch plane, then the stencil update, so
 // every conversion is done once per lattice point.  Both passes stream x-fastest rows.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -48,12 +49,13 @@ __device__ __forceinline__ T avg(const T* __restrict__ a, long long c, long long
   return s / T(cnt);
 }
 
+// pred = true reads d from the midpoint predictor planes (time-centred E step).
 template <int TL, typename T>
 __device__ __forceinline__ void gather_pair(const Fields<T>& F, long long c, long long sy, long long sz, T b[3],
-                                            T d[3]) {
-  d[0] = avg<TL, 0>(F.d[0], c, sy, sz);
-  d[1] = avg<TL, 1>(F.d[1], c, sy, sz);
-  d[2] = avg<TL, 2>(F.d[2], c, sy, sz);
+                                            T d[3], bool pred = false) {
+  d[0] = avg<TL, 0>(pred ? F.dp[0] : F.d[0], c, sy, sz);
+  d[1] = avg<TL, 1>(pred ? F.dp[1] : F.d[1], c, sy, sz);
+  d[2] = avg<TL, 2>(pred ? F.dp[2] : F.d[2], c, sy, sz);
   b[0] = avg<TL, 3>(F.b[0], c, sy, sz);
   b[1] = avg<TL, 4>(F.b[1], c, sy, sz);
   b[2] = avg<TL, 5>(F.b[2], c, sy, sz);
@@ -119,11 +121,10 @@ __global__ void k_metric_cache(const Grid g, T* __restrict__ mc, uint8_t* __rest
   mask[c] = bits;
 }
 
-// ---- B half-step ------------------------------------------------------------------------
+// ---- per-cell stencils (shared by the single-context and the batched kernels) -------------
+// covariant e_i = F_i4 at the three edge points of cell (i,j,k) into the scratch planes
 template <typename T>
-__global__ void k_cov_e(const Grid g, const Fields<T> F, const Box bx) {
-  int i, j, k;
-  if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void cov_e_cell(const Grid& g, const Fields<T>& F, int i, int j, int k) {
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long c = cell_index(g, i, j, k);
   T b[3], d[3], h[3], e[3], f, k0, k1, k2;
@@ -144,15 +145,16 @@ __global__ void k_cov_e(const Grid g, const Fields<T> F, const Box bx) {
   F.s[2][c] = e[2];
 }
 
-// mode 0: b -= coef curl e (in place); 1: save b to bp, then b -= coef curl e;
-// 2: b = bp - coef curl e.  Only advanced (masked) locations are touched.
+// Eq. 10 at the three face points of cell (i,j,k).  mode 0: b -= (dx4/2) curl e in place;
+// 1: save b to bp, then b -= (dx4/2) curl e; 2: b = bp - dx4 curl e.  Only advanced (masked)
+// locations are touched.
 template <typename T>
-__global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, T coef, int mode) {
-  int i, j, k;
-  if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void b_update_cell(const Grid& g, const Fields<T>& F, int i, int j, int k, int mode) {
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
+  const T dx4 = (T)(g.c * g.dt);
+  const T coef = (mode == 2) ? dx4 : dx4 / T(2);
   const T* ev[3] = {F.s[0], F.s[1], F.s[2]};
   // (alpha, beta) of F_{alpha beta}: b_x = F_yz, b_y = F_zx, b_z = F_xy
   const int al[3] = {1, 2, 0}, be[3] = {2, 0, 1};
@@ -169,43 +171,45 @@ __global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, T coef
   }
 }
 
-// ---- E step -----------------------------------------------------------------------------
+// contravariant F^{jk} at the three face points of cell (i,j,k) into the scratch planes;
+// pred = true takes d from the midpoint predictor
 template <typename T>
-__global__ void k_contra_h(const Grid g, const Fields<T> F, const Box bx) {
-  int i, j, k;
-  if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void contra_h_cell(const Grid& g, const Fields<T>& F, int i, int j, int k, bool pred) {
   const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   const long long c = cell_index(g, i, j, k);
   T b[3], d[3], h[3], f, k0, k1, k2;
-  gather_pair<3>(F, c, sy, sz, b, d);
+  gather_pair<3>(F, c, sy, sz, b, d, pred);
   cached_metric<3>(F, g.ncell, c, f, k0, k1, k2);
   contra_spatial(f, k0, k1, k2, b, d, h);
   F.s[0][c] = h[0];
-  gather_pair<4>(F, c, sy, sz, b, d);
+  gather_pair<4>(F, c, sy, sz, b, d, pred);
   cached_metric<4>(F, g.ncell, c, f, k0, k1, k2);
   contra_spatial(f, k0, k1, k2, b, d, h);
   F.s[1][c] = h[1];
-  gather_pair<5>(F, c, sy, sz, b, d);
+  gather_pair<5>(F, c, sy, sz, b, d, pred);
   cached_metric<5>(F, g.ncell, c, f, k0, k1, k2);
   contra_spatial(f, k0, k1, k2, b, d, h);
   F.s[2][c] = h[2];
 }
 
-// d_out = d + coef (4 pi/c J - div h) at advanced locations.  full = true writes every cell
-// of the grid (d copied where not advanced) so d_out can be read as a whole field.
+// Eq. 12 at the three edge points of cell (i,j,k): d_out = d + coef (4 pi/c J - div h) at
+// advanced locations.  predictor = true: coef = dx4/2, d_out = the predictor planes, written
+// at every cell (d copied where not advanced) so they read as a whole field; otherwise
+// coef = dx4 and d is updated in place.
 template <typename T>
-__global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, T coef, double four_pi_over_c,
-                           T* out0, T* out1, T* out2, bool full) {
-  int i, j, k;
-  if (!box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void d_update_cell(const Grid& g, const Fields<T>& F, int i, int j, int k,
+                                              bool predictor) {
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
-  T* out[3] = {out0, out1, out2};
+  const T dx4 = (T)(g.c * g.dt);
+  const T coef = predictor ? dx4 / T(2) : dx4;
+  const double four_pi_over_c = 4.0 * M_PI / g.c;
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
+    T* out = predictor ? F.dp[al] : F.d[al];
     if (!(bits & (1u << al))) {
-      if (full) out[al][c] = F.d[al][c];
+      if (predictor) out[c] = F.d[al][c];
       continue;
     }
     T div = T(0);
@@ -219,7 +223,70 @@ __global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, T coef
       div += sgn * (hq[c] - hq[c - st[nu]]);
     }
     const T src = (T)(four_pi_over_c * F.J[al][c]);
-    out[al][c] = F.d[al][c] + (src - div) * coef;
+    out[c] = F.d[al][c] + (src - div) * coef;
+  }
+}
+
+// ---- single-context kernels ----------------------------------------------------------------
+template <typename T>
+__global__ void k_cov_e(const Grid g, const Fields<T> F, const Box bx) {
+  int i, j, k;
+  if (box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) cov_e_cell(g, F, i, j, k);
+}
+
+template <typename T>
+__global__ void k_b_update(const Grid g, const Fields<T> F, const Box bx, int mode) {
+  int i, j, k;
+  if (box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k)) b_update_cell(g, F, i, j, k, mode);
+}
+
+template <typename T>
+__global__ void k_contra_h(const Grid g, const Fields<T> F, const Box bx, bool pred) {
+  int i, j, k;
+  if (box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k))
+    contra_h_cell(g, F, i, j, k, pred);
+}
+
+template <typename T>
+__global__ void k_d_update(const Grid g, const Fields<T> F, const Box bx, bool predictor) {
+  int i, j, k;
+  if (box_cell(g, bx, blockIdx.x * (long long)blockDim.x + threadIdx.x, i, j, k))
+    d_update_cell(g, F, i, j, k, predictor);
+}
+
+// ---- batched kernels: grid-stride over a table of (instance, block) work items -------------
+// lo = 1: conversion box [1, n-2]^3; 2: update box [2, n-3]^3; 0: the whole grid.
+__device__ __forceinline__ Box box_of(const Grid& g, int lo) {
+  Box b;
+  b.lo = lo;
+  b.nxb = g.nx - 2 * lo;
+  b.nyb = g.ny - 2 * lo;
+  b.nzb = g.nz - 2 * lo;
+  return b;
+}
+
+// op: 0 cov_e, 1 b_update(mode), 2 contra_h(pred = mode), 3 d_update(predictor = mode),
+// 4 zero J
+template <typename T, int OP>
+__global__ void k_batch_field(const InstDesc<T>* __restrict__ desc, const BlockEntry* __restrict__ blk, int nblk,
+                              int lo, int mode) {
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const BlockEntry e = blk[bi];
+    const InstDesc<T>& D = desc[e.inst];
+    const Grid& g = D.g;
+    const long long t = (long long)e.block * blockDim.x + threadIdx.x;
+    int i, j, k;
+    if (!box_cell(g, box_of(g, lo), t, i, j, k)) continue;
+    if (OP == 0) cov_e_cell(g, D.F, i, j, k);
+    if (OP == 1) b_update_cell(g, D.F, i, j, k, mode);
+    if (OP == 2) contra_h_cell(g, D.F, i, j, k, mode != 0);
+    if (OP == 3) d_update_cell(g, D.F, i, j, k, mode != 0);
+    if (OP == 4) {
+      const long long c = cell_index(g, i, j, k);
+      D.F.J[0][c] = 0.0;
+      D.F.J[1][c] = 0.0;
+      D.F.J[2][c] = 0.0;
+    }
   }
 }
 
@@ -276,14 +343,9 @@ void launch_b_half(const Grid& g, const Fields<T>& F, int which, bool literal, c
   const Box conv = make_box(g, 1), upd = make_box(g, 2);
   const long long nconv = (long long)conv.nxb * conv.nyb * conv.nzb;
   const long long nupd = (long long)upd.nxb * upd.nyb * upd.nzb;
-  const T dx4 = (T)(g.c * g.dt);
   k_cov_e<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv);
-  if (literal)
-    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4 / T(2), 0);
-  else if (which == 0)
-    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4 / T(2), 1);
-  else
-    k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4, 2);
+  const int mode = literal ? 0 : (which == 0 ? 1 : 2);
+  k_b_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, mode);
 }
 
 template <typename T>
@@ -292,18 +354,35 @@ void launch_e_step(const Grid& g, const Fields<T>& F, bool literal, cudaStream_t
   const long long nconv = (long long)conv.nxb * conv.nyb * conv.nzb;
   const long long nupd = (long long)upd.nxb * upd.nyb * upd.nzb;
   const long long nall = (long long)all.nxb * all.nyb * all.nzb;
-  const T dx4 = (T)(g.c * g.dt);
-  const double fpc = 4.0 * M_PI / g.c;
-  k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv);
+  k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv, false);
   if (!literal) {
     // midpoint predictor d* = d + (dx4/2) rhs(d), then h from (b, d*)
-    k_d_update<T><<<blocks_for(nall, 256), 256, 0, st>>>(g, F, all, dx4 / T(2), fpc, F.dp[0], F.dp[1], F.dp[2],
-                                                          true);
-    Fields<T> Fp = F;
-    for (int q = 0; q < 3; ++q) Fp.d[q] = F.dp[q];
-    k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, Fp, conv);
+    k_d_update<T><<<blocks_for(nall, 256), 256, 0, st>>>(g, F, all, true);
+    k_contra_h<T><<<blocks_for(nconv, 128), 128, 0, st>>>(g, F, conv, true);
   }
-  k_d_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, dx4, fpc, F.d[0], F.d[1], F.d[2], false);
+  k_d_update<T><<<blocks_for(nupd, 256), 256, 0, st>>>(g, F, upd, false);
+}
+
+template <typename T>
+void launch_batch_b_half(const BatchTables<T>& bt, int which, bool literal, cudaStream_t st) {
+  const int mode = literal ? 0 : (which == 0 ? 1 : 2);
+  k_batch_field<T, 0><<<std::min(bt.nconv, bt.persist_blocks), 128, 0, st>>>(bt.desc, bt.conv, bt.nconv, 1, 0);
+  k_batch_field<T, 1><<<std::min(bt.nupd, bt.persist_blocks), 256, 0, st>>>(bt.desc, bt.upd, bt.nupd, 2, mode);
+}
+
+template <typename T>
+void launch_batch_e_step(const BatchTables<T>& bt, bool literal, cudaStream_t st) {
+  k_batch_field<T, 2><<<std::min(bt.nconv, bt.persist_blocks), 128, 0, st>>>(bt.desc, bt.conv, bt.nconv, 1, 0);
+  if (!literal) {
+    k_batch_field<T, 3><<<std::min(bt.nall, bt.persist_blocks), 256, 0, st>>>(bt.desc, bt.all, bt.nall, 0, 1);
+    k_batch_field<T, 2><<<std::min(bt.nconv, bt.persist_blocks), 128, 0, st>>>(bt.desc, bt.conv, bt.nconv, 1, 1);
+  }
+  k_batch_field<T, 3><<<std::min(bt.nupd, bt.persist_blocks), 256, 0, st>>>(bt.desc, bt.upd, bt.nupd, 2, 0);
+}
+
+template <typename T>
+void launch_batch_zero_j(const BatchTables<T>& bt, cudaStream_t st) {
+  k_batch_field<T, 4><<<std::min(bt.nall, bt.persist_blocks), 256, 0, st>>>(bt.desc, bt.all, bt.nall, 0, 0);
 }
 
 template <typename T>
@@ -327,7 +406,10 @@ void launch_convert_out(double* dst, const T* src, long long n, cudaStream_t st)
   template void launch_uniform_field<T>(const Grid&, const Fields<T>&, const double*, const double*,     \
                                         cudaStream_t);                                                   \
   template void launch_convert_in<T>(T*, const double*, long long, cudaStream_t);                       \
-  template void launch_convert_out<T>(double*, const T*, long long, cudaStream_t);
+  template void launch_convert_out<T>(double*, const T*, long long, cudaStream_t);                      \
+  template void launch_batch_b_half<T>(const BatchTables<T>&, int, bool, cudaStream_t);                 \
+  template void launch_batch_e_step<T>(const BatchTables<T>&, bool, cudaStream_t);                      \
+  template void launch_batch_zero_j<T>(const BatchTables<T>&, cudaStream_t);
 
 GRPIC_INST_FIELDS(float)
 GRPIC_INST_FIELDS(double)

@@ -719,39 +719,257 @@ grpic_status grpic_get_profile(grpic_ctx* c, double times_ms[6], int64_t counts[
   return GRPIC_OK;
 }
 
-// ---- batched engine (stage-interleaved over contexts) ----------------------------------
+}  // extern "C"
+
+// ---- batched engine ----------------------------------------------------------------------------
 struct grpic_batch {
   std::vector<grpic_ctx*> ctxs;
+  cudaStream_t stream = nullptr;  // created by the batch: capturable, ordered with the contexts by events
+  bool mixed = false, literal = false;
+  int quad = 2;
+  std::vector<void*> allocs;
+  void* desc = nullptr;
+  BlockEntry *conv = nullptr, *upd = nullptr, *all = nullptr, *part = nullptr;
+  int nconv = 0, nupd = 0, nall = 0, npart = 0;
+  int *counts = nullptr, *offsets = nullptr, *tiles = nullptr, *pairs = nullptr, *pair_base = nullptr;
+  int* cur = nullptr;  // device ping-pong index per (instance, species)
+  long long nbins = 0;
+  int npairs = 0;
+  int persist_blocks = 0;
+  std::vector<long long> pair_n;  // work upper bound of each pair when the batch was built
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev = nullptr;
+  long long kernels_per_step = 0;
 };
+
+namespace {
+
+void* batch_alloc(grpic_batch* b, size_t bytes) {
+  void* p = dev_alloc(b->ctxs[0], bytes);
+  if (p) b->allocs.push_back(p);
+  return p;
+}
+
+template <typename T>
+BatchTables<T> batch_tables(grpic_batch* b) {
+  BatchTables<T> t;
+  t.desc = static_cast<const InstDesc<T>*>(b->desc);
+  t.conv = b->conv;
+  t.nconv = b->nconv;
+  t.upd = b->upd;
+  t.nupd = b->nupd;
+  t.all = b->all;
+  t.nall = b->nall;
+  t.part = b->part;
+  t.npart = b->npart;
+  t.counts = b->counts;
+  t.offsets = b->offsets;
+  t.tiles = b->tiles;
+  t.nbins = b->nbins;
+  t.pairs = b->pairs;
+  t.npairs = b->npairs;
+  t.pair_base = b->pair_base;
+  t.persist_blocks = b->persist_blocks;
+  return t;
+}
+
+void append_blocks(std::vector<BlockEntry>& v, int inst, long long items, int bs) {
+  const long long nb = (items + bs - 1) / bs;
+  for (long long q = 0; q < nb; ++q) v.push_back(BlockEntry{inst, (int)q});
+}
+
+template <typename T>
+grpic_status batch_build(grpic_batch* b) {
+  const int n = (int)b->ctxs.size();
+  std::vector<InstDesc<T>> desc(n);
+  std::vector<BlockEntry> conv, upd, all, part;
+  std::vector<int> pairs, cur_init;
+  std::vector<long long> bin_base;
+  long long nbins = 0;
+  // device ping-pong indices: one int per (instance, species)
+  b->cur = static_cast<int*>(batch_alloc(b, sizeof(int) * 4 * n));
+  if (!b->cur) return GRPIC_ERR_OOM;
+  cur_init.assign(4 * n, 0);
+  for (int i = 0; i < n; ++i) {
+    grpic_ctx* c = b->ctxs[i];
+    InstDesc<T>& D = desc[i];
+    D.g = c->g;
+    D.F = fields_view<T>(c);
+    D.st = c->st;
+    const Grid& g = c->g;
+    append_blocks(conv, i, (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2), 128);
+    append_blocks(upd, i, (long long)(g.nx - 4) * (g.ny - 4) * (g.nz - 4), 256);
+    append_blocks(all, i, g.ncell, 256);
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      SpeciesStore& S = c->sp[s];
+      SpeciesDesc<T>& SD = D.sp[s];
+      SD.active = S.loaded ? 1 : 0;
+      SD.qm = S.qm;
+      SD.qmacro = S.qmacro;
+      SD.cur = b->cur + 4 * i + s;
+      SD.bin_base = 0;
+      if (!S.loaded) continue;
+      SD.buf[0] = particles_view<T>(c, s, 0);
+      SD.buf[1] = particles_view<T>(c, s, 1);
+      SD.bin_base = nbins;
+      nbins += g.ncell + 1;
+      cur_init[4 * i + s] = S.cur;
+      pairs.push_back(4 * i + s);
+      b->pair_n.push_back(S.n);
+      append_blocks(part, 4 * i + s, S.n, 128);
+    }
+  }
+  b->npairs = (int)pairs.size();
+  b->nbins = std::max<long long>(nbins, 1);
+  b->nconv = (int)conv.size();
+  b->nupd = (int)upd.size();
+  b->nall = (int)all.size();
+  b->npart = (int)part.size();
+  b->desc = batch_alloc(b, sizeof(InstDesc<T>) * n);
+  b->conv = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, conv.size())));
+  b->upd = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, upd.size())));
+  b->all = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, all.size())));
+  b->part = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, part.size())));
+  b->counts = static_cast<int*>(batch_alloc(b, sizeof(int) * b->nbins));
+  b->offsets = static_cast<int*>(batch_alloc(b, sizeof(int) * b->nbins));
+  b->tiles = static_cast<int*>(batch_alloc(b, sizeof(int) * (scan_tiles(b->nbins) + 1)));
+  b->pairs = static_cast<int*>(batch_alloc(b, sizeof(int) * std::max(1, b->npairs)));
+  // pair_base: npairs per-step bases, then pair_of_inst for every instance * 4 + species
+  b->pair_base = static_cast<int*>(batch_alloc(b, sizeof(int) * (b->npairs + 4 * n)));
+  if (!b->desc || !b->conv || !b->upd || !b->all || !b->part || !b->counts || !b->offsets || !b->tiles ||
+      !b->pairs || !b->pair_base)
+    return GRPIC_ERR_OOM;
+  std::vector<int> pair_of_inst(4 * n, 0);
+  for (int p = 0; p < b->npairs; ++p) pair_of_inst[pairs[p]] = p;
+  cudaStream_t st = b->stream;
+  cudaMemcpyAsync(b->desc, desc.data(), sizeof(InstDesc<T>) * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->conv, conv.data(), sizeof(BlockEntry) * conv.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->upd, upd.data(), sizeof(BlockEntry) * upd.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->all, all.data(), sizeof(BlockEntry) * all.size(), cudaMemcpyHostToDevice, st);
+  if (!part.empty())
+    cudaMemcpyAsync(b->part, part.data(), sizeof(BlockEntry) * part.size(), cudaMemcpyHostToDevice, st);
+  if (!pairs.empty()) cudaMemcpyAsync(b->pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->pair_base + b->npairs, pair_of_inst.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->cur, cur_init.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, st);
+  return cudaStreamSynchronize(st) == cudaSuccess ? GRPIC_OK : GRPIC_ERR_CUDA;
+}
+
+// One batched timestep (Sec. 2.2 for every instance): B half, J = 0, push + deposit, B half, E,
+// removal + sort.  Each stage is one launch over all instances.
+template <typename T>
+void batch_enqueue_step(grpic_batch* b) {
+  const BatchTables<T> t = batch_tables<T>(b);
+  launch_batch_b_half<T>(t, 0, b->literal, b->stream);
+  launch_batch_zero_j<T>(t, b->stream);
+  launch_batch_push<T>(t, b->quad, b->stream);
+  launch_batch_b_half<T>(t, 1, b->literal, b->stream);
+  launch_batch_e_step<T>(t, b->literal, b->stream);
+  launch_batch_sort<T>(t, b->stream);
+}
+
+}  // namespace
+
+extern "C" {
 
 grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grpic_batch** out) {
   (void)stream;
   if (!ctxs || n <= 0 || !out) return GRPIC_ERR_INVALID;
-  grpic_batch* b = new grpic_batch();
-  for (int i = 0; i < n; ++i) {
-    if (!ctxs[i]) {
-      delete b;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->mixed != ctxs[0]->mixed || ctxs[i]->g.quad_order != ctxs[0]->g.quad_order ||
+        literal_fields(ctxs[i]) != literal_fields(ctxs[0]))
       return GRPIC_ERR_INVALID;
-    }
-    b->ctxs.push_back(ctxs[i]);
+  grpic_batch* b = new grpic_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->mixed = ctxs[0]->mixed;
+  b->quad = ctxs[0]->g.quad_order;
+  b->literal = literal_fields(ctxs[0]);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->persist_blocks = std::max(1, sms) * 8;
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    grpic_batch_destroy(b);
+    return GRPIC_ERR_CUDA;
   }
+  for (grpic_ctx* c : b->ctxs) cudaStreamSynchronize(c->stream);
+  const grpic_status s = b->mixed ? batch_build<float>(b) : batch_build<double>(b);
+  if (s != GRPIC_OK) {
+    grpic_batch_destroy(b);
+    return s;
+  }
+  // kernels per step: B halves 2 x 2, zero J 1, push 1, E 2 or 4, sort 5 (+2 with particles; and 1 memset)
+  b->kernels_per_step =
+      4 + 1 + (b->npart > 0 ? 1 : 0) + (b->literal ? 2 : 4) + (b->npairs ? 5 + 2 * (b->npart > 0 ? 1 : 0) : 0);
   *out = b;
   return GRPIC_OK;
 }
 
 grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
   if (!b || nsteps < 0) return GRPIC_ERR_INVALID;
-  for (int s = 0; s < nsteps; ++s)
-    for (grpic_ctx* c : b->ctxs) enqueue_step(c);
+  // the batch was built for the particle counts of its creation
+  size_t p = 0;
+  for (grpic_ctx* c : b->ctxs)
+    for (int s = 0; s < kMaxSpecies; ++s)
+      if (c->sp[s].loaded && (p >= b->pair_n.size() || c->sp[s].n > b->pair_n[p++])) return GRPIC_ERR_INVALID;
+  // order after each context's pending work; refresh the device ping-pong indices
+  std::vector<int> cur(4 * b->ctxs.size(), 0);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    grpic_ctx* c = b->ctxs[i];
+    for (int s = 0; s < kMaxSpecies; ++s) cur[4 * i + s] = c->sp[s].cur;
+    cudaEventRecord(b->ev, c->stream);
+    cudaStreamWaitEvent(b->stream, b->ev, 0);
+  }
+  cudaMemcpyAsync(b->cur, cur.data(), sizeof(int) * cur.size(), cudaMemcpyHostToDevice, b->stream);
+  if (!b->graph) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GRPIC_ERR_CUDA;
+    if (b->mixed)
+      batch_enqueue_step<float>(b);
+    else
+      batch_enqueue_step<double>(b);
+    if (cudaStreamEndCapture(b->stream, &graph) != cudaSuccess || !graph) return GRPIC_ERR_CUDA;
+    const cudaError_t e = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return GRPIC_ERR_CUDA;
+  }
+  for (int k = 0; k < nsteps; ++k)
+    if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
+  cudaMemcpyAsync(cur.data(), b->cur, sizeof(int) * cur.size(), cudaMemcpyDeviceToHost, b->stream);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    grpic_ctx* c = b->ctxs[i];
+    c->steps += nsteps;
+    c->pushes += nsteps;
+    c->since_sort = 0;
+    c->launches += (long long)nsteps * b->kernels_per_step / (long long)b->ctxs.size();
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      c->sp[s].cur = cur[4 * i + s];
+      c->sp[s].shadow_pending = false;
+    }
+  }
   for (grpic_ctx* c : b->ctxs) {
-    grpic_status st = read_status(c);
+    const grpic_status st = read_status(c);
     if (st != GRPIC_OK) return st;
   }
   return GRPIC_OK;
 }
 
+grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t* work_blocks) {
+  if (!b) return GRPIC_ERR_INVALID;
+  if (kernels_per_step) *kernels_per_step = b->kernels_per_step;
+  if (work_blocks) *work_blocks = (int64_t)b->nconv + b->nupd + b->nall + b->npart;
+  return GRPIC_OK;
+}
+
 grpic_status grpic_batch_destroy(grpic_batch* b) {
   if (!b) return GRPIC_ERR_INVALID;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) dev_free(b->ctxs[0], p);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return GRPIC_OK;
 }

@@ -18,6 +18,7 @@
 // velocities, fields and arithmetic in FP32 except where the FP32 estimate of r is below
 // r_fp64 (default 4m): there the quartic, the metric and the Christoffel contraction are
 // evaluated again in FP64.  The global J accumulators are FP64 in both modes.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -257,14 +258,12 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
   }
 }
 
+// One particle-step of particle i: RK4 push, deposit, removal flag and sort key.
 template <typename T, int Q, bool MIXED>
-__global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fields<T> F, const Particles<T> P,
-                                                        const Species sp, DevStatus* st) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  unsigned flags = 0, n64 = 0;
-  bool active = i < P.n && i < (long long)(*P.n_dev);
-  if (active) active = P.key[i] != kDead;
-  if (active) {
+__device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F, const Particles<T>& P,
+                                              const Species& sp, long long i, DevStatus* st, unsigned& flags,
+                                              unsigned& n64) {
+  {
     Consts C;
     C.m = g.m;
     C.a = g.a;
@@ -360,7 +359,10 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
     }
     if (fb) atomicAdd(&st->fallbacks, 1ull);
   }
-  // one status update per warp
+}
+
+// Warp-aggregated status: flags, FP64 evaluations and particle-steps of the warp's lanes.
+__device__ __forceinline__ void warp_status(DevStatus* st, unsigned flags, unsigned n64, bool active) {
   const unsigned any_flags = __reduce_or_sync(0xffffffffu, flags);
   const unsigned sum64 = __reduce_add_sync(0xffffffffu, n64);
   const unsigned npush = __popc(__ballot_sync(0xffffffffu, active));
@@ -368,6 +370,37 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
     if (any_flags) atomicOr(&st->flags, any_flags);
     if (sum64) atomicAdd(&st->fp64_evals, (unsigned long long)sum64);
     if (npush) atomicAdd(&st->pushed, (unsigned long long)npush);
+  }
+}
+
+template <typename T, int Q, bool MIXED>
+__global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fields<T> F, const Particles<T> P,
+                                                           const Species sp, DevStatus* st) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned flags = 0, n64 = 0;
+  bool active = i < P.n && i < (long long)(*P.n_dev);
+  if (active) active = P.key[i] != kDead;
+  if (active) push_particle<T, Q, MIXED>(g, F, P, sp, i, st, flags, n64);
+  warp_status(st, flags, n64, active);
+}
+
+// Batched: grid-stride over (instance * 4 + species, block) work items; each block belongs to
+// one instance and species, so the warp-level status stays per instance.
+template <typename T, int Q, bool MIXED>
+__global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>* __restrict__ desc,
+                                                                 const BlockEntry* __restrict__ blk, int nblk) {
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const BlockEntry e = blk[bi];
+    const InstDesc<T>& D = desc[e.inst >> 2];
+    const SpeciesDesc<T>& S = D.sp[e.inst & 3];
+    const Particles<T>& P = S.buf[*S.cur];
+    const Species sp{S.qm, S.qmacro};
+    const long long i = (long long)e.block * blockDim.x + threadIdx.x;
+    unsigned flags = 0, n64 = 0;
+    bool active = i < P.n && i < (long long)(*P.n_dev);
+    if (active) active = P.key[i] != kDead;
+    if (active) push_particle<T, Q, MIXED>(D.g, D.F, P, sp, i, D.st, flags, n64);
+    warp_status(D.st, flags, n64, active);
   }
 }
 
@@ -485,6 +518,27 @@ template <>
 void launch_push_deposit<float>(const Grid& g, const Fields<float>& F, const Particles<float>& P,
                                 const Species& sp, DevStatus* st, bool, double, cudaStream_t stream) {
   if (P.n > 0) launch_push_q<float, true>(g, F, P, sp, st, stream);
+}
+
+template <typename T, bool MIXED>
+void launch_batch_push_q(const BatchTables<T>& bt, int quad_order, cudaStream_t stream) {
+  const unsigned nb = (unsigned)std::min(bt.npart, bt.persist_blocks);
+  if (bt.npart == 0) return;
+  if (quad_order == 1)
+    k_push_deposit_batch<T, 1, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+  else if (quad_order == 3)
+    k_push_deposit_batch<T, 3, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+  else
+    k_push_deposit_batch<T, 2, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+}
+
+template <>
+void launch_batch_push<double>(const BatchTables<double>& bt, int quad_order, cudaStream_t stream) {
+  launch_batch_push_q<double, false>(bt, quad_order, stream);
+}
+template <>
+void launch_batch_push<float>(const BatchTables<float>& bt, int quad_order, cudaStream_t stream) {
+  launch_batch_push_q<float, true>(bt, quad_order, stream);
 }
 
 template <typename T>

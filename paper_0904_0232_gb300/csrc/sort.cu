@@ -6,6 +6,8 @@
 //   3. scatter of x, u, id, key into the alternate buffers at bin offset + running count.
 // The live count (start of the removed bin) is left in device memory, so no host round
 // trip is needed between steps.  Within a cell the order is not stable.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace grpic {
@@ -123,6 +125,70 @@ __global__ void k_scatter(const Particles<T> src, const Particles<T> dst, int* _
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ---- batched: all (instance, species) pairs share one bin array -------------------------------
+template <typename T>
+__global__ void k_batch_hist(const InstDesc<T>* __restrict__ desc, const BlockEntry* __restrict__ blk, int nblk,
+                             int* __restrict__ counts) {
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const BlockEntry e = blk[bi];
+    const InstDesc<T>& D = desc[e.inst >> 2];
+    const SpeciesDesc<T>& S = D.sp[e.inst & 3];
+    const Particles<T>& P = S.buf[*S.cur];
+    const long long i = (long long)e.block * blockDim.x + threadIdx.x;
+    if (i >= P.n || i >= (long long)(*P.n_dev)) continue;
+    const uint32_t k = P.key[i];
+    atomicAdd(counts + S.bin_base + (k == kDead ? D.g.ncell : (long long)k), 1);
+  }
+}
+
+template <typename T>
+__global__ void k_batch_base(const InstDesc<T>* __restrict__ desc, const int* __restrict__ pairs, int npairs,
+                             const int* __restrict__ offsets, int* __restrict__ base) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const InstDesc<T>& D = desc[pairs[p] >> 2];
+  base[p] = offsets[D.sp[pairs[p] & 3].bin_base];
+}
+
+template <typename T>
+__global__ void k_batch_scatter(const InstDesc<T>* __restrict__ desc, const BlockEntry* __restrict__ blk, int nblk,
+                                const int* __restrict__ pair_of_inst, const int* __restrict__ base,
+                                int* __restrict__ cursor) {
+  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const BlockEntry e = blk[bi];
+    const InstDesc<T>& D = desc[e.inst >> 2];
+    const SpeciesDesc<T>& S = D.sp[e.inst & 3];
+    const int cur = *S.cur;
+    const Particles<T>& src = S.buf[cur];
+    const Particles<T>& dst = S.buf[1 - cur];
+    const long long i = (long long)e.block * blockDim.x + threadIdx.x;
+    if (i >= src.n || i >= (long long)(*src.n_dev)) continue;
+    const uint32_t k = src.key[i];
+    if (k == kDead) continue;
+    const int pos = atomicAdd(cursor + S.bin_base + k, 1) - base[pair_of_inst[e.inst]];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dst.x[q][pos] = src.x[q][i];
+      dst.u[q][pos] = src.u[q][i];
+    }
+    dst.id[pos] = src.id[i];
+    dst.key[pos] = k;
+  }
+}
+
+// live count and buffer flip of every pair (after the scatter has read the old index)
+template <typename T>
+__global__ void k_batch_finish(const InstDesc<T>* __restrict__ desc, const int* __restrict__ pairs, int npairs,
+                               const int* __restrict__ offsets, const int* __restrict__ base) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  const InstDesc<T>& D = desc[pairs[p] >> 2];
+  const SpeciesDesc<T>& S = D.sp[pairs[p] & 3];
+  const int cur = *S.cur;
+  *const_cast<int*>(S.buf[cur].n_dev) = offsets[S.bin_base + D.g.ncell] - base[p];  // shared by both buffers
+  *S.cur = 1 - cur;
+}
+
 }  // namespace
 
 int scan_tiles(long long nbins) { return (int)((nbins + kScanTile - 1) / kScanTile); }
@@ -143,6 +209,29 @@ void launch_sort(const Grid& g, const Particles<T>& src, const Particles<T>& dst
   if (src.n > 0) k_scatter<T><<<blocks_for(src.n, 256), 256, 0, stream>>>(src, dst, s.offsets, dead_bin);
   k_live_count<<<1, 1, 0, stream>>>(s.offsets, dead_bin, n_out);
 }
+
+// pair_of_inst: for each (instance * 4 + species) the index of its pair (stored after `base`).
+template <typename T>
+void launch_batch_sort(const BatchTables<T>& bt, cudaStream_t stream) {
+  if (bt.npairs == 0) return;
+  cudaMemsetAsync(bt.counts, 0, sizeof(int) * bt.nbins, stream);
+  const unsigned nb = (unsigned)std::min(bt.npart, bt.persist_blocks);
+  const int* pair_of_inst = bt.pair_base + bt.npairs;
+  if (bt.npart > 0) k_batch_hist<T><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, bt.counts);
+  const int ntiles = (int)((bt.nbins + kScanTile - 1) / kScanTile);
+  k_tile_sums<<<ntiles, kScanThreads, 0, stream>>>(bt.counts, bt.nbins, bt.tiles);
+  k_scan_tile_sums<<<1, kScanThreads, 0, stream>>>(bt.tiles, ntiles);
+  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(bt.counts, bt.nbins, bt.tiles, bt.offsets);
+  k_batch_base<T><<<blocks_for(bt.npairs, 128), 128, 0, stream>>>(bt.desc, bt.pairs, bt.npairs, bt.offsets,
+                                                                     bt.pair_base);
+  if (bt.npart > 0)
+    k_batch_scatter<T><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, pair_of_inst, bt.pair_base, bt.offsets);
+  k_batch_finish<T><<<blocks_for(bt.npairs, 128), 128, 0, stream>>>(bt.desc, bt.pairs, bt.npairs, bt.offsets,
+                                                                       bt.pair_base);
+}
+
+template void launch_batch_sort<float>(const BatchTables<float>&, cudaStream_t);
+template void launch_batch_sort<double>(const BatchTables<double>&, cudaStream_t);
 
 template void launch_sort<float>(const Grid&, const Particles<float>&, const Particles<float>&, const SortScratch&,
                                  int*, cudaStream_t);

@@ -80,6 +80,8 @@ EXPORTS = {
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grpic_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "grpic_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
 }
 
 _lib = None
@@ -297,6 +299,13 @@ def grpic_batch_create(ctxs, stream=None):
 
 def grpic_batch_step(b, nsteps):
     _check(None, load_library().grpic_batch_step(b, int(nsteps)), "grpic_batch_step")
+
+
+def grpic_batch_info(b):
+    k = ctypes.c_int64(0)
+    w = ctypes.c_int64(0)
+    _check(None, load_library().grpic_batch_info(b, ctypes.byref(k), ctypes.byref(w)), "grpic_batch_info")
+    return k.value, w.value
 
 
 def grpic_batch_destroy(b):

@@ -143,3 +143,39 @@ def random_fields(shape, seed, scale=0.05):
     d = rng.standard_normal((3,) + tuple(shape)) * scale
     b = rng.standard_normal((3,) + tuple(shape)) * scale
     return d, b
+
+
+@dataclasses.dataclass
+class InstanceSpec:
+    grid: int
+    ppc: int
+    m: float
+    a: float
+
+
+def batch_specs(n=64, seed=7, grids=(32, 48, 64, 96), ppc_range=(1, 32), m_range=(1.0, 4.0), spin_max=0.99):
+    """Parameters of n independent instances: grid drawn from `grids`, particles per cell per
+    species uniform in ppc_range, m uniform in m_range (cells), a uniform in [0, spin_max] m."""
+    rng = _rng(seed, 7)
+    out = []
+    for _ in range(n):
+        g = int(grids[rng.integers(0, len(grids))])
+        ppc = int(rng.integers(ppc_range[0], ppc_range[1] + 1))
+        m = float(rng.uniform(*m_range))
+        a = float(rng.uniform(0.0, spin_max)) * m
+        out.append(InstanceSpec(g, ppc, m, a))
+    return out
+
+
+def cell_major_pairs(n, ppc_max, u_th, c, seed):
+    """Pair-plasma draws for a grid of n^3 nodes with ppc_max particles in every cell of
+    [1, n-3]^3, laid out (3, ncell, ppc_max): positions (shared by both species, co-located
+    pairs) and covariant spatial momenta per species.  Taking [:, :, :ppc] gives ppc per cell."""
+    rng = _rng(seed, 1000 + n)
+    x = uniform_positions(rng, n, n, n, ppc_max)
+    ncell = x.shape[1] // ppc_max
+    theta = (u_th / c) ** 2
+    u0 = maxwell_juettner(_rng(seed, 2000 + n), x.shape[1], theta) * c
+    u1 = maxwell_juettner(_rng(seed, 3000 + n), x.shape[1], theta) * c
+    shape = (3, ncell, ppc_max)
+    return x.reshape(shape), u0.reshape(shape), u1.reshape(shape)
