@@ -385,22 +385,40 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
 }
 
 // Batched: grid-stride over (instance * 4 + species, block) work items; each block belongs to
-// one instance and species, so the warp-level status stays per instance.
+// one instance and species, so the warp-level status stays per instance.  The block's instance
+// descriptor is staged in shared memory and reloaded only when the instance changes (a CTA's
+// consecutive grid-stride blocks mostly stay inside one instance).
 template <typename T, int Q, bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>* __restrict__ desc,
                                                                  const BlockEntry* __restrict__ blk, int nblk) {
+  __shared__ Grid sg;
+  __shared__ Fields<T> sF;
+  __shared__ Particles<T> sP;
+  __shared__ Species ssp;
+  __shared__ DevStatus* sst;
+  int loaded = -1;
   for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
     const BlockEntry e = blk[bi];
-    const InstDesc<T>& D = desc[e.inst >> 2];
-    const SpeciesDesc<T>& S = D.sp[e.inst & 3];
-    const Particles<T>& P = S.buf[*S.cur];
-    const Species sp{S.qm, S.qmacro};
+    if (e.inst != loaded) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const InstDesc<T>& D = desc[e.inst >> 2];
+        const SpeciesDesc<T>& S = D.sp[e.inst & 3];
+        sg = D.g;
+        sF = D.F;
+        sP = S.buf[*S.cur];
+        ssp = Species{S.qm, S.qmacro};
+        sst = D.st;
+      }
+      __syncthreads();
+      loaded = e.inst;
+    }
     const long long i = (long long)e.block * blockDim.x + threadIdx.x;
     unsigned flags = 0, n64 = 0;
-    bool active = i < P.n && i < (long long)(*P.n_dev);
-    if (active) active = P.key[i] != kDead;
-    if (active) push_particle<T, Q, MIXED>(D.g, D.F, P, sp, i, D.st, flags, n64);
-    warp_status(D.st, flags, n64, active);
+    bool active = i < sP.n && i < (long long)(*sP.n_dev);
+    if (active) active = sP.key[i] != kDead;
+    if (active) push_particle<T, Q, MIXED>(sg, sF, sP, ssp, i, sst, flags, n64);
+    warp_status(sst, flags, n64, active);
   }
 }
 
