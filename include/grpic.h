@@ -250,6 +250,57 @@ grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t
 
 grpic_status grpic_batch_destroy(grpic_batch* b);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: a request loop over whole simulation runs (not in the paper).  Requests are queued
+ * by grpic_submit and admitted in arrival order when a slot is free and the run's device-memory
+ * estimate fits the budget; each admitted run gets its own context whose plasma is generated on
+ * the device; every grpic_server_tick advances all running runs by one timestep together (the
+ * batched engine, rebuilt when the set of running runs changes) and retires the finished ones.
+ * All runs of a server share precision, quadrature order and flags (those of the first request).
+ * ------------------------------------------------------------------------------------- */
+typedef struct grpic_server grpic_server;
+
+typedef struct {
+  grpic_config cfg;        /* grid, m, a, c, dt, precision, ... (the allocator fields are ignored) */
+  double E_contra[3];      /* initial uniform field (Eq. 8) */
+  double B_contra[3];
+  int nspecies;            /* 1..4 species, co-located at start */
+  double q_over_m[4];
+  double q_macro[4];
+  int ppc;                 /* particles per cell per species in the cells [1, n-3]^3 */
+  double u_th;             /* thermal spread: covariant u_i from Maxwell-Juettner, theta = (u_th/c)^2 */
+  double r_min;            /* no particles closer than r_min (Euclidean, cells) to the centre */
+  uint64_t seed;           /* the plasma is a function of (seed, species, cell, slot) only */
+  int nsteps;              /* timesteps to run */
+} grpic_request;
+
+enum { GRPIC_RUN_QUEUED = 0, GRPIC_RUN_RUNNING = 1, GRPIC_RUN_DONE = 2 };
+
+/* hbm_budget: bytes of device memory the running runs may use together (their estimates);
+ * max_slots: running runs at most; alloc/free/user: device allocator (NULL -> cudaMalloc). */
+grpic_status grpic_server_create(size_t hbm_budget, int max_slots, grpic_alloc_fn alloc, grpic_free_fn free_fn,
+                                 void* alloc_user, grpic_server** out);
+
+/* Queue a run; *ticket identifies it.  GRPIC_ERR_CAPACITY if it could never fit the budget,
+ * GRPIC_ERR_INVALID for a bad request or one whose precision/quadrature/flags differ. */
+grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* ticket);
+
+/* Admit what fits, advance every running run one timestep, retire finished runs.
+ * *running / *queued (may be NULL) receive the counts after the tick. */
+grpic_status grpic_server_tick(grpic_server* s, int* running, int* queued);
+
+/* State of a run (GRPIC_RUN_*); once done, *ctx (may be NULL) borrows its context (fields,
+ * particles, stats) until grpic_server_release. */
+grpic_status grpic_poll(grpic_server* s, uint64_t ticket, int* state, grpic_ctx** ctx);
+
+/* Free a finished run's context and forget the ticket. */
+grpic_status grpic_server_release(grpic_server* s, uint64_t ticket);
+
+/* Device-memory estimate of a request's run (what admission charges against the budget). */
+grpic_status grpic_request_bytes(const grpic_request* req, size_t* bytes);
+
+grpic_status grpic_server_destroy(grpic_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,16 @@ class grpic_config(ctypes.Structure):
                 ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
+class grpic_request(ctypes.Structure):
+    _fields_ = [("cfg", grpic_config), ("E_contra", ctypes.c_double * 3), ("B_contra", ctypes.c_double * 3),
+                ("nspecies", ctypes.c_int), ("q_over_m", ctypes.c_double * 4), ("q_macro", ctypes.c_double * 4),
+                ("ppc", ctypes.c_int), ("u_th", ctypes.c_double), ("r_min", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("nsteps", ctypes.c_int)]
+
+
+GRPIC_RUN_QUEUED, GRPIC_RUN_RUNNING, GRPIC_RUN_DONE = 0, 1, 2
+
+
 class grpic_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("removed_horizon", ctypes.c_int64), ("removed_outer", ctypes.c_int64),
                 ("gamma_fallbacks", ctypes.c_int64), ("fp64_evals", ctypes.c_int64),
@@ -76,6 +86,15 @@ EXPORTS = {
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "grpic_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ALLOC_FN, FREE_FN, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "grpic_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "grpic_server_tick": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "grpic_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "grpic_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "grpic_request_bytes": (ctypes.c_int, [ctypes.POINTER(grpic_request), ctypes.POINTER(ctypes.c_size_t)]),
+    "grpic_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "grpic_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -310,6 +329,73 @@ def grpic_batch_info(b):
 
 def grpic_batch_destroy(b):
     _check(None, load_library().grpic_batch_destroy(b), "grpic_batch_destroy")
+
+
+def grpic_server_create(hbm_budget, max_slots, torch_allocator=True):
+    h = ctypes.c_void_p()
+    alloc, free = (_torch_alloc, _torch_free) if torch_allocator else (ALLOC_FN(), FREE_FN())
+    _check(None, load_library().grpic_server_create(int(hbm_budget), int(max_slots), alloc, free, None,
+                                                    ctypes.byref(h)), "grpic_server_create")
+    return h.value
+
+
+def grpic_submit(server, req):
+    t = ctypes.c_uint64(0)
+    _check(None, load_library().grpic_submit(server, ctypes.byref(req), ctypes.byref(t)), "grpic_submit")
+    return t.value
+
+
+def grpic_server_tick(server):
+    r = ctypes.c_int(0)
+    q = ctypes.c_int(0)
+    _check(None, load_library().grpic_server_tick(server, ctypes.byref(r), ctypes.byref(q)), "grpic_server_tick")
+    return r.value, q.value
+
+
+def grpic_poll(server, ticket):
+    """(state, ctx handle or None); raises if the finished run failed."""
+    st = ctypes.c_int(0)
+    ctx = ctypes.c_void_p()
+    code = load_library().grpic_poll(server, int(ticket), ctypes.byref(st), ctypes.byref(ctx))
+    if code not in (GRPIC_OK, 7):
+        raise GrpicError(code, "grpic_poll")
+    return st.value, ctx.value
+
+
+def grpic_server_release(server, ticket):
+    _check(None, load_library().grpic_server_release(server, int(ticket)), "grpic_server_release")
+
+
+def grpic_request_bytes(req):
+    b = ctypes.c_size_t(0)
+    _check(None, load_library().grpic_request_bytes(ctypes.byref(req), ctypes.byref(b)), "grpic_request_bytes")
+    return b.value
+
+
+def grpic_server_destroy(server):
+    _check(None, load_library().grpic_server_destroy(server), "grpic_server_destroy")
+
+
+def make_request(n, m, a, ppc, nsteps, seed, precision="fp32_mixed", c=1.0, dt=0.4, B=(0.0, 0.0, 0.05),
+                 species=((-1.0,), (1.0,)), wp_dt=0.1, u_th=0.1, r_min=None, quad_order=2):
+    """A run request: n^3 grid, pair plasma (q/m = -1, +1) by default, macro charge for the
+    stated omega_p dt at ppc particles per cell per species."""
+    prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
+    qms = [sp[0] for sp in species]
+    q = (wp_dt / dt) ** 2 / (4.0 * np.pi * max(ppc, 1) * sum(abs(v) for v in qms))
+    req = grpic_request()
+    req.cfg = grpic_config(n, n, n, m, a, c, dt, prec, quad_order, 0.0, 0, 1, 0, 0.0)
+    req.B_contra[:] = list(B)
+    req.nspecies = len(qms)
+    for s_, qm in enumerate(qms):
+        req.q_over_m[s_] = qm
+        req.q_macro[s_] = float(np.sign(qm) * q)
+    req.ppc = ppc
+    req.u_th = u_th
+    req.r_min = 2.5 * m if r_min is None else r_min
+    req.seed = seed
+    req.nsteps = nsteps
+    return req
 
 
 # ---- convenience wrapper -----------------------------------------------------------------------

@@ -1,0 +1,104 @@
+"""Serving: runs admitted by the library's server (device-memory budget, slots), resident on
+the device, advanced together one batched timestep per tick.
+
+* a run's result is the same alone and in a mix of runs that arrive before and after it
+  (J is accumulated with atomics, so within the parity tolerances rather than bitwise);
+* admission waits for memory: with a budget for one run, the second stays queued until the
+  first is released;
+* requests that could never fit, or that differ in precision, are refused.
+"""
+import numpy as np
+import pytest
+
+from parity_util import TOL, rel_l2
+from paper_0904_0232_gb300.grpic import (GRPIC_RUN_DONE, GRPIC_RUN_QUEUED, GRPIC_RUN_RUNNING, GrpicError,
+                                         grpic_get_fields, grpic_get_particles, grpic_poll, grpic_request_bytes,
+                                         grpic_server_create, grpic_server_destroy, grpic_server_release,
+                                         grpic_server_tick, grpic_submit, make_request)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _run_to_done(server, ticket, max_ticks=1000):
+    for _ in range(max_ticks):
+        state, ctx = grpic_poll(server, ticket)
+        if state == GRPIC_RUN_DONE:
+            return ctx
+        grpic_server_tick(server)
+    raise AssertionError("run did not finish")
+
+
+def _snapshot(ctx, n):
+    parts = [grpic_get_particles(ctx, s) for s in range(2)]
+    return parts, grpic_get_fields(ctx, (n, n, n))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_same_result_alone_and_in_a_mix(prec):
+    A = dict(n=24, m=1.5, a=1.2, ppc=2, nsteps=6, seed=11, precision=prec)
+    alone = grpic_server_create(int(4e9), 8)
+    ta = grpic_submit(alone, make_request(**A))
+    res_alone = _snapshot(_run_to_done(alone, ta), 24)
+
+    mix = grpic_server_create(int(4e9), 8)
+    tb = grpic_submit(mix, make_request(n=20, m=1.0, a=0.3, ppc=1, nsteps=3, seed=12, precision=prec))
+    grpic_server_tick(mix)
+    ta2 = grpic_submit(mix, make_request(**A))
+    grpic_server_tick(mix)
+    tc = grpic_submit(mix, make_request(n=28, m=2.0, a=1.9, ppc=2, nsteps=10, seed=13, precision=prec))
+    res_mix = _snapshot(_run_to_done(mix, ta2), 24)
+    for tk in (tb, tc):
+        _run_to_done(mix, tk)
+
+    tol = TOL[prec]
+    factor = 1.0 if prec == "fp64" else 16.0
+    for s in range(2):
+        (xa, ua, ia), (xb, ub, ib) = res_alone[0][s], res_mix[0][s]
+        oa, ob = np.argsort(ia), np.argsort(ib)
+        assert ia.size > 100 and np.array_equal(ia[oa], ib[ob])
+        assert np.abs(xa[:3, oa] - xb[:3, ob]).max() <= tol["particles"] * factor * np.abs(xa[:3]).max()
+        assert np.abs(ua[:, oa] - ub[:, ob]).max() <= tol["particles"] * factor * np.abs(ua).max()
+    (da, ba, Ja), (db, bb, Jb) = res_alone[1], res_mix[1]
+    assert rel_l2(Jb, Ja) <= tol["J"] * factor and rel_l2(bb, ba) <= tol["fields"] * factor
+    grpic_server_destroy(alone)
+    grpic_server_destroy(mix)
+
+
+def test_admission_waits_for_memory():
+    req = make_request(n=24, m=1.5, a=0.5, ppc=2, nsteps=4, seed=21)
+    one = grpic_request_bytes(req)
+    server = grpic_server_create(int(one * 1.5), 8)
+    t1 = grpic_submit(server, req)
+    t2 = grpic_submit(server, make_request(n=24, m=1.5, a=0.5, ppc=2, nsteps=4, seed=22))
+    running, queued = grpic_server_tick(server)
+    assert (running, queued) == (1, 1)
+    assert grpic_poll(server, t2)[0] == GRPIC_RUN_QUEUED
+    _run_to_done(server, t1)
+    # finished but not released: its memory is still held, so the second run cannot start
+    grpic_server_tick(server)
+    assert grpic_poll(server, t2)[0] == GRPIC_RUN_QUEUED
+    grpic_server_release(server, t1)
+    grpic_server_tick(server)
+    assert grpic_poll(server, t2)[0] in (GRPIC_RUN_RUNNING, GRPIC_RUN_DONE)
+    _run_to_done(server, t2)
+    grpic_server_destroy(server)
+
+
+def test_refused_requests():
+    server = grpic_server_create(int(1e6), 4)
+    with pytest.raises(GrpicError) as ei:
+        grpic_submit(server, make_request(n=64, m=2.0, a=1.0, ppc=8, nsteps=4, seed=1))
+    assert ei.value.code == 8
+    grpic_server_destroy(server)
+    server = grpic_server_create(int(4e9), 4)
+    grpic_submit(server, make_request(n=20, m=1.0, a=0.5, ppc=1, nsteps=2, seed=1, precision="fp32_mixed"))
+    with pytest.raises(GrpicError):
+        grpic_submit(server, make_request(n=20, m=1.0, a=0.5, ppc=1, nsteps=2, seed=2, precision="fp64"))
+    grpic_server_destroy(server)
