@@ -52,7 +52,7 @@ PUSH_TRAFFIC = {"sha": "b10997ac32049e48", "bytes_per_particle": 1223.29e6 / 15.
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("push.cu", "metric.cuh", "common.cuh"):
+    for f in ("push.cu", "push_far.cu", "push_core.cuh", "metric.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_0904_0232_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -73,6 +73,9 @@ def parse():
     p.add_argument("--workload", choices=["kerr128", "batch"], default="kerr128",
                    help="kerr128: the single-instance Kerr electron-ion workload; batch: many small "
                         "instances advanced by the batched engine")
+    p.add_argument("--single-kernel-steps", type=int, default=20,
+                   help="steps of the comparison run with the single mixed push kernel; 0 skips it")
+    p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
     p.add_argument("--batch-n", type=int, default=64)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -229,13 +232,15 @@ def run_reference(args, dist):
 
 
 # ---- GPU arm ------------------------------------------------------------------------------------
-def make_sim(wl, precision, args, device_inputs=True, fp64_radius=0.0):
+def make_sim(wl, precision, args, device_inputs=True, fp64_radius=0.0, flags=0, tuning=None):
     import torch
 
     from paper_0904_0232_gb300.grpic import GRPIC_U_COV_SPATIAL, Simulation
 
     sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=args.quad,
-                     sort_interval=args.sort_interval, fp64_radius=fp64_radius)
+                     sort_interval=args.sort_interval, fp64_radius=fp64_radius, flags=flags)
+    if tuning is not None:
+        sim.set_tuning(**tuning)
     sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
     for s, sp in enumerate(wl.species):
         if device_inputs:
@@ -278,14 +283,19 @@ def run_gpu(args, dist):
 
     from paper_0904_0232_gb300 import synth
     from paper_0904_0232_gb300.build import build
-    from paper_0904_0232_gb300.grpic import GRPIC_FP32_MIXED, grpic_probe_fma_peak
+    from paper_0904_0232_gb300 import autotune
+    from paper_0904_0232_gb300.grpic import GRPIC_FP32_MIXED, GRPIC_SINGLE_PUSH_KERNEL, grpic_probe_fma_peak
 
     torch.cuda.set_device(dist.local)
     build()
     wl = synth.kerr_ion_electron_128(seed=2, n=args.grid)
 
-    # --- FP32-mixed, inputs resident in HBM
+    # --- FP32-mixed, inputs resident in HBM; launch shapes from the autotuner (untimed)
     sim = make_sim(wl, "fp32_mixed", args)
+    if args.no_tune:
+        tuned = {"tuning": sim.tuning(), "cached": False, "trials": 0, "ms_per_step": None}
+    else:
+        tuned = autotune.tune(sim, f"kerr_ion_electron_{args.grid}|Q{args.quad}|{wl.n_particles}", steps=4)
     sim.set_profiling(True)
     sim.step(args.warmup)
     clocks = Clocks(dist.local)
@@ -325,10 +335,25 @@ def run_gpu(args, dist):
                 "ms_per_step": ms64 / args.fp64_steps,
                 "push_ms_per_step": prof64["push_deposit"][0] / args.fp64_steps}
 
+    # --- the same workload pushed by the single mixed-precision kernel (no near/far split)
+    single = None
+    if args.single_kernel_steps > 0:
+        sim1 = make_sim(wl, "fp32_mixed", args, flags=GRPIC_SINGLE_PUSH_KERNEL, tuning=tuned["tuning"])
+        sim1.set_profiling(True)
+        sim1.step(1)
+        ms1, ps1, prof1, _ = timed_steps(sim1, args.single_kernel_steps, dist)
+        sim1.close()
+        del sim1
+        torch.cuda.empty_cache()
+        single = {"value": dist.sum(ps1) / (dist.max(ms1) * 1e-3), "unit": UNIT, "steps": args.single_kernel_steps,
+                  "ms_per_step": ms1 / args.single_kernel_steps,
+                  "push_ms_per_step": prof1["push_deposit"][0] / args.single_kernel_steps,
+                  "note": "GRPIC_SINGLE_PUSH_KERNEL: every particle through the one mixed kernel"}
+
     # --- the same workload with the FP64 region switched off (all-FP32 metric evaluations)
     fp32_all = None
     if args.fp32_compare_steps > 0:
-        sim32 = make_sim(wl, "fp32_mixed", args, fp64_radius=-1.0)
+        sim32 = make_sim(wl, "fp32_mixed", args, fp64_radius=-1.0, tuning=tuned["tuning"])
         sim32.set_profiling(True)
         sim32.step(1)
         ms32, ps32, prof32, _ = timed_steps(sim32, args.fp32_compare_steps, dist)
@@ -347,7 +372,7 @@ def run_gpu(args, dist):
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim = make_sim(wl, "fp32_mixed", args, device_inputs=False)
+        sim = make_sim(wl, "fp32_mixed", args, device_inputs=False, tuning=tuned["tuning"])
         d_h2d = sum(sp.x4.nbytes + sp.usp.nbytes * 4 // 3 + sp.ids.nbytes for sp in wl.species)
         sim.step_async(args.steps)
         out_bytes = 0
@@ -378,17 +403,21 @@ def run_gpu(args, dist):
         "data": "synthetic (seeded generator; stands in for the paper's disk/corona plasma)",
         "config": {"workload": f"kerr_ion_electron_{args.grid}: Kerr a=0.9m, m=4 cells, {args.grid}^3 grid, "
                                "e-/ion (mass ratio 20), 8 ppc per species, u_th=0.05c, B_z=0.1, dt=0.4",
-                   "particles": wl.n_particles, "quad_order": args.quad, "sort_interval": args.sort_interval,
+                   "particles": wl.n_particles, "quad_order": args.quad,
+                   "tuning": dict(tuned["tuning"], autotuned=not args.no_tune, cached=tuned["cached"],
+                                  trials=tuned["trials"]),
                    "parallelism": f"replicas x{dist.world}",
                    "l2": "inputs larger than L2 (particle store %.2f GB)" % (wl.n_particles * 40 / 1e9)},
         "gpu_launches": int(launches),
         "stage_ms_per_step": stage_ms,
-        "roofline": {"kernel": "k_push_deposit (FP32-mixed)", "bound": "alu", "achieved": achieved / 1e12,
+        "roofline": {"kernel": "push stage: k_classify_near, then k_push_far (FP32) overlapped with k_push_near "
+                               "(FP32-mixed) on a second stream", "bound": "alu", "achieved": achieved / 1e12,
                      "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_NOMINAL,
                      "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)",
                      "fma_probe_tflops": fp32_probe / 1e12,
                      "flops_per_particle_step": ALG_FLOPS[args.quad], "kernel_sha": sha},
         "fp64": fp64,
+        "single_push_kernel": single,
         "fp32_no_fp64_region": fp32_all,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -407,8 +436,10 @@ def run_batch(args, dist):
 
     from paper_0904_0232_gb300 import synth
     from paper_0904_0232_gb300.build import build
+    from paper_0904_0232_gb300 import autotune
     from paper_0904_0232_gb300.grpic import (GRPIC_U_COV_SPATIAL, Simulation, grpic_batch_create,
-                                             grpic_batch_destroy, grpic_batch_info, grpic_batch_step)
+                                             grpic_batch_destroy, grpic_batch_info, grpic_batch_set_blocks_per_sm,
+                                             grpic_batch_step)
 
     torch.cuda.set_device(dist.local)
     build()
@@ -443,6 +474,18 @@ def run_batch(args, dist):
 
     b = grpic_batch_create([s.handle for s in sims])
     kps, blocks = grpic_batch_info(b)
+
+    def run_steps(k):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        grpic_batch_step(b, k)
+        return 1e3 * (time.perf_counter() - t)
+
+    if args.no_tune:
+        tuned = {"tuning": {"batch_blocks_per_sm": 8}, "cached": False, "trials": 0}
+    else:
+        tuned = autotune.tune_batch(run_steps, lambda v: grpic_batch_set_blocks_per_sm(b, v),
+                                    f"batch{len(specs)}|Q{args.quad}|{npart}")
     grpic_batch_step(b, args.warmup)
     p0 = psteps()
     torch.cuda.synchronize()
@@ -470,6 +513,8 @@ def run_batch(args, dist):
             "config": {"workload": f"batch of {len(specs)} instances: grids 32^3-96^3, 1-32 ppc per species, "
                                    "m 1-4 cells, a 0-0.99 m, pair plasma, B_z=0.05, dt=0.4, omega_p dt=0.1",
                        "particles": npart, "kernels_per_step": kps, "work_blocks": blocks,
+                       "tuning": dict(tuned["tuning"], autotuned=not args.no_tune, cached=tuned["cached"],
+                                      trials=tuned["trials"]),
                        "timing": "host wall clock around synchronising graph replays"},
             "sequential": {"value": sequential, "unit": UNIT, "steps": seq_steps,
                            "note": "the same contexts stepped one after another (non-batched launches)"},

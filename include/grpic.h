@@ -57,8 +57,10 @@ typedef enum {
 enum { GRPIC_FP64 = 0, GRPIC_FP32_MIXED = 1 };
 
 enum {
-  GRPIC_NO_GAMMA_IN_J = 1u,     /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
-  GRPIC_LITERAL_HALF_STEPS = 2u /* field update with each half-step explicit in its own start value (see below) */
+  GRPIC_NO_GAMMA_IN_J = 1u,      /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
+  GRPIC_LITERAL_HALF_STEPS = 2u, /* field update with each half-step explicit in its own start value (see below) */
+  GRPIC_SINGLE_PUSH_KERNEL = 4u  /* FP32_MIXED: push every particle with the one mixed-precision kernel instead
+                                    of the near/far split (see grpic_tuning); same arithmetic, for comparison */
 };
 
 enum { GRPIC_MEM_HOST = 0, GRPIC_MEM_DEVICE = 1 };
@@ -161,7 +163,9 @@ grpic_status grpic_step(grpic_ctx* ctx, int nsteps);
 /* As grpic_step, without the final synchronisation; errors surface at the next grpic_sync. */
 grpic_status grpic_step_async(grpic_ctx* ctx, int nsteps);
 
-/* Run one stage of the timestep (GRPIC_STAGE_*), then synchronise. */
+/* Run one stage of the timestep (GRPIC_STAGE_*), then synchronise.  Driving the stages by hand
+ * leaves the removal to the caller: particles flagged by a GRPIC_STAGE_PUSH_DEPOSIT (r <= r_+ or
+ * outside the grid) stay listed, at the position the push gave them, until GRPIC_STAGE_SORT. */
 grpic_status grpic_stage(grpic_ctx* ctx, int stage);
 
 /* Wait for the context's stream and report the device status. */
@@ -173,7 +177,8 @@ grpic_status grpic_get_fields(grpic_ctx* ctx, double* d3, double* b3, double* J3
 /* Number of live particles of a species. */
 grpic_status grpic_num_particles(grpic_ctx* ctx, int species, int64_t* n);
 
-/* Copy out the live particles of a species in the library's (cell-sorted) order, with ids.
+/* Copy out the live particles of a species in the library's (cell-sorted) order, with ids
+ * (after grpic_step; after hand-driven stages, the particles listed since the last sort stage).
  * *n_inout: capacity of the caller's arrays on entry, particles written on return.
  * x^4 is returned as the particle's own clock coordinate. */
 grpic_status grpic_get_particles(grpic_ctx* ctx, int species, int64_t* n_inout, double* x4, double* u4,
@@ -195,11 +200,47 @@ grpic_status grpic_set_profiling(grpic_ctx* ctx, int on);
 grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t counts[6], int64_t* kernel_launches,
                                int reset);
 
+/* Launch-shape choices of a context (not in the paper; what the autotuner chooses).
+ * FP32_MIXED contexts split the push in two: a classification lists the particles with
+ * R(x_n) < r_fp64 + |a| + 4 cells (each of their RK4 stages and quadrature nodes may fall
+ * inside r < r_fp64, where the FP64 policy applies), a near-hole kernel pushes those on a
+ * second, higher-priority stream while an FP32-only kernel pushes the rest.
+ *   far_min_blocks:     4, 5 or 6 resident 128-thread blocks per SM for the far kernel at Q = 2
+ *                       (register budget 128, 96, 80 per thread); other Q always use 5
+ *   near_blocks_per_sm: persistent blocks per SM of the near-hole kernel (>= 1)
+ *   sort_interval:      counting sort every k timesteps (>= 1)
+ *   overlap:            1: the near-hole kernel runs on the second stream alongside the far kernel;
+ *                       0: after it, on the context stream
+ * grpic_set_tuning validates all four (GRPIC_ERR_INVALID) and applies them from the next step. */
+typedef struct {
+  int far_min_blocks;
+  int near_blocks_per_sm;
+  int sort_interval;
+  int overlap;
+} grpic_tuning;
+grpic_status grpic_set_tuning(grpic_ctx* ctx, const grpic_tuning* t);
+grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);
+
 /* Measure the sustained fused-multiply-add rate of this GPU's CUDA cores (not the tensor
  * cores) with independent FMA chains in every lane: precision GRPIC_FP32_MIXED measures FP32,
  * GRPIC_FP64 measures FP64.  *flops_per_s counts an FMA as two operations.  Used as the
  * roofline denominator of the ALU-bound push. */
 grpic_status grpic_probe_fma_peak(int precision, double* flops_per_s);
+
+/* Self-check of the FP64 reciprocal, quotient and square root that the FP32-mixed policy uses
+ * for its FP64 evaluations near the hole (Newton's iteration for 1/x, Heron's correction for
+ * sqrt x, seeded by the PTX approximate instructions; their results are rounded to FP32).
+ * Compares them on the current device with the IEEE operations over n log-uniform arguments in
+ * [1e-8, 1e8] and returns the largest relative deviations: max_rel[0] 1/x, [1] y/x, [2] sqrt x. */
+grpic_status grpic_check_newton64(int64_t n, double max_rel[3]);
+
+/* Self-check of the integer-only FP32 -> FP64 widening and FP64 -> FP32 narrowing (round to
+ * nearest even) that the FP32-mixed push uses instead of the hardware conversions (which run on
+ * this GPU's FP64 pipe): over n pseudo-random bit patterns it counts, on the current device,
+ * results that differ bit for bit from the hardware conversions -- mismatches[0] widening
+ * (normal, infinite and NaN floats), mismatches[1] narrowing (doubles around and inside the
+ * binary32 normal range, a quarter of them exact ties). */
+grpic_status grpic_check_conversions(int64_t n, int64_t mismatches[2]);
 
 /* Sort a particle set by cell without allocating any device memory.  The paper has no
  * counterpart: this is the library's counting sort offered to callers that cannot allocate at
@@ -247,6 +288,10 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps);
 
 /* Kernels launched per batched step, and the total number of work blocks in the stage tables. */
 grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t* work_blocks);
+
+/* Persistent blocks per SM of the batch's launches (1..32, default 8; what the autotuner
+ * chooses).  Takes effect at the next grpic_batch_step, which captures the graph again. */
+grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm);
 
 grpic_status grpic_batch_destroy(grpic_batch* b);
 

@@ -13,13 +13,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrpic.so")
-SOURCES = ["grpic.cu", "fields.cu", "push.cu", "sort.cu", "peak.cu", "static_sort.cu", "server.cu"]
-HEADERS = ["common.cuh", "metric.cuh"]
+SOURCES = ["grpic.cu", "fields.cu", "push.cu", "push_far.cu", "sort.cu", "peak.cu", "static_sort.cu", "server.cu"]
+HEADERS = ["common.cuh", "metric.cuh", "push_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 path of the push tolerates the hardware's approximate single-precision divide and
 # square root (1-2 ulp): measured particle-state errors stay ~1e-7 against the FP64 oracle,
 # 20x inside the 2e-6 bound.  FP64 arithmetic is unaffected by these flags.
-PER_FILE_FLAGS = {"push.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
+PER_FILE_FLAGS = {src: ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"] for src in ("push.cu", "push_far.cu")}
 
 
 def nvcc() -> str:

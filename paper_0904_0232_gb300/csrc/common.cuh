@@ -7,6 +7,9 @@
 namespace grpic {
 
 constexpr uint32_t kDead = 0xffffffffu;  // sort key of a removed particle
+// Transient key of a particle handed to the near-hole pass of the split FP32-mixed push (set
+// by the classification, overwritten by the push); cell keys stay below 2^31.
+constexpr uint32_t kNear = 0xfffffffeu;
 
 // Device status word (sticky until read by the host).
 enum : unsigned {
@@ -93,6 +96,21 @@ struct Species {
 template <typename T>
 void launch_push_deposit(const Grid& g, const Fields<T>& F, const Particles<T>& P, const Species& sp,
                          DevStatus* st, bool mixed, double t_offset, cudaStream_t stream);
+
+// Split FP32-mixed push.  near_radius: particles with R(x_n) below it are classified near
+// (marked kNear, listed) and pushed by launch_push_near (grid-stride over the list, nblocks
+// blocks; new sort keys to keys[slot]); the rest by launch_push_far (FP32 only; minb selects
+// the register budget), concurrently.  launch_near_keys then copies keys[slot] to P.key.
+double near_radius(const Grid& g);
+void launch_classify_near(const Grid& g, const Particles<float>& P, uint32_t* list, int* count,
+                          cudaStream_t stream);
+void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
+                     DevStatus* st, int minb, cudaStream_t stream);
+void launch_push_near(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
+                      DevStatus* st, const uint32_t* list, uint32_t* keys, const int* count, int nblocks,
+                      cudaStream_t stream);
+void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uint32_t* keys, const int* count,
+                      int nblocks, cudaStream_t stream);
 
 template <typename T>
 void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,

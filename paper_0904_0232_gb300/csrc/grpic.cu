@@ -27,6 +27,7 @@ struct SpeciesStore {
   int cur = 0;
   int* n_dev = nullptr;
   int* n_shadow = nullptr;  // pinned host copy of n_dev
+  int* near_n = nullptr;    // split push: length of the near-hole list (device)
   cudaEvent_t shadow_ev = nullptr;
   bool shadow_pending = false;
   bool loaded = false;
@@ -42,6 +43,11 @@ struct grpic_ctx {
   bool mixed = false;
   size_t tsize = 8;
   std::string err;
+  // split FP32-mixed push: second stream (higher priority) and its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int sms = 0;
+  grpic_tuning tune{4, 4, 1, 1};
   void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T
@@ -145,6 +151,71 @@ void refresh_count(SpeciesStore& S) {
 
 bool literal_fields(const grpic_ctx* c) { return (c->cfg.flags & GRPIC_LITERAL_HALF_STEPS) != 0; }
 
+bool split_push(const grpic_ctx* c) {
+  return c->mixed && c->g.r_fp64 > 0.0 && !(c->cfg.flags & GRPIC_SINGLE_PUSH_KERNEL);
+}
+
+void enqueue_far(grpic_ctx* c, const Fields<float>& F) {
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    launch_push_far(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
+                    c->tune.far_min_blocks, c->stream);
+    c->launches += 1;
+  }
+}
+
+// Split FP32-mixed push: classify every species on the context stream, then the near-hole
+// kernels on the side stream and the far kernels on the context stream, joined at the end, and
+// the near particles' sort keys copied into place (with tune.overlap = 0: far kernels, then
+// near kernels, all on the context stream).  The near list and the near kernel's keys
+// live in the key and id planes of the idle ping-pong buffer (written again only by the next
+// sort, which follows the push).
+void enqueue_split_push(grpic_ctx* c) {
+  Fields<float> F = fields_view<float>(c);
+  bool any = false;
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    refresh_count(S);
+    cudaMemsetAsync(S.near_n, 0, sizeof(int), c->stream);
+    launch_classify_near(c->g, particles_view<float>(c, s, S.cur), particles_view<float>(c, s, 1 - S.cur).key,
+                         S.near_n, c->stream);
+    c->launches += 1;
+    any = true;
+  }
+  if (!any) return;
+  const bool overlap = c->tune.overlap != 0;
+  cudaStream_t near_stream = overlap ? c->side : c->stream;
+  if (overlap) {
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  } else {
+    enqueue_far(c, F);
+  }
+  const int nb = c->sms * c->tune.near_blocks_per_sm;
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    const Particles<float> idle = particles_view<float>(c, s, 1 - S.cur);
+    launch_push_near(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st, idle.key,
+                     idle.id, S.near_n, nb, near_stream);
+    c->launches += 1;
+  }
+  if (overlap) {
+    enqueue_far(c, F);
+    cudaEventRecord(c->ev_join, c->side);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  }
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    const Particles<float> idle = particles_view<float>(c, s, 1 - S.cur);
+    launch_near_keys(particles_view<float>(c, s, S.cur), idle.key, idle.id, S.near_n, c->sms * 2, c->stream);
+    c->launches += 1;
+  }
+}
+
 template <typename T>
 void enqueue_stage(grpic_ctx* c, int stage) {
   Fields<T> F = fields_view<T>(c);
@@ -158,13 +229,17 @@ void enqueue_stage(grpic_ctx* c, int stage) {
       cudaMemsetAsync(c->J, 0, sizeof(double) * 3 * (size_t)c->g.ncell, c->stream);
       break;
     case GRPIC_STAGE_PUSH_DEPOSIT:
-      for (int s = 0; s < kMaxSpecies; ++s) {
-        SpeciesStore& S = c->sp[s];
-        if (!S.loaded || S.n == 0) continue;
-        refresh_count(S);
-        Species spc{S.qm, S.qmacro};
-        launch_push_deposit<T>(c->g, F, particles_view<T>(c, s, S.cur), spc, c->st, c->mixed, 0.0, c->stream);
-        c->launches += 1;
+      if (split_push(c)) {
+        enqueue_split_push(c);
+      } else {
+        for (int s = 0; s < kMaxSpecies; ++s) {
+          SpeciesStore& S = c->sp[s];
+          if (!S.loaded || S.n == 0) continue;
+          refresh_count(S);
+          Species spc{S.qm, S.qmacro};
+          launch_push_deposit<T>(c->g, F, particles_view<T>(c, s, S.cur), spc, c->st, c->mixed, 0.0, c->stream);
+          c->launches += 1;
+        }
       }
       c->pushes += 1;
       break;
@@ -241,7 +316,7 @@ void enqueue_step(grpic_ctx* c) {
   enqueue_stage_any(c, GRPIC_STAGE_B_HALF2);
   enqueue_stage_any(c, GRPIC_STAGE_E);
   c->steps += 1;
-  if (++c->since_sort >= std::max(1, c->cfg.sort_interval)) {
+  if (++c->since_sort >= std::max(1, c->tune.sort_interval)) {
     enqueue_stage_any(c, GRPIC_STAGE_SORT);
     c->since_sort = 0;
   }
@@ -370,11 +445,21 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   bool ok = c->fields && c->J && c->mc && c->mask && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
   for (int s = 0; s < kMaxSpecies && ok; ++s) {
     c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
-    ok = c->sp[s].n_dev != nullptr;
+    c->sp[s].near_n = static_cast<int*>(dev_alloc(c, sizeof(int)));
+    ok = c->sp[s].n_dev != nullptr && c->sp[s].near_n != nullptr;
     if (ok) ok = cudaMallocHost(&c->sp[s].n_shadow, sizeof(int)) == cudaSuccess;
     if (ok) ok = cudaEventCreateWithFlags(&c->sp[s].shadow_ev, cudaEventDisableTiming) == cudaSuccess;
   }
   if (ok) ok = cudaMallocHost(&c->st_host, sizeof(DevStatus)) == cudaSuccess;
+  if (ok) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    ok = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess;
+  }
+  c->tune.sort_interval = c->cfg.sort_interval;
   if (!ok) {
     grpic_destroy(c);
     return GRPIC_ERR_OOM;
@@ -412,10 +497,17 @@ grpic_status grpic_destroy(grpic_ctx* c) {
     dev_free(c, c->sp[s].buf[0]);
     dev_free(c, c->sp[s].buf[1]);
     dev_free(c, c->sp[s].n_dev);
+    dev_free(c, c->sp[s].near_n);
     if (c->sp[s].n_shadow) cudaFreeHost(c->sp[s].n_shadow);
     if (c->sp[s].shadow_ev) cudaEventDestroy(c->sp[s].shadow_ev);
   }
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto& p : c->pending) {
     c->ev_pool.push_back(p.a);
     c->ev_pool.push_back(p.b);
@@ -692,6 +784,22 @@ grpic_status grpic_get_stats(grpic_ctx* c, grpic_stats* out) {
   return GRPIC_OK;
 }
 
+grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
+  if (!c || !t) return GRPIC_ERR_INVALID;
+  if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
+      t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1))
+    return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
+  c->tune = *t;
+  c->cfg.sort_interval = t->sort_interval;
+  return GRPIC_OK;
+}
+
+grpic_status grpic_get_tuning(const grpic_ctx* c, grpic_tuning* t) {
+  if (!c || !t) return GRPIC_ERR_INVALID;
+  *t = c->tune;
+  return GRPIC_OK;
+}
+
 grpic_status grpic_set_profiling(grpic_ctx* c, int on) {
   if (!c) return GRPIC_ERR_INVALID;
   c->profiling = on != 0;
@@ -736,6 +844,7 @@ struct grpic_batch {
   long long nbins = 0;
   int npairs = 0;
   int persist_blocks = 0;
+  int sms = 1;
   std::vector<long long> pair_n;  // work upper bound of each pair when the batch was built
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev = nullptr;
@@ -887,7 +996,8 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->persist_blocks = std::max(1, sms) * 8;
+  b->sms = std::max(1, sms);
+  b->persist_blocks = b->sms * 8;
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
     grpic_batch_destroy(b);
@@ -952,6 +1062,18 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
   for (grpic_ctx* c : b->ctxs) {
     const grpic_status st = read_status(c);
     if (st != GRPIC_OK) return st;
+  }
+  return GRPIC_OK;
+}
+
+grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm) {
+  if (!b || blocks_per_sm < 1 || blocks_per_sm > 32) return GRPIC_ERR_INVALID;
+  if (b->persist_blocks == b->sms * blocks_per_sm) return GRPIC_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->persist_blocks = b->sms * blocks_per_sm;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;  // re-captured with the new grid by the next grpic_batch_step
   }
   return GRPIC_OK;
 }

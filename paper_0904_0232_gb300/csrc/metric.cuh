@@ -13,6 +13,43 @@
 
 namespace grpic {
 
+// Division and square root used by the metric functions.  IeeeOps is the compiler's own
+// operators (the default everywhere); a caller that needs less than full precision can pass a
+// cheaper policy with the same three members.
+struct IeeeOps {
+  template <typename S>
+  __device__ static __forceinline__ S rcp(S x) { return S(1) / x; }
+  template <typename S>
+  __device__ static __forceinline__ S div(S a, S b) { return a / b; }
+  template <typename S>
+  __device__ static __forceinline__ S root(S x) { return sqrt(x); }
+};
+
+// FP64 reciprocal, quotient and square root for evaluations whose results are rounded to FP32
+// afterwards (the FP32-mixed policy near the hole), where IEEE rounding of the last FP64 bit
+// buys nothing.  Newton's iteration for 1/x, y <- y + y (1 - x y), twice, and one Heron
+// correction for sqrt x, s <- s + (x - s^2) y / 2 with y ~ 1/sqrt x; both start from the PTX
+// approximate instructions rcp.approx.ftz.f64 / rsqrt.approx.f64, and each step squares the
+// relative error of its seed.  Non-positive square-root arguments take the IEEE path.
+struct NewtonOps64 {
+  __device__ static __forceinline__ double rcp(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+  }
+  __device__ static __forceinline__ double div(double a, double b) { return a * rcp(b); }
+  __device__ static __forceinline__ double root(double x) {
+    if (!(x > 0.0)) return sqrt(x);
+    double y;
+    asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double s = x * y;
+    return fma(0.5 * y, fma(-s, s, x), s);
+  }
+};
+
 template <typename S>
 struct Kerr {
   S r, f;        // r of Eq. 6, f of Eq. 4
@@ -24,17 +61,17 @@ struct Kerr {
 
 // Non-negative root of Eq. 6 as r^2, written so that neither branch cancels; *D receives
 // sqrt((R^2 - a^2)^2 + 4 a^2 z^2).
-template <typename S>
+template <typename S, typename Ops = IeeeOps>
 __device__ __forceinline__ S kerr_r2(S x, S y, S z, S a, S* D) {
   const S a2 = a * a;
   const S q = a2 * z * z;
   const S p = x * x + y * y + z * z - a2;
-  *D = sqrt(p * p + S(4) * q);
-  return (p >= S(0)) ? S(0.5) * (p + *D) : (S(2) * q) / (*D - p);
+  *D = Ops::root(p * p + S(4) * q);
+  return (p >= S(0)) ? S(0.5) * (p + *D) : Ops::div(S(2) * q, *D - p);
 }
 
 // f and k of Eqs. 4-5 at (x, y, z) given r^2 from Eq. 6.
-template <typename S>
+template <typename S, typename Ops = IeeeOps>
 __device__ __forceinline__ Kerr<S> kerr_from_r2(S x, S y, S z, S m, S a, S r2, S D) {
   Kerr<S> K;
   const S a2 = a * a;
@@ -50,10 +87,10 @@ __device__ __forceinline__ Kerr<S> kerr_from_r2(S x, S y, S z, S m, S a, S r2, S
     return K;
   }
   K.flat = false;
-  K.r = sqrt(r2);
-  K.inv_r = S(1) / K.r;
-  K.inv_rho2 = S(1) / (r2 + a2);
-  K.inv_sig = S(1) / (r2 * r2 + q);
+  K.r = Ops::root(r2);
+  K.inv_r = Ops::rcp(K.r);
+  K.inv_rho2 = Ops::rcp(r2 + a2);
+  K.inv_sig = Ops::rcp(r2 * r2 + q);
   K.f = S(2) * m * K.r * r2 * K.inv_sig;
   K.k0 = (K.r * x - a * y) * K.inv_rho2;
   K.k1 = (K.r * y + a * x) * K.inv_rho2;
@@ -80,18 +117,18 @@ __device__ __forceinline__ S area_density(S x, S y, S z, S m, S a, S r2, int K) 
   return sqrt(S(1) + S(2) * m * r * r2 * (S(1) - kk) / sig);
 }
 
-template <typename S>
+template <typename S, typename Ops = IeeeOps>
 __device__ __forceinline__ Kerr<S> kerr_eval(S x, S y, S z, S m, S a) {
   S D;
-  const S r2 = kerr_r2<S>(x, y, z, a, &D);
-  return kerr_from_r2<S>(x, y, z, m, a, r2, D);
+  const S r2 = kerr_r2<S, Ops>(x, y, z, a, &D);
+  return kerr_from_r2<S, Ops>(x, y, z, m, a, r2, D);
 }
 
 // Gamma^a_mn u^m u^n = g^ab (u^m d_m g_bn u^n - 1/2 d_b g_mn u^m u^n) for g = eta + f k k.
 // With s = k.u, D_b = u^m d_m k_b, E_b = u^n d_b k_n and d_4 = 0:
 //   w_b = (u.df) s k_b + f s D_b + f (u.D) k_b - 1/2 s^2 d_b f - f s E_b
 //   Gamma u u = eta^ab w_b - f k^a (k^b w_b)
-template <typename S>
+template <typename S, typename Ops = IeeeOps>
 __device__ __forceinline__ void christoffel_uu(const Kerr<S>& K, S x, S y, S z, S a, const S u[4], S out[4]) {
   if (K.flat) {
     out[0] = out[1] = out[2] = out[3] = S(0);
@@ -101,7 +138,7 @@ __device__ __forceinline__ void christoffel_uu(const Kerr<S>& K, S x, S y, S z, 
   const S k0 = K.k0, k1 = K.k1, k2 = K.k2;
   const S r2 = r * r, a2 = a * a;
   const S inv_rho2 = K.inv_rho2;
-  const S inv_D = S(1) / K.D;
+  const S inv_D = Ops::rcp(K.D);
   const S inv_r = K.inv_r;
   // grad r from the implicit quartic: r_x = x r / D, r_y = y r / D, r_z = z (r^2 + a^2) / (r D)
   const S rx = x * r * inv_D;

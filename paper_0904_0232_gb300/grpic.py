@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
@@ -22,6 +23,7 @@ STATUS_NAMES = {0: "GRPIC_OK", 1: "GRPIC_ERR_INVALID", 2: "GRPIC_ERR_OOM", 3: "G
 GRPIC_FP64, GRPIC_FP32_MIXED = 0, 1
 GRPIC_NO_GAMMA_IN_J = 1
 GRPIC_LITERAL_HALF_STEPS = 2
+GRPIC_SINGLE_PUSH_KERNEL = 4
 GRPIC_MEM_HOST, GRPIC_MEM_DEVICE = 0, 1
 GRPIC_U_FULL, GRPIC_U_COV_SPATIAL, GRPIC_U_CONTRA_SPATIAL, GRPIC_LOAD_DEVICE = 0, 1, 2, 16
 GRPIC_STAGE_B_HALF, GRPIC_STAGE_ZERO_J, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_E, GRPIC_STAGE_SORT, GRPIC_STAGE_B_HALF2 = range(6)
@@ -55,6 +57,11 @@ class grpic_stats(ctypes.Structure):
                 ("particle_steps", ctypes.c_int64), ("n_alive", ctypes.c_int64 * 4)]
 
 
+class grpic_tuning(ctypes.Structure):
+    _fields_ = [("far_min_blocks", ctypes.c_int), ("near_blocks_per_sm", ctypes.c_int), ("sort_interval", ctypes.c_int),
+                ("overlap", ctypes.c_int)]
+
+
 EXPORTS = {
     "grpic_create": (ctypes.c_int, [ctypes.POINTER(grpic_config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "grpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -81,7 +88,11 @@ EXPORTS = {
     "grpic_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int]),
+    "grpic_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_tuning)]),
+    "grpic_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_tuning)]),
     "grpic_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "grpic_check_newton64": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "grpic_check_conversions": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "grpic_sort_particles_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -99,6 +110,7 @@ EXPORTS = {
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grpic_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "grpic_batch_set_blocks_per_sm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grpic_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -146,7 +158,7 @@ def _torch_alloc(nbytes, user):
 
 @FREE_FN
 def _torch_free(ptr, user):
-    if ptr:
+    if ptr and sys.meta_path is not None:  # at interpreter shutdown the process frees everything
         _torch().cuda.caching_allocator_delete(ptr)
 
 
@@ -286,6 +298,30 @@ def grpic_get_profile(ctx, reset=False):
     return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(6)}, nl.value
 
 
+def grpic_set_tuning(ctx, far_min_blocks, near_blocks_per_sm, sort_interval, overlap=1):
+    t = grpic_tuning(int(far_min_blocks), int(near_blocks_per_sm), int(sort_interval), int(overlap))
+    _check(ctx, load_library().grpic_set_tuning(ctx, ctypes.byref(t)), "grpic_set_tuning")
+
+
+def grpic_get_tuning(ctx):
+    t = grpic_tuning()
+    _check(ctx, load_library().grpic_get_tuning(ctx, ctypes.byref(t)), "grpic_get_tuning")
+    return dict(far_min_blocks=t.far_min_blocks, near_blocks_per_sm=t.near_blocks_per_sm,
+                sort_interval=t.sort_interval, overlap=t.overlap)
+
+
+def grpic_check_newton64(n=1 << 22):
+    out = (ctypes.c_double * 3)()
+    _check(None, load_library().grpic_check_newton64(int(n), out), "grpic_check_newton64")
+    return dict(rcp=out[0], div=out[1], sqrt=out[2])
+
+
+def grpic_check_conversions(n=1 << 24):
+    out = (ctypes.c_int64 * 2)()
+    _check(None, load_library().grpic_check_conversions(int(n), out), "grpic_check_conversions")
+    return dict(widen=out[0], narrow=out[1])
+
+
 def grpic_probe_fma_peak(precision):
     v = ctypes.c_double(0.0)
     _check(None, load_library().grpic_probe_fma_peak(int(precision), ctypes.byref(v)), "grpic_probe_fma_peak")
@@ -325,6 +361,11 @@ def grpic_batch_info(b):
     w = ctypes.c_int64(0)
     _check(None, load_library().grpic_batch_info(b, ctypes.byref(k), ctypes.byref(w)), "grpic_batch_info")
     return k.value, w.value
+
+
+def grpic_batch_set_blocks_per_sm(b, blocks_per_sm):
+    _check(None, load_library().grpic_batch_set_blocks_per_sm(b, int(blocks_per_sm)),
+           "grpic_batch_set_blocks_per_sm")
 
 
 def grpic_batch_destroy(b):
@@ -475,3 +516,9 @@ class Simulation:
 
     def profile(self, reset=False):
         return grpic_get_profile(self.handle, reset)
+
+    def set_tuning(self, far_min_blocks=4, near_blocks_per_sm=4, sort_interval=1, overlap=1):
+        grpic_set_tuning(self.handle, far_min_blocks, near_blocks_per_sm, sort_interval, overlap)
+
+    def tuning(self):
+        return grpic_get_tuning(self.handle)

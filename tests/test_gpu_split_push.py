@@ -1,0 +1,178 @@
+"""The split FP32-mixed push: a classification lists the particles within r_fp64 + |a| + 4 cells
+of the hole for a near-hole kernel (the FP64 policy applies there) while an FP32-only kernel
+pushes the rest, on two overlapping streams.
+
+* against the oracle, on a grid where both populations are present;
+* against the single mixed kernel (GRPIC_SINGLE_PUSH_KERNEL): the same particle-step, the same
+  number of FP64 evaluations (no far particle ever needed one);
+* every launch-shape choice of grpic_tuning gives the same result;
+* the FP64 reciprocal / quotient / root of the near-hole evaluations against the IEEE operations.
+"""
+import numpy as np
+import pytest
+
+from parity_util import TOL, gpu_from_oracle, oracle_start, particle_errors, rel_l2, small_kerr
+from paper_0904_0232_gb300.grpic import (GRPIC_SINGLE_PUSH_KERNEL, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_SORT,
+                                         GRPIC_STAGE_ZERO_J,
+                                         GrpicError, grpic_check_conversions, grpic_check_newton64)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+M, A, N = 1.5, 1.2, 40
+R_NEAR = 4.0 * M + abs(A) + 4.0
+
+
+def _workload(seed=31):
+    wl = small_kerr(n=N, ppc=1, seed=seed, m=M, a=A, r_min=1.6 * M)
+    cen = (N - 1) / 2.0
+    R = np.concatenate([np.sqrt(((sp.x4[:3] - cen) ** 2).sum(0)) for sp in wl.species])
+    near = int((R < R_NEAR).sum())
+    assert 0.02 * R.size < near < 0.5 * R.size  # both kernels have work
+    return wl
+
+
+def _push_once(sim):
+    sim.stage(GRPIC_STAGE_ZERO_J)
+    sim.stage(GRPIC_STAGE_PUSH_DEPOSIT)
+
+
+def _state(sim):
+    out = []
+    for s in range(2):
+        x, u, ids = sim.get_particles(s)
+        o = np.argsort(ids)
+        out.append((x[:, o], u[:, o], ids[o]))
+    return out, sim.get_fields()[2], sim.stats()
+
+
+def test_split_push_against_oracle():
+    wl = _workload()
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+    n_live = sum(sim.num_particles(s) for s in range(2))
+    ref.zero_j()
+    ref.push_deposit()
+    _push_once(sim)
+    assert sim.stats()["particle_steps"] == n_live  # each particle pushed once, by one of the two kernels
+    _, _, J = sim.get_fields()
+    sim.stage(GRPIC_STAGE_SORT)  # drop the particles this push removed, as the oracle has
+    tol = TOL["fp32_mixed"]
+    for s in range(2):
+        ex, e4, eu = particle_errors(sim, ref, s)
+        assert max(ex, e4, eu) <= tol["particles"], (s, ex, e4, eu)
+    _, _, Jr = ref.get_fields()
+    assert rel_l2(J, Jr) <= tol["J"] * 10  # split ambiguity at faces is the only source above 1e-5
+    assert sim.stats()["fp64_evals"] > 0
+
+
+def test_split_equals_single_kernel():
+    wl = _workload(seed=32)
+    ref = oracle_start(wl)
+    split = gpu_from_oracle(ref, wl, "fp32_mixed")
+    single = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
+    _push_once(split)
+    _push_once(single)
+    (ps, Js, sts), (pq, Jq, stq) = _state(split), _state(single)
+    assert sts["fp64_evals"] == stq["fp64_evals"] > 0
+    assert sts["particle_steps"] == stq["particle_steps"]
+    for (xs, us, i_s), (xq, uq, iq) in zip(ps, pq):
+        assert np.array_equal(i_s, iq)
+        assert np.abs(xs - xq).max() <= 1e-6 * np.abs(xq).max()
+        assert np.abs(us - uq).max() <= 1e-6 * np.abs(uq).max()
+    # the two kernels compile the same FP32 arithmetic separately (contraction may differ in
+    # the last bit) and accumulate J in another order
+    assert rel_l2(Js, Jq) <= 1e-6
+    # whole steps stay together too
+    split.step(4)
+    single.step(4)
+    (ps, Js, _), (pq, Jq, _) = _state(split), _state(single)
+    for (xs, us, i_s), (xq, uq, iq) in zip(ps, pq):
+        assert np.array_equal(i_s, iq)
+        assert np.abs(xs - xq).max() <= 1e-5 * np.abs(xq).max()
+
+
+@pytest.mark.parametrize("far,near,overlap", [(4, 1, 1), (5, 2, 0), (6, 3, 1), (5, 4, 0)])
+def test_tuning_variants_agree(far, near, overlap):
+    wl = _workload(seed=33)
+    ref = oracle_start(wl)
+    base = gpu_from_oracle(ref, wl, "fp32_mixed")
+    var = gpu_from_oracle(ref, wl, "fp32_mixed")
+    var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap)
+    assert var.tuning() == dict(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap)
+    _push_once(base)
+    _push_once(var)
+    (pb, Jb, sb), (pv, Jv, sv) = _state(base), _state(var)
+    assert sb["fp64_evals"] == sv["fp64_evals"]
+    for (xb, ub, ib), (xv, uv, iv) in zip(pb, pv):
+        assert np.array_equal(ib, iv)
+        assert np.abs(xb - xv).max() <= 1e-6 * np.abs(xb).max()
+        assert np.abs(ub - uv).max() <= 1e-6 * np.abs(ub).max()
+    assert sb["particle_steps"] == sv["particle_steps"]
+    assert rel_l2(Jv, Jb) <= 1e-6
+
+
+def test_sort_interval_from_tuning_matches_oracle():
+    wl = _workload(seed=34)
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+    sim.set_tuning(far_min_blocks=5, near_blocks_per_sm=2, sort_interval=3, overlap=1)
+    ref.step(2)
+    sim.step(2)
+    tol = TOL["fp32_mixed"]
+    for s in range(2):
+        ex, e4, eu = particle_errors(sim, ref, s)
+        assert max(ex, eu) <= tol["particles"] * 8, (s, ex, eu)
+
+
+def test_fresh_contexts_push_each_particle_once():
+    """The near kernel runs concurrently with the far kernel; neither may push a particle the
+    other owns, whichever starts first (fresh contexts, first launches included)."""
+    wl = _workload(seed=36)
+    ref = oracle_start(wl)
+    single = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
+    _push_once(single)
+    single.step(2)
+    want = single.stats()
+    single.close()
+    for rep in range(4):
+        sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+        if rep % 2:
+            sim.set_tuning(far_min_blocks=4 + rep // 2, near_blocks_per_sm=1 + rep, sort_interval=1, overlap=rep // 2)
+        n_live = sum(sim.num_particles(s) for s in range(2))
+        _push_once(sim)
+        assert sim.stats()["particle_steps"] == n_live, rep
+        sim.step(2)
+        got = sim.stats()
+        assert got["particle_steps"] == want["particle_steps"], rep
+        assert got["removed_horizon"] == want["removed_horizon"], rep
+        sim.close()
+
+
+def test_tuning_validation():
+    wl = _workload(seed=35)
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+    for bad in [(3, 2, 1, 1), (7, 2, 1, 1), (5, 0, 1, 1), (5, 2, 0, 1), (5, 2, 1, 2)]:
+        with pytest.raises(GrpicError):
+            sim.set_tuning(*bad)
+    assert sim.tuning()["far_min_blocks"] == 4
+
+
+def test_newton64_against_ieee():
+    err = grpic_check_newton64(1 << 22)
+    print("NewtonOps64 max relative deviation from IEEE:", err)
+    assert err["rcp"] <= 4e-16 and err["div"] <= 6e-16
+    assert err["sqrt"] <= 1e-12
+
+
+def test_integer_conversions_match_hardware():
+    bad = grpic_check_conversions(1 << 24)
+    assert bad == dict(widen=0, narrow=0)
