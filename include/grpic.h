@@ -228,8 +228,8 @@ grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);
 grpic_status grpic_probe_fma_peak(int precision, double* flops_per_s);
 
 /* Self-check of the FP64 reciprocal, quotient and square root that the FP32-mixed policy uses
- * for its FP64 evaluations near the hole (Newton's iteration for 1/x, Heron's correction for
- * sqrt x, seeded by the PTX approximate instructions; their results are rounded to FP32).
+ * for its FP64 evaluations near the hole (one step of Newton's iteration for 1/x, of Heron's
+ * for sqrt x, from the FP32 approximations; their results are rounded to FP32 afterwards).
  * Compares them on the current device with the IEEE operations over n log-uniform arguments in
  * [1e-8, 1e8] and returns the largest relative deviations: max_rel[0] 1/x, [1] y/x, [2] sqrt x. */
 grpic_status grpic_check_newton64(int64_t n, double max_rel[3]);

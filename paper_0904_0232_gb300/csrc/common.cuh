@@ -98,8 +98,8 @@ void launch_push_deposit(const Grid& g, const Fields<T>& F, const Particles<T>& 
                          DevStatus* st, bool mixed, double t_offset, cudaStream_t stream);
 
 // Split FP32-mixed push.  near_radius: particles with R(x_n) below it are classified near
-// (marked kNear, listed) and pushed by launch_push_near (grid-stride over the list, nblocks
-// blocks; new sort keys to keys[slot]); the rest by launch_push_far (FP32 only; minb selects
+// (marked kNear, listed; count[0] = list length, count[1] = work cursor) and pushed by
+// launch_push_near (nblocks persistent blocks; new sort keys to keys[slot]); the rest by launch_push_far (FP32 only; minb selects
 // the register budget), concurrently.  launch_near_keys then copies keys[slot] to P.key.
 double near_radius(const Grid& g);
 void launch_classify_near(const Grid& g, const Particles<float>& P, uint32_t* list, int* count,
@@ -107,7 +107,7 @@ void launch_classify_near(const Grid& g, const Particles<float>& P, uint32_t* li
 void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
                      DevStatus* st, int minb, cudaStream_t stream);
 void launch_push_near(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                      DevStatus* st, const uint32_t* list, uint32_t* keys, const int* count, int nblocks,
+                      DevStatus* st, const uint32_t* list, uint32_t* keys, int* count, int nblocks,
                       cudaStream_t stream);
 void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uint32_t* keys, const int* count,
                       int nblocks, cudaStream_t stream);

@@ -27,7 +27,7 @@ struct SpeciesStore {
   int cur = 0;
   int* n_dev = nullptr;
   int* n_shadow = nullptr;  // pinned host copy of n_dev
-  int* near_n = nullptr;    // split push: length of the near-hole list (device)
+  int* near_n = nullptr;    // split push: near-hole list length and work cursor (2 device ints)
   cudaEvent_t shadow_ev = nullptr;
   bool shadow_pending = false;
   bool loaded = false;
@@ -178,7 +178,7 @@ void enqueue_split_push(grpic_ctx* c) {
     SpeciesStore& S = c->sp[s];
     if (!S.loaded || S.n == 0) continue;
     refresh_count(S);
-    cudaMemsetAsync(S.near_n, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(S.near_n, 0, 2 * sizeof(int), c->stream);
     launch_classify_near(c->g, particles_view<float>(c, s, S.cur), particles_view<float>(c, s, 1 - S.cur).key,
                          S.near_n, c->stream);
     c->launches += 1;
@@ -445,7 +445,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   bool ok = c->fields && c->J && c->mc && c->mask && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
   for (int s = 0; s < kMaxSpecies && ok; ++s) {
     c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
-    c->sp[s].near_n = static_cast<int*>(dev_alloc(c, sizeof(int)));
+    c->sp[s].near_n = static_cast<int*>(dev_alloc(c, 2 * sizeof(int)));
     ok = c->sp[s].n_dev != nullptr && c->sp[s].near_n != nullptr;
     if (ok) ok = cudaMallocHost(&c->sp[s].n_shadow, sizeof(int)) == cudaSuccess;
     if (ok) ok = cudaEventCreateWithFlags(&c->sp[s].shadow_ev, cudaEventDisableTiming) == cudaSuccess;

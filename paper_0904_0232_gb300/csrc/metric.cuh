@@ -25,26 +25,55 @@ struct IeeeOps {
   __device__ static __forceinline__ S root(S x) { return sqrt(x); }
 };
 
+// IEEE 754 binary32 -> binary64, exact, with integer operations only (sign, exponent rebiased
+// by 1023 - 127 = 896, mantissa shifted by 29).  Zero and subnormal inputs give a signed zero
+// (the FP32 push runs with subnormals flushed); infinities and NaNs keep their class.  On this
+// GPU the hardware conversions run on the reduced-rate FP64 pipe.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned hi = u & 0x80000000u, lo = 0u;
+  if (e != 0u) {
+    const unsigned m = u & 0x7fffffu;
+    hi |= ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// IEEE 754 binary64 -> binary32 with round-to-nearest-even, with integer operations for every
+// result in the normal binary32 range (the 29 dropped mantissa bits decide; a carry may step the
+// exponent, to infinity at the top, as the rounding rule says); other inputs (zero, subnormal
+// or out-of-range results, infinities, NaNs) take the hardware conversion.
+__device__ __forceinline__ float narrow(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(d);
+  unsigned r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;
+  return __uint_as_float(r);
+}
+
 // FP64 reciprocal, quotient and square root for evaluations whose results are rounded to FP32
 // afterwards (the FP32-mixed policy near the hole), where IEEE rounding of the last FP64 bit
-// buys nothing.  Newton's iteration for 1/x, y <- y + y (1 - x y), twice, and one Heron
-// correction for sqrt x, s <- s + (x - s^2) y / 2 with y ~ 1/sqrt x; both start from the PTX
-// approximate instructions rcp.approx.ftz.f64 / rsqrt.approx.f64, and each step squares the
-// relative error of its seed.  Non-positive square-root arguments take the IEEE path.
-struct NewtonOps64 {
+// buys nothing: an FP32 estimate (the approximate reciprocal / reciprocal square root, relative
+// error a few 2^-23) refined by one FP64 Newton step -- y <- y + y (1 - x y) for 1/x, and
+// s <- s + (x - s^2) y / 2 with s = x y, y ~ 1/sqrt x, for sqrt x (Heron).  A Newton step
+// squares the relative error.  Arguments outside [1e-30, 1e30] in magnitude (and non-positive
+// square-root arguments) take the IEEE operations.
+struct SeededOps64 {
   __device__ static __forceinline__ double rcp(double x) {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const float xf = narrow(x);
+    if (!(fabsf(xf) >= 1e-30f && fabsf(xf) <= 1e30f)) return 1.0 / x;
+    const double y = widen(__fdividef(1.f, xf));
+    return fma(y, fma(-x, y, 1.0), y);
   }
   __device__ static __forceinline__ double div(double a, double b) { return a * rcp(b); }
   __device__ static __forceinline__ double root(double x) {
-    if (!(x > 0.0)) return sqrt(x);
-    double y;
-    asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const float xf = narrow(x);
+    if (!(xf >= 1e-30f && xf <= 1e30f)) return sqrt(x);
+    const double y = widen(rsqrtf(xf));
     const double s = x * y;
     return fma(0.5 * y, fma(-s, s, x), s);
   }

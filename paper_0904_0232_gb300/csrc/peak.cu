@@ -65,7 +65,7 @@ __device__ __forceinline__ double uniform01(unsigned long long k) {
   return (double)(z >> 11) * 0x1.0p-53;
 }
 
-// Relative deviation of NewtonOps64 from the IEEE operations over log-uniform arguments in
+// Relative deviation of SeededOps64 from the IEEE operations over log-uniform arguments in
 // [1e-8, 1e8]; maxima by atomicMax on the bit patterns (non-negative doubles order as integers).
 __global__ void k_check_newton64(long long n, unsigned long long* worst) {
   double e_rcp = 0.0, e_div = 0.0, e_root = 0.0;
@@ -73,9 +73,9 @@ __global__ void k_check_newton64(long long n, unsigned long long* worst) {
     const double x = exp10(-8.0 + 16.0 * uniform01(2 * i));
     const double y = exp10(-8.0 + 16.0 * uniform01(2 * i + 1));
     const double r_ieee = 1.0 / x, q_ieee = y / x, s_ieee = sqrt(x);
-    e_rcp = fmax(e_rcp, fabs(grpic::NewtonOps64::rcp(x) - r_ieee) / r_ieee);
-    e_div = fmax(e_div, fabs(grpic::NewtonOps64::div(y, x) - q_ieee) / q_ieee);
-    e_root = fmax(e_root, fabs(grpic::NewtonOps64::root(x) - s_ieee) / s_ieee);
+    e_rcp = fmax(e_rcp, fabs(grpic::SeededOps64::rcp(x) - r_ieee) / r_ieee);
+    e_div = fmax(e_div, fabs(grpic::SeededOps64::div(y, x) - q_ieee) / q_ieee);
+    e_root = fmax(e_root, fabs(grpic::SeededOps64::root(x) - s_ieee) / s_ieee);
   }
   atomicMax(worst + 0, (unsigned long long)__double_as_longlong(e_rcp));
   atomicMax(worst + 1, (unsigned long long)__double_as_longlong(e_div));

@@ -22,17 +22,25 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
 }
 
 // Near-hole pass of the split FP32-mixed push: the particles listed by the classification
-// (whose stages and quadrature nodes may fall inside r < r_fp64), grid-stride over the list.
-// Consecutive list entries come from consecutive cell-sorted particles, so a warp stays local.
-// The far kernel runs at the same time and tells near from far particles by the kNear mark in
-// P.key, so the new sort keys go to keys[j] (by list slot) and are copied back after both end.
+// (whose stages and quadrature nodes may fall inside r < r_fp64).  Persistent blocks take
+// 128-entry chunks of the list from a cursor (count[1]) until it is exhausted: the FP64 work
+// per particle varies a lot, so a dynamic queue keeps the SMs evenly loaded.  Consecutive list
+// entries come from consecutive cell-sorted particles, so a warp stays local.  The far kernel
+// runs at the same time and tells near from far particles by the kNear mark in P.key, so the
+// new sort keys go to keys[j] (by list slot) and are copied back after both end.
 template <int Q>
 __global__ void __launch_bounds__(128, 4) k_push_near(const Grid g, const Fields<float> F, const Particles<float> P,
                                                         const Consts<float> C, DevStatus* st,
                                                         const uint32_t* __restrict__ list, uint32_t* __restrict__ keys,
-                                                        const int* count) {
-  const int n = *count;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+                                                        int* count) {
+  __shared__ int s_base;
+  const int n = count[0];
+  for (;;) {
+    if (threadIdx.x == 0) s_base = atomicAdd(count + 1, (int)blockDim.x);
+    __syncthreads();
+    const int base = s_base;
+    __syncthreads();
+    if (base >= n) break;
     const int j = base + threadIdx.x;
     const bool active = j < n;
     unsigned flags = 0, n64 = 0;
@@ -204,7 +212,7 @@ void launch_push_deposit<float>(const Grid& g, const Fields<float>& F, const Par
 }
 
 void launch_push_near(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                      DevStatus* st, const uint32_t* list, uint32_t* keys, const int* count, int nblocks,
+                      DevStatus* st, const uint32_t* list, uint32_t* keys, int* count, int nblocks,
                       cudaStream_t stream) {
   if (P.n <= 0 || nblocks <= 0) return;
   const Consts<float> C = make_consts<float>(g, sp);

@@ -88,7 +88,7 @@ __host__ __device__ inline Consts<T> make_consts(const Grid& g, const Species& s
   C.qmacro = (T)sp.qmacro;
   C.rcheck2 = (T)(1.2 * g.r_plus * g.r_plus + 1.0);
   C.r_fp64 = (float)g.r_fp64;
-  C.r2_fp64 = C.r_fp64 * C.r_fp64;
+  C.r2_fp64 = C.r_fp64 > 0.f ? C.r_fp64 * C.r_fp64 : -1.f;  // negative: never promote
   C.massive = g.m > 0.0;
   C.gamma_in_j = (g.flags & 1u) == 0;
   C.dxc = g.xc;
@@ -101,35 +101,6 @@ __host__ __device__ inline Consts<T> make_consts(const Grid& g, const Species& s
   return C;
 }
 
-// IEEE 754 binary32 -> binary64, exact, with integer operations only (sign, exponent rebiased
-// by 1023 - 127 = 896, mantissa shifted by 29).  Zero and subnormal inputs give a signed zero
-// (the FP32 push runs with subnormals flushed); infinities and NaNs keep their class.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  unsigned hi = u & 0x80000000u, lo = 0u;
-  if (e != 0u) {
-    const unsigned m = u & 0x7fffffu;
-    hi |= ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3);
-    lo = m << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-// IEEE 754 binary64 -> binary32 with round-to-nearest-even, with integer operations for every
-// result in the normal binary32 range (the 29 dropped mantissa bits decide; a carry may step the
-// exponent, to infinity at the top, as the rounding rule says); other inputs (zero, subnormal
-// or out-of-range results, infinities, NaNs) take the hardware conversion.
-__device__ __forceinline__ float narrow(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned e = (hi >> 20) & 0x7ffu;
-  if (e < 897u || e > 1150u) return __double2float_rn(d);
-  unsigned r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;
-  if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;
-  return __uint_as_float(r);
-}
-
 __device__ __forceinline__ double to_f64(float v) { return widen(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
@@ -138,16 +109,40 @@ __device__ __forceinline__ T sel3(int i, T a, T b, T c) {
   return i == 0 ? a : (i == 1 ? b : c);
 }
 
+// FP64 r^2 at a grid position near the hole from the FP32 root s0 = r^2 (with the FP32
+// D0 = sqrt((R^2 - a^2)^2 + 4 a^2 z^2)), by one Newton step on the quartic (Eq. 6).  With s = r^2
+// it reads F(s) = s^2 - p s - q = 0 (p = R^2 - a^2, q = a^2 z^2); F'(s) = 2s - p = D at the root,
+// and D >= s there (the difference of the two roots).  For s0 = s (1 + e) and D0 = D (1 + d),
+// s0 - F(s0)/D0 has relative error about e (d - e s/D), i.e. ~1e-14: F(s0) is formed in FP64
+// (it cancels), its quotient by D0 in FP32.  A poor FP32 start (a correction above 1e-5 s0,
+// or s0 <= 0) takes the closed form in FP64.  X, Y, Z: the point minus the centre, in FP64.
+__device__ __forceinline__ double quartic_newton(const Consts<float>& C, double X, double Y, double Z, float s0,
+                                                 float D0, double* p_out) {
+  const double p = fma(X, X, fma(Y, Y, fma(Z, Z, -C.da2)));
+  *p_out = p;
+  if (s0 > 0.f && D0 > 0.f) {
+    const double q = C.da2 * Z * Z;
+    const double S = widen(s0);
+    const float corr = narrow(fma(S, S - p, -q)) / D0;
+    if (fabsf(corr) <= 1e-5f * s0) return S - widen(corr);
+  }
+  double D;
+  return kerr_r2<double, SeededOps64>(X, Y, Z, C.da, &D);
+}
+
 // FP64 metric and Christoffel contraction at a grid position (the FP32-mixed policy near the
-// hole); kept out of line: it runs for few particles and would otherwise bloat every call site.
-// The results are rounded to FP32, so the FP64 divisions and roots use NewtonOps64.
+// hole), from the FP32 r and D of the same point: r^2 by quartic_newton, D = 2 r^2 - p (the
+// derivative of the quartic at its root), reciprocals and roots by SeededOps64; f, k and the
+// contraction in FP64, rounded to FP32.  Out of line: it runs for few particles.
 __device__ __noinline__ void metric_christoffel_fp64(const Consts<float>& C, float x, float y, float z, float u0,
-                                                     float u1, float u2, float u3, float* out) {
+                                                     float u1, float u2, float u3, float rf, float Df, float* out) {
   const double Xd = widen(x) - C.dxc, Yd = widen(y) - C.dyc, Zd = widen(z) - C.dzc;
-  const Kerr<double> K = kerr_eval<double, NewtonOps64>(Xd, Yd, Zd, C.dm, C.da);
+  double p;
+  const double s = quartic_newton(C, Xd, Yd, Zd, rf * rf, Df, &p);
+  const Kerr<double> K = kerr_from_r2<double, SeededOps64>(Xd, Yd, Zd, C.dm, C.da, s, 2.0 * s - p);
   const double ud[4] = {widen(u0), widen(u1), widen(u2), widen(u3)};
   double gd[4];
-  christoffel_uu<double, NewtonOps64>(K, Xd, Yd, Zd, C.da, ud, gd);
+  christoffel_uu<double, SeededOps64>(K, Xd, Yd, Zd, C.da, ud, gd);
   out[0] = narrow(K.f);
   out[1] = narrow(K.k0);
   out[2] = narrow(K.k1);
@@ -158,24 +153,12 @@ __device__ __noinline__ void metric_christoffel_fp64(const Consts<float>& C, flo
   out[7] = narrow(gd[3]);
 }
 
-// FP64 root of the quartic (Eq. 6) at a quadrature node near the hole, as r^2, by one Newton
-// step from the FP32 root s0.  With s = r^2 the quartic reads F(s) = s^2 - p s - q = 0
-// (p = R^2 - a^2, q = a^2 z^2); F'(s) = 2s - p = D at the root, and D >= s there (both roots'
-// difference).  For s0 = s (1 + e) and the FP32 D0 = D (1 + d), s0 - F(s0)/D0 has relative error
-// about e (d - e s/D), i.e. ~1e-14: F(s0) is formed in FP64 (it cancels), the quotient in FP32.
-// A poor FP32 start (a correction above 1e-5 s0, or s0 <= 0) takes the closed form in FP64.
+// FP64 root of the quartic (Eq. 6) at a quadrature node near the hole (absolute FP32 node
+// coordinates px, py, pz), as r^2 rounded to FP32.
 __device__ __noinline__ float quartic_fp64(const Consts<float>& C, float px, float py, float pz, float s0,
                                            float D0) {
-  const double X = widen(px) - C.dxc, Y = widen(py) - C.dyc, Z = widen(pz) - C.dzc;
-  if (s0 > 0.f && D0 > 0.f) {
-    const double p = fma(X, X, fma(Y, Y, fma(Z, Z, -C.da2)));
-    const double q = C.da2 * Z * Z;
-    const double S = widen(s0);
-    const float corr = narrow(fma(S, S - p, -q)) / D0;
-    if (fabsf(corr) <= 1e-5f * s0) return narrow(S - widen(corr));
-  }
-  double Dd;
-  return narrow(kerr_r2<double, NewtonOps64>(X, Y, Z, C.da, &Dd));
+  double p;
+  return narrow(quartic_newton(C, widen(px) - C.dxc, widen(py) - C.dyc, widen(pz) - C.dzc, s0, D0, &p));
 }
 
 // a~ at (x, u): gather, convert, Lorentz - Christoffel.
@@ -233,7 +216,7 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
   if constexpr (MIXED) {
     if (Kt.r < C.r_fp64) {
       float o[8];
-      metric_christoffel_fp64(C, x[0], x[1], x[2], u[0], u[1], u[2], u[3], o);
+      metric_christoffel_fp64(C, x[0], x[1], x[2], u[0], u[1], u[2], u[3], Kt.r, Kt.D, o);
       f = o[0];
       k0 = o[1];
       k1 = o[2];
@@ -359,22 +342,24 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
   }
 }
 
-// Deposit of a particle far from the hole (the far kernel of the split FP32-mixed push): the
-// same zig-zag split, fluxes and Eq. 18 weights as deposit(), in FP32 with no FP64 promotion.
-// Every quadrature node lies where R > |a| (the classification guarantees it), so the quartic
-// takes its p = R^2 - a^2 > 0 branch and every square-root argument is positive and finite:
-// roots are formed as v * rsqrt(v) and each node needs a single reciprocal.  The Q x Q Gauss
-// nodes of the four sub-rectangles of a face make a 2Q x 2Q lattice in (x^I, x^J); the node
-// coordinates, their squares and the spin terms are formed once per face.
+// FP32 deposit (the zig-zag split, fluxes and Eq. 18 weights of deposit() below) evaluated on a
+// per-face node lattice: the Q x Q Gauss nodes of the four sub-rectangles of a face make a
+// 2Q x 2Q lattice in (x^I, x^J), so node coordinates, their squares and the spin terms are
+// formed once per face, roots are v * rsqrt(v) and each node needs one reciprocal.
 //   Integrand: 1 + f (1 - k_K^2) with f = 2 m r^3 / Sigma, Sigma = r^4 + a^2 z^2, and
 //   1 - k_z^2 = (r^2 - z^2) / r^2;  1 - k_x^2 = (rho^4 - (r x - a y)^2) / rho^4,
 //   1 - k_y^2 = (rho^4 - (r y + a x)^2) / rho^4,  rho^2 = r^2 + a^2.
 // With (I, J) = (K+1, K+2) mod 3: K = 0 -> (x, y, z) = (x^K, x^I, x^J); K = 1 -> (x^J, x^K, x^I);
 // K = 2 -> (x^I, x^J, x^K).
-template <int Q>
-__device__ __forceinline__ void deposit_far(const Grid& g, const Fields<float>& F, const Consts<float>& C,
-                                            const float x0[3], const float dx[3], float qg, float inv_dt,
-                                            unsigned& flags) {
+// MIXED = false is the far-field form: every node has R > |a| (the classification of the split
+// push guarantees it), so the quartic takes its p = R^2 - a^2 > 0 branch and every root
+// argument is positive.  MIXED = true takes either branch of the quartic, the flat limit r = 0,
+// and the FP64 policy: a node whose FP32 r is below r_fp64 gets its r^2 from quartic_fp64 at
+// its FP32 coordinates.
+template <int Q, bool MIXED>
+__device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<float>& F, const Consts<float>& C,
+                                                const float x0[3], const float dx[3], float qg, float inv_dt,
+                                                unsigned& flags, unsigned& n64) {
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
   float s1[3], s2[3];
@@ -406,12 +391,14 @@ __device__ __forceinline__ void deposit_far(const Grid& g, const Fields<float>& 
       const float dK = sel3(K, dseg[0], dseg[1], dseg[2]);
       if (dK == 0.f) continue;
       const float flux = qg * dK * inv_dt;
-      const float XK = sel3(K, P[0], P[1], P[2]) - sel3(K, cen[0], cen[1], cen[2]);
+      const float PK = sel3(K, P[0], P[1], P[2]);
+      const float XK = PK - sel3(K, cen[0], cen[1], cen[2]);
       const float PI = sel3(K, P[1], P[2], P[0]), PJ = sel3(K, P[2], P[0], P[1]);
       const float i0 = (float)sel3(K, cy, cz, cx), j0 = (float)sel3(K, cz, cx, cy);
       const float cI = sel3(K, cen[1], cen[2], cen[0]), cJ = sel3(K, cen[2], cen[0], cen[1]);
-      // node lattice: sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J)
-      float XI[2 * Q], XJ[2 * Q], wI[2], wJ[2];
+      // node lattice: sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J); AI, AJ the
+      // nodes' grid coordinates, XI, XJ relative to the centre
+      float AI[2 * Q], AJ[2 * Q], XI[2 * Q], XJ[2 * Q], wI[2], wJ[2];
 #pragma unroll
       for (int sub = 0; sub < 2; ++sub) {
         const float lo_i = sub ? PI : i0, hi_i = sub ? i0 + 1.f : PI;
@@ -420,11 +407,12 @@ __device__ __forceinline__ void deposit_far(const Grid& g, const Fields<float>& 
         wJ[sub] = hi_j - lo_j;
 #pragma unroll
         for (int p = 0; p < Q; ++p) {
-          XI[sub * Q + p] = 0.5f * (lo_i + hi_i) + 0.5f * wI[sub] * (float)Gauss<Q>::x(p) - cI;
-          XJ[sub * Q + p] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p) - cJ;
+          AI[sub * Q + p] = 0.5f * (lo_i + hi_i) + 0.5f * wI[sub] * (float)Gauss<Q>::x(p);
+          AJ[sub * Q + p] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p);
+          XI[sub * Q + p] = AI[sub * Q + p] - cI;
+          XJ[sub * Q + p] = AJ[sub * Q + p] - cJ;
         }
       }
-      // z and the spin term of the numerator of k_K (K = 0: -a x^I; K = 1: +a x^J)
       const bool z_is_K = K == 2, z_is_I = K == 1;
       const float pK = XK * XK - C.a2;
       float S[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -436,21 +424,38 @@ __device__ __forceinline__ void deposit_far(const Grid& g, const Fields<float>& 
           const float p = pK + XI2 + XJ[jb] * XJ[jb];
           const float Z = z_is_K ? XK : (z_is_I ? XI[ia] : XJ[jb]);
           const float q = C.a2 * Z * Z;
-          const float D2 = fmaf(p, p, 4.f * q);
-          const float r2 = 0.5f * (p + D2 * rsqrtf(D2));
-          const float r = r2 * rsqrtf(r2);
-          const float sig = fmaf(r2, r2, q);
-          float fperp;
-          if (K == 2) {
-            fperp = __fdividef(C.two_m * r * (r2 - Z * Z), sig);
+          float r2, val;
+          if constexpr (!MIXED) {
+            const float D2 = fmaf(p, p, 4.f * q);
+            r2 = 0.5f * (p + D2 * rsqrtf(D2));
           } else {
-            const float num = fmaf(r, XK, K == 0 ? -C.a * XI[ia] : C.a * XJ[jb]);
-            const float rho2 = r2 + C.a2;
-            const float rho4 = rho2 * rho2;
-            fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
+            const float D = sqrtf(fmaf(p, p, 4.f * q));
+            r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
+            if (!(r2 >= C.r2_fp64)) {
+              const float ax = sel3(K, PK, AJ[jb], AI[ia]), ay = sel3(K, AI[ia], PK, AJ[jb]);
+              const float az = sel3(K, AJ[jb], AI[ia], PK);
+              r2 = quartic_fp64(C, ax, ay, az, r2, D);
+              ++n64;
+            }
           }
-          const float v = 1.f + fperp;
-          S[ia / Q][jb / Q] += (float)(Gauss<Q>::w(ia % Q) * Gauss<Q>::w(jb % Q)) * (v * rsqrtf(v));
+          if (MIXED && !(r2 > 0.f)) {
+            val = 1.f;  // the flat limit r = 0
+          } else {
+            const float r = r2 * rsqrtf(r2);
+            const float sig = fmaf(r2, r2, q);
+            float fperp;
+            if (K == 2) {
+              fperp = __fdividef(C.two_m * r * (r2 - Z * Z), sig);
+            } else {
+              const float num = fmaf(r, XK, K == 0 ? -C.a * XI[ia] : C.a * XJ[jb]);
+              const float rho2 = r2 + C.a2;
+              const float rho4 = rho2 * rho2;
+              fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
+            }
+            const float v = 1.f + fperp;
+            val = v * rsqrtf(v);
+          }
+          S[ia / Q][jb / Q] += (float)(Gauss<Q>::w(ia % Q) * Gauss<Q>::w(jb % Q)) * val;
         }
       }
       // sub-rectangle areas; a node's weight is the area of the sub-rectangle opposite it
@@ -526,7 +531,9 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
   if (finite && C.qmacro != T(0)) {
     const T gbar = C.gamma_in_j ? (u0[3] + u1[3]) / (T(2) * C.c) : T(1);
     if constexpr (FAR)
-      deposit_far<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
+      deposit_lattice<Q, false>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
+    else if constexpr (MIXED)
+      deposit_lattice<Q, true>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
     else
       deposit<T, Q, MIXED>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
   }

@@ -166,11 +166,11 @@ def test_tuning_validation():
     assert sim.tuning()["far_min_blocks"] == 4
 
 
-def test_newton64_against_ieee():
+def test_seeded_fp64_ops_against_ieee():
+    # one Newton step from an FP32 estimate (relative error a few 2^-23) squares that error
     err = grpic_check_newton64(1 << 22)
-    print("NewtonOps64 max relative deviation from IEEE:", err)
-    assert err["rcp"] <= 4e-16 and err["div"] <= 6e-16
-    assert err["sqrt"] <= 1e-12
+    print("SeededOps64 max relative deviation from IEEE:", err)
+    assert max(err.values()) <= 1e-12
 
 
 def test_integer_conversions_match_hardware():
