@@ -67,13 +67,13 @@ def parse():
     p.add_argument("--grid", type=int, default=128)
     p.add_argument("--quad", type=int, default=2)
     p.add_argument("--sort-interval", type=int, default=1)
-    p.add_argument("--fp64-steps", type=int, default=4)
-    p.add_argument("--fp32-compare-steps", type=int, default=50,
+    p.add_argument("--fp64-steps", type=int, default=10)
+    p.add_argument("--fp32-compare-steps", type=int, default=200,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
     p.add_argument("--workload", choices=["kerr128", "batch"], default="kerr128",
                    help="kerr128: the single-instance Kerr electron-ion workload; batch: many small "
                         "instances advanced by the batched engine")
-    p.add_argument("--single-kernel-steps", type=int, default=20,
+    p.add_argument("--single-kernel-steps", type=int, default=200,
                    help="steps of the comparison run with the single mixed push kernel; 0 skips it")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
     p.add_argument("--batch-n", type=int, default=64)
@@ -290,29 +290,46 @@ def run_gpu(args, dist):
     build()
     wl = synth.kerr_ion_electron_128(seed=2, n=args.grid)
 
-    # --- FP32-mixed, inputs resident in HBM; launch shapes from the autotuner (untimed)
-    sim = make_sim(wl, "fp32_mixed", args)
+    # --- launch shapes from the autotuner, on a context of its own (tuning advances its state)
+    sig = f"kerr_ion_electron_{args.grid}|Q{args.quad}|{wl.n_particles}"
     if args.no_tune:
-        tuned = {"tuning": sim.tuning(), "cached": False, "trials": 0, "ms_per_step": None}
+        tuned = {"tuning": None, "cached": False, "trials": 0, "ms_per_step": None}
     else:
-        tuned = autotune.tune(sim, f"kerr_ion_electron_{args.grid}|Q{args.quad}|{wl.n_particles}", steps=4)
-    sim.set_profiling(True)
-    sim.step(args.warmup)
+        simt = make_sim(wl, "fp32_mixed", args)
+        tuned = autotune.tune(simt, sig, steps=4)
+        simt.close()
+        del simt
+        torch.cuda.empty_cache()
+
+    def leg(precision, steps, warmup, **kw):
+        """A fresh context from the same initial state, `warmup` untimed then `steps` timed steps."""
+        s_ = make_sim(wl, precision, args, tuning=tuned["tuning"], **kw)
+        s_.set_profiling(True)
+        s_.step(warmup)
+        out = timed_steps(s_, steps, dist) + (s_.stats(), s_.tuning())
+        s_.close()
+        del s_
+        torch.cuda.empty_cache()
+        return out
+
+    def summary(ms_, ps_, prof_, steps, note=None):
+        d = {"value": dist.sum(ps_) / (dist.max(ms_) * 1e-3), "unit": UNIT, "steps": steps,
+             "ms_per_step": ms_ / steps, "push_ms_per_step": prof_["push_deposit"][0] / steps}
+        if note:
+            d["note"] = note
+        return d
+
+    # --- FP32-mixed, inputs resident in HBM
     clocks = Clocks(dist.local)
     clocks.start()
-    ms, psteps, prof, launches = timed_steps(sim, args.steps, dist)
+    ms, psteps, prof, launches, st, tuning_used = leg("fp32_mixed", args.steps, args.warmup)
     clk = clocks.stop()
-    st = sim.stats()
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
 
     t_max = dist.max(ms)
     psteps_all = dist.sum(psteps)
     value = psteps_all / (t_max * 1e-3)
 
     push_ms, push_n = prof["push_deposit"]
-    # one push stage = one launch per species; per-launch figures use the stage average
     flops = ALG_FLOPS[args.quad] * psteps
     achieved = flops / (push_ms * 1e-3) if push_ms > 0 else 0.0
     fp32_probe = grpic_probe_fma_peak(GRPIC_FP32_MIXED)
@@ -321,49 +338,29 @@ def run_gpu(args, dist):
     if PUSH_TRAFFIC["sha"] == sha and PUSH_TRAFFIC["bytes_per_particle"]:
         traffic = PUSH_TRAFFIC["bytes_per_particle"] * psteps / max(1, push_n)
 
-    # --- FP64 path on the same workload (fewer steps; FP64 runs at a small fraction of FP32)
+    # --- FP64 path over the first steps (it runs at a small fraction of the FP32 rate), beside the
+    #     FP32-mixed path over the same window from the same start
     fp64 = None
     if args.fp64_steps > 0:
-        sim64 = make_sim(wl, "fp64", args)
-        sim64.set_profiling(True)
-        sim64.step(1)
-        ms64, ps64, prof64, _ = timed_steps(sim64, args.fp64_steps, dist)
-        sim64.close()
-        del sim64
-        torch.cuda.empty_cache()
-        fp64 = {"value": dist.sum(ps64) / (dist.max(ms64) * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": ms64 / args.fp64_steps,
-                "push_ms_per_step": prof64["push_deposit"][0] / args.fp64_steps}
+        ms64, ps64, prof64, _, _, _ = leg("fp64", args.fp64_steps, 1)
+        msw, psw, profw, _, _, _ = leg("fp32_mixed", args.fp64_steps, 1)
+        fp64 = summary(ms64, ps64, prof64, args.fp64_steps, f"steps 2-{args.fp64_steps + 1} from the start")
+        fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, args.fp64_steps)
 
-    # --- the same workload pushed by the single mixed-precision kernel (no near/far split)
+    # --- the same steps with every particle through the FP32-mixed code (no far-field path)
     single = None
     if args.single_kernel_steps > 0:
-        sim1 = make_sim(wl, "fp32_mixed", args, flags=GRPIC_SINGLE_PUSH_KERNEL, tuning=tuned["tuning"])
-        sim1.set_profiling(True)
-        sim1.step(1)
-        ms1, ps1, prof1, _ = timed_steps(sim1, args.single_kernel_steps, dist)
-        sim1.close()
-        del sim1
-        torch.cuda.empty_cache()
-        single = {"value": dist.sum(ps1) / (dist.max(ms1) * 1e-3), "unit": UNIT, "steps": args.single_kernel_steps,
-                  "ms_per_step": ms1 / args.single_kernel_steps,
-                  "push_ms_per_step": prof1["push_deposit"][0] / args.single_kernel_steps,
-                  "note": "GRPIC_SINGLE_PUSH_KERNEL: every particle through the one mixed kernel"}
+        ms1, ps1, prof1, _, _, _ = leg("fp32_mixed", args.single_kernel_steps, args.warmup,
+                                       flags=GRPIC_SINGLE_PUSH_KERNEL)
+        single = summary(ms1, ps1, prof1, args.single_kernel_steps,
+                         "GRPIC_SINGLE_PUSH_KERNEL: every particle through the FP32-mixed code")
 
-    # --- the same workload with the FP64 region switched off (all-FP32 metric evaluations)
+    # --- the same steps with the FP64 region switched off (all-FP32 metric evaluations)
     fp32_all = None
     if args.fp32_compare_steps > 0:
-        sim32 = make_sim(wl, "fp32_mixed", args, fp64_radius=-1.0, tuning=tuned["tuning"])
-        sim32.set_profiling(True)
-        sim32.step(1)
-        ms32, ps32, prof32, _ = timed_steps(sim32, args.fp32_compare_steps, dist)
-        sim32.close()
-        del sim32
-        torch.cuda.empty_cache()
-        fp32_all = {"value": dist.sum(ps32) / (dist.max(ms32) * 1e-3), "unit": UNIT,
-                    "steps": args.fp32_compare_steps, "ms_per_step": ms32 / args.fp32_compare_steps,
-                    "push_ms_per_step": prof32["push_deposit"][0] / args.fp32_compare_steps,
-                    "note": "fp64_radius < 0: no FP64 metric evaluations (error vs oracle in DESIGN.md)"}
+        ms32, ps32, prof32, _, _, _ = leg("fp32_mixed", args.fp32_compare_steps, args.warmup, fp64_radius=-1.0)
+        fp32_all = summary(ms32, ps32, prof32, args.fp32_compare_steps,
+                           "fp64_radius < 0: no FP64 metric evaluations (error vs oracle in DESIGN.md)")
 
     # --- end to end through the C ABI with host buffers
     e2e = None
@@ -404,14 +401,17 @@ def run_gpu(args, dist):
         "config": {"workload": f"kerr_ion_electron_{args.grid}: Kerr a=0.9m, m=4 cells, {args.grid}^3 grid, "
                                "e-/ion (mass ratio 20), 8 ppc per species, u_th=0.05c, B_z=0.1, dt=0.4",
                    "particles": wl.n_particles, "quad_order": args.quad,
-                   "tuning": dict(tuned["tuning"], autotuned=not args.no_tune, cached=tuned["cached"],
+                   "tuning": dict(tuning_used, autotuned=not args.no_tune, cached=tuned["cached"],
                                   trials=tuned["trials"]),
+                   "window": f"steps {args.warmup + 1}-{args.warmup + args.steps} from the start; every "
+                             "comparison leg starts from the same state",
                    "parallelism": f"replicas x{dist.world}",
                    "l2": "inputs larger than L2 (particle store %.2f GB)" % (wl.n_particles * 40 / 1e9)},
         "gpu_launches": int(launches),
         "stage_ms_per_step": stage_ms,
-        "roofline": {"kernel": "push stage: k_classify_near, then k_push_far (FP32) overlapped with k_push_near "
-                               "(FP32-mixed) on a second stream", "bound": "alu", "achieved": achieved / 1e12,
+        "roofline": {"kernel": "push stage (k_push_select: far-field FP32 or FP32-mixed code per warp; with "
+                               "tuning split=1 the k_classify_near + k_push_near + k_push_far kernels)",
+                     "bound": "alu", "achieved": achieved / 1e12,
                      "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_NOMINAL,
                      "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)",
                      "fma_probe_tflops": fp32_probe / 1e12,

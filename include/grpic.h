@@ -59,8 +59,8 @@ enum { GRPIC_FP64 = 0, GRPIC_FP32_MIXED = 1 };
 enum {
   GRPIC_NO_GAMMA_IN_J = 1u,      /* deposit the plain Umeda flux, without the factor gamma of J = rho gamma v */
   GRPIC_LITERAL_HALF_STEPS = 2u, /* field update with each half-step explicit in its own start value (see below) */
-  GRPIC_SINGLE_PUSH_KERNEL = 4u  /* FP32_MIXED: push every particle with the one mixed-precision kernel instead
-                                    of the near/far split (see grpic_tuning); same arithmetic, for comparison */
+  GRPIC_SINGLE_PUSH_KERNEL = 4u  /* FP32_MIXED: push every particle with the FP32-mixed code (no far-field
+                                    path; see grpic_tuning); same policy, for comparison */
 };
 
 enum { GRPIC_MEM_HOST = 0, GRPIC_MEM_DEVICE = 1 };
@@ -201,22 +201,27 @@ grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t count
                                int reset);
 
 /* Launch-shape choices of a context (not in the paper; what the autotuner chooses).
- * FP32_MIXED contexts split the push in two: a classification lists the particles with
- * R(x_n) < r_fp64 + |a| + 4 cells (each of their RK4 stages and quadrature nodes may fall
- * inside r < r_fp64, where the FP64 policy applies), a near-hole kernel pushes those on a
- * second, higher-priority stream while an FP32-only kernel pushes the rest.
- *   far_min_blocks:     4, 5 or 6 resident 128-thread blocks per SM for the far kernel at Q = 2
- *                       (register budget 128, 96, 80 per thread); other Q always use 5
+ * FP32_MIXED contexts tell "near" particles, R(x_n) < r_fp64 + |a| + 4 cells (some RK4 stage
+ * or quadrature node of theirs may fall inside r < r_fp64, where the FP64 policy applies), from
+ * "far" ones, which take an FP32-only code path.  Two ways to run that:
+ *   split = 0: one launch per species; each warp takes the far-field code unless one of its
+ *              particles is near, then the FP32-mixed code (near and far warps share the SMs)
+ *   split = 1: a classification lists the near particles, a near-hole kernel pushes them (on a
+ *              second, higher-priority stream if overlap = 1, else afterwards) and an FP32-only
+ *              kernel pushes the rest
+ *   far_min_blocks:     4, 5 or 6 resident 128-thread blocks per SM for the far-field (split = 1)
+ *                       or per-warp (split = 0: 4 or 5) kernel at Q = 2 (register budget 128,
+ *                       96, 80 per thread); other Q use fixed choices
  *   near_blocks_per_sm: persistent blocks per SM of the near-hole kernel (>= 1)
  *   sort_interval:      counting sort every k timesteps (>= 1)
- *   overlap:            1: the near-hole kernel runs on the second stream alongside the far kernel;
- *                       0: after it, on the context stream
- * grpic_set_tuning validates all four (GRPIC_ERR_INVALID) and applies them from the next step. */
+ *   overlap:            split = 1 only, as above
+ * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */
 typedef struct {
   int far_min_blocks;
   int near_blocks_per_sm;
   int sort_interval;
   int overlap;
+  int split;
 } grpic_tuning;
 grpic_status grpic_set_tuning(grpic_ctx* ctx, const grpic_tuning* t);
 grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);

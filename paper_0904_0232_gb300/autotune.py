@@ -1,7 +1,8 @@
 """Autotuner for the launch-shape choices of a GRPIC context (grpic_tuning in include/grpic.h):
-the register budget of the far-field push kernel (resident blocks per SM), the persistent
-blocks per SM of the near-hole kernel, whether that kernel overlaps the far one on a second
-stream, and the sort interval.
+whether the FP32-mixed push runs as one kernel with a per-warp choice of code or split into
+near-hole and far-field kernels, the register budget of the far-field code (resident blocks
+per SM), the persistent blocks per SM of the near-hole kernel, whether that kernel overlaps the
+far one on a second stream, and the sort interval.
 
 Coordinate descent: starting from the current choice, each knob in turn is set to each of its
 values while the others stay fixed, and the fastest is kept; two rounds.  A trial times
@@ -19,6 +20,7 @@ import json
 import os
 
 CHOICES = {
+    "split": (0, 1),
     "far_min_blocks": (4, 5, 6),
     "near_blocks_per_sm": (1, 2, 4),
     "overlap": (0, 1),

@@ -97,11 +97,19 @@ template <typename T>
 void launch_push_deposit(const Grid& g, const Fields<T>& F, const Particles<T>& P, const Species& sp,
                          DevStatus* st, bool mixed, double t_offset, cudaStream_t stream);
 
+// Far-field criterion of the FP32-mixed push: every RK4 stage and quadrature node of a
+// particle-step lies within 2 sqrt(3) < 4 cells of x_n (stages move less than a cell; nodes lie
+// in the cells of x_n and x_{n+1}, neighbours since |dx^i| < 1), and r >= R - |a| (Eq. 6), so a
+// particle with R(x_n) >= r_fp64 + |a| + 4 never needs the FP64 policy and every node of its
+// deposit has R > |a|.
+__host__ __device__ inline double near_radius(const Grid& g) {
+  return (g.r_fp64 > 0.0 ? g.r_fp64 : 0.0) + (g.a < 0.0 ? -g.a : g.a) + 4.0;
+}
+
 // Split FP32-mixed push.  near_radius: particles with R(x_n) below it are classified near
 // (marked kNear, listed; count[0] = list length, count[1] = work cursor) and pushed by
 // launch_push_near (nblocks persistent blocks; new sort keys to keys[slot]); the rest by launch_push_far (FP32 only; minb selects
 // the register budget), concurrently.  launch_near_keys then copies keys[slot] to P.key.
-double near_radius(const Grid& g);
 void launch_classify_near(const Grid& g, const Particles<float>& P, uint32_t* list, int* count,
                           cudaStream_t stream);
 void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
@@ -111,6 +119,10 @@ void launch_push_near(const Grid& g, const Fields<float>& F, const Particles<flo
                       cudaStream_t stream);
 void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uint32_t* keys, const int* count,
                       int nblocks, cudaStream_t stream);
+// Unsplit alternative: one launch, far-field or FP32-mixed code chosen per warp by the same
+// near_radius criterion.
+void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
+                        DevStatus* st, int minb, cudaStream_t stream);
 
 template <typename T>
 void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,

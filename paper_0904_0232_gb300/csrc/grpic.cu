@@ -47,7 +47,7 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
-  grpic_tuning tune{4, 4, 1, 1};
+  grpic_tuning tune{4, 4, 1, 1, 0};
   void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T
@@ -155,6 +155,19 @@ bool split_push(const grpic_ctx* c) {
   return c->mixed && c->g.r_fp64 > 0.0 && !(c->cfg.flags & GRPIC_SINGLE_PUSH_KERNEL);
 }
 
+// Unsplit FP32-mixed push: one launch per species, far-field or mixed code chosen per warp.
+void enqueue_select_push(grpic_ctx* c) {
+  Fields<float> F = fields_view<float>(c);
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    refresh_count(S);
+    launch_push_select(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
+                       c->tune.far_min_blocks, c->stream);
+    c->launches += 1;
+  }
+}
+
 void enqueue_far(grpic_ctx* c, const Fields<float>& F) {
   for (int s = 0; s < kMaxSpecies; ++s) {
     SpeciesStore& S = c->sp[s];
@@ -230,7 +243,10 @@ void enqueue_stage(grpic_ctx* c, int stage) {
       break;
     case GRPIC_STAGE_PUSH_DEPOSIT:
       if (split_push(c)) {
-        enqueue_split_push(c);
+        if (c->tune.split)
+          enqueue_split_push(c);
+        else
+          enqueue_select_push(c);
       } else {
         for (int s = 0; s < kMaxSpecies; ++s) {
           SpeciesStore& S = c->sp[s];
@@ -787,7 +803,8 @@ grpic_status grpic_get_stats(grpic_ctx* c, grpic_stats* out) {
 grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
   if (!c || !t) return GRPIC_ERR_INVALID;
   if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
-      t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1))
+      t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1) ||
+      (t->split != 0 && t->split != 1))
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   c->cfg.sort_interval = t->sort_interval;

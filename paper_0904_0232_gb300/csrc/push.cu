@@ -59,7 +59,8 @@ __global__ void k_near_keys(uint32_t* __restrict__ key, const uint32_t* __restri
 // Batched: grid-stride over (instance * 4 + species, block) work items; each block belongs to
 // one instance and species, so the warp-level status stays per instance.  The block's instance
 // descriptor is staged in shared memory and reloaded only when the instance changes (a CTA's
-// consecutive grid-stride blocks mostly stay inside one instance).
+// consecutive grid-stride blocks mostly stay inside one instance).  FP32-mixed: each warp takes
+// the far-field code unless one of its particles lies within the instance's near_radius.
 template <typename T, int Q, bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>* __restrict__ desc,
                                                                  const BlockEntry* __restrict__ blk, int nblk) {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
   __shared__ Particles<T> sP;
   __shared__ Consts<T> sC;
   __shared__ DevStatus* sst;
+  __shared__ float s_rnear2;
   int loaded = -1;
   for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
     const BlockEntry e = blk[bi];
@@ -81,6 +83,8 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
         sP = S.buf[*S.cur];
         sC = make_consts<T>(D.g, Species{S.qm, S.qmacro});
         sst = D.st;
+        const double rn = near_radius(D.g);
+        s_rnear2 = (float)(rn * rn);
       }
       __syncthreads();
       loaded = e.inst;
@@ -89,7 +93,20 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
     unsigned flags = 0, n64 = 0;
     bool active = i < sP.n && i < (long long)(*sP.n_dev);
     if (active) active = sP.key[i] != kDead;
-    if (active) push_particle<T, Q, MIXED>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
+    if constexpr (MIXED) {
+      bool near = false;
+      if (active) {
+        const float X = sP.x[0][i] - sC.xc, Y = sP.x[1][i] - sC.yc, Z = sP.x[2][i] - sC.zc;
+        near = X * X + Y * Y + Z * Z < s_rnear2;
+      }
+      if (__any_sync(0xffffffffu, near)) {
+        if (active) push_particle<T, Q, true>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
+      } else {
+        if (active) push_particle<T, Q, false, true>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
+      }
+    } else {
+      if (active) push_particle<T, Q, MIXED>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
+    }
     warp_status(sst, flags, n64, active);
   }
 }

@@ -1,13 +1,9 @@
-// Split FP32-mixed push, far side: the classification of particles by distance from the hole
-// and the FP32-only push of the particles far from it.
-//
-// The FP32-mixed policy evaluates the quartic, the metric and the Christoffel contraction in
-// FP64 wherever the FP32 estimate of r is below r_fp64.  Every evaluation of a particle-step
-// lies near x_n: the RK4 stages move it by less than a cell, and the quadrature nodes of the
-// deposit lie in the cells of x_n and x_{n+1}, which are neighbours (|dx^i| < 1), so within
-// 2 sqrt(3) < 4 cells of x_n.  Since r^2 >= R^2 - a^2 (Eq. 6), r >= R - |a|; so a particle
-// with R(x_n) >= r_fp64 + |a| + 4 never needs FP64 and runs here, with no FP64 code at all
-// (fewer registers, more resident warps).  The others are marked and listed for the near pass.
+// FP32-mixed push with a far-field code path.  The FP32-mixed policy evaluates the quartic, the
+// metric and the Christoffel contraction in FP64 wherever the FP32 estimate of r is below
+// r_fp64; a particle with R(x_n) >= near_radius (common.cuh) never needs that, so it can take
+// FP32-only code with no FP64 at all.  Here: the per-warp choice of code in one kernel
+// (k_push_select), and the split form -- the classification of near particles for a separate
+// near-hole kernel and the FP32-only push of the others (k_push_far).
 #include <algorithm>
 #include <cmath>
 
@@ -58,11 +54,35 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
   warp_status(st, flags, n64, active);
 }
 
+// One kernel for every particle, the path chosen per warp: a warp none of whose particles is
+// near (R(x_n) >= near_radius, the same criterion as the classification) takes the far-field
+// code; a warp with any near particle takes the FP32-mixed code with the FP64 policy.  Particles
+// are cell-sorted, so warps are nearly always homogeneous, and the near warps share every SM
+// with far warps: FP64 and FP32 work proceed side by side on their own pipes.
+template <int Q, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
+                                                           const Particles<float> P, const Consts<float> C,
+                                                           float r_near2, DevStatus* st) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned flags = 0, n64 = 0;
+  bool active = i < P.n && i < (long long)(*P.n_dev);
+  if (active) active = P.key[i] != kDead;
+  bool near = false;
+  if (active) {
+    const float X = P.x[0][i] - C.xc, Y = P.x[1][i] - C.yc, Z = P.x[2][i] - C.zc;
+    near = X * X + Y * Y + Z * Z < r_near2;
+  }
+  if (__any_sync(0xffffffffu, near)) {
+    if (active) push_particle<float, Q, true>(g, F, P, C, i, st, flags, n64, P.key + i);
+  } else {
+    if (active) push_particle<float, Q, false, true>(g, F, P, C, i, st, flags, n64, P.key + i);
+  }
+  warp_status(st, flags, n64, active);
+}
+
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
-
-double near_radius(const Grid& g) { return g.r_fp64 + std::fabs(g.a) + 4.0; }
 
 void launch_classify_near(const Grid& g, const Particles<float>& P, uint32_t* list, int* count,
                           cudaStream_t stream) {
@@ -92,6 +112,23 @@ void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<floa
     k_push_far<2, 6><<<nb, 128, 0, stream>>>(g, F, P, C, st);
   else
     k_push_far<2, 5><<<nb, 128, 0, stream>>>(g, F, P, C, st);
+}
+
+void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
+                        DevStatus* st, int minb, cudaStream_t stream) {
+  if (P.n <= 0) return;
+  const unsigned nb = blocks_for(P.n, 128);
+  const Consts<float> C = make_consts<float>(g, sp);
+  const double rn = near_radius(g);
+  const float r_near2 = (float)(rn * rn);
+  if (g.quad_order == 1)
+    k_push_select<1, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+  else if (g.quad_order == 3)
+    k_push_select<3, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+  else if (minb >= 5)
+    k_push_select<2, 5><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+  else
+    k_push_select<2, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
 }
 
 }  // namespace grpic

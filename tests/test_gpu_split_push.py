@@ -1,6 +1,7 @@
-"""The split FP32-mixed push: a classification lists the particles within r_fp64 + |a| + 4 cells
-of the hole for a near-hole kernel (the FP64 policy applies there) while an FP32-only kernel
-pushes the rest, on two overlapping streams.
+"""The FP32-mixed push with a far-field code path: particles within r_fp64 + |a| + 4 cells of the
+hole ("near") take the FP32-mixed code with the FP64 policy, the others FP32-only code -- either
+per warp in one kernel (split = 0) or in separate near-hole and far-field kernels on two streams
+(split = 1).
 
 * against the oracle, on a grid where both populations are present;
 * against the single mixed kernel (GRPIC_SINGLE_PUSH_KERNEL): the same particle-step, the same
@@ -53,10 +54,12 @@ def _state(sim):
     return out, sim.get_fields()[2], sim.stats()
 
 
-def test_split_push_against_oracle():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_split_push_against_oracle(mode):
     wl = _workload()
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+    sim.set_tuning(split=mode)
     n_live = sum(sim.num_particles(s) for s in range(2))
     ref.zero_j()
     ref.push_deposit()
@@ -73,10 +76,12 @@ def test_split_push_against_oracle():
     assert sim.stats()["fp64_evals"] > 0
 
 
-def test_split_equals_single_kernel():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_split_equals_single_kernel(mode):
     wl = _workload(seed=32)
     ref = oracle_start(wl)
     split = gpu_from_oracle(ref, wl, "fp32_mixed")
+    split.set_tuning(split=mode)
     single = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
     _push_once(split)
     _push_once(single)
@@ -99,14 +104,16 @@ def test_split_equals_single_kernel():
         assert np.abs(xs - xq).max() <= 1e-5 * np.abs(xq).max()
 
 
-@pytest.mark.parametrize("far,near,overlap", [(4, 1, 1), (5, 2, 0), (6, 3, 1), (5, 4, 0)])
-def test_tuning_variants_agree(far, near, overlap):
+@pytest.mark.parametrize("far,near,overlap,split", [(4, 1, 1, 1), (5, 2, 0, 1), (6, 3, 1, 1), (5, 4, 0, 1),
+                                                   (4, 4, 1, 0), (5, 4, 1, 0)])
+def test_tuning_variants_agree(far, near, overlap, split):
     wl = _workload(seed=33)
     ref = oracle_start(wl)
-    base = gpu_from_oracle(ref, wl, "fp32_mixed")
+    base = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
     var = gpu_from_oracle(ref, wl, "fp32_mixed")
-    var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap)
-    assert var.tuning() == dict(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap)
+    var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap, split=split)
+    assert var.tuning() == dict(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap,
+                                split=split)
     _push_once(base)
     _push_once(var)
     (pb, Jb, sb), (pv, Jv, sv) = _state(base), _state(var)
@@ -144,8 +151,8 @@ def test_fresh_contexts_push_each_particle_once():
     single.close()
     for rep in range(4):
         sim = gpu_from_oracle(ref, wl, "fp32_mixed")
-        if rep % 2:
-            sim.set_tuning(far_min_blocks=4 + rep // 2, near_blocks_per_sm=1 + rep, sort_interval=1, overlap=rep // 2)
+        sim.set_tuning(far_min_blocks=4 + rep // 2, near_blocks_per_sm=1 + rep, sort_interval=1, overlap=rep // 2,
+                       split=rep % 2)
         n_live = sum(sim.num_particles(s) for s in range(2))
         _push_once(sim)
         assert sim.stats()["particle_steps"] == n_live, rep
@@ -160,7 +167,7 @@ def test_tuning_validation():
     wl = _workload(seed=35)
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, "fp32_mixed")
-    for bad in [(3, 2, 1, 1), (7, 2, 1, 1), (5, 0, 1, 1), (5, 2, 0, 1), (5, 2, 1, 2)]:
+    for bad in [(3, 2, 1, 1, 0), (7, 2, 1, 1, 0), (5, 0, 1, 1, 0), (5, 2, 0, 1, 0), (5, 2, 1, 2, 0), (5, 2, 1, 1, 2)]:
         with pytest.raises(GrpicError):
             sim.set_tuning(*bad)
     assert sim.tuning()["far_min_blocks"] == 4
