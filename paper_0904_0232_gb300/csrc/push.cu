@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
   unsigned flags = 0, n64 = 0;
   bool active = i < P.n && i < (long long)(*P.n_dev);
   if (active) active = P.key[i] != kDead;
-  if (active) push_particle<T, Q, MIXED>(g, F, P, C, i, st, flags, n64, P.key + i);
+  if (active) push_particle<T, Q>(g, F, P, C, i, st, flags, n64, P.key + i, MIXED);
   warp_status(st, flags, n64, active);
 }
 
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128, 4) k_push_near(const Grid g, const Fields
     const int j = base + threadIdx.x;
     const bool active = j < n;
     unsigned flags = 0, n64 = 0;
-    if (active) push_particle<float, Q, true>(g, F, P, C, (long long)list[j], st, flags, n64, keys + j);
+    if (active) push_particle<float, Q>(g, F, P, C, (long long)list[j], st, flags, n64, keys + j, true);
     warp_status(st, flags, n64, active);
   }
 }
@@ -93,19 +93,19 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
     unsigned flags = 0, n64 = 0;
     bool active = i < sP.n && i < (long long)(*sP.n_dev);
     if (active) active = sP.key[i] != kDead;
+    bool mixed = false;
     if constexpr (MIXED) {
       bool near = false;
       if (active) {
         const float X = sP.x[0][i] - sC.xc, Y = sP.x[1][i] - sC.yc, Z = sP.x[2][i] - sC.zc;
         near = X * X + Y * Y + Z * Z < s_rnear2;
       }
-      if (__any_sync(0xffffffffu, near)) {
-        if (active) push_particle<T, Q, true>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
-      } else {
-        if (active) push_particle<T, Q, false, true>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
-      }
+      mixed = __any_sync(0xffffffffu, near);
+    }
+    if (mixed) {  // two inlined copies with a constant flag (see k_push_select)
+      if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, true);
     } else {
-      if (active) push_particle<T, Q, MIXED>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i);
+      if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, false);
     }
     warp_status(sst, flags, n64, active);
   }

@@ -162,9 +162,11 @@ __device__ __noinline__ float quartic_fp64(const Consts<float>& C, float px, flo
 }
 
 // a~ at (x, u): gather, convert, Lorentz - Christoffel.
-template <typename T, bool MIXED>
+// mixed: the FP32-mixed policy applies (T = float): where the FP32 r is below r_fp64 the metric
+// and the Christoffel contraction are taken from metric_christoffel_fp64.
+template <typename T>
 __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const Consts<T>& C, const T x[3],
-                                      const T u[4], T out[4], unsigned& flags, unsigned& n64) {
+                                      const T u[4], T out[4], unsigned& flags, unsigned& n64, bool mixed) {
   // --- CIC gather: integer lattice (floor x) and half lattice (floor(x - 1/2)) per axis
   int ii[3], ih[3];
   T wi[3], wh[3];
@@ -213,8 +215,9 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
   T f, k0, k1, k2, gam[4];
   const T X = x[0] - C.xc, Y = x[1] - C.yc, Z = x[2] - C.zc;
   const Kerr<T> Kt = kerr_eval<T>(X, Y, Z, C.m, C.a);
-  if constexpr (MIXED) {
-    if (Kt.r < C.r_fp64) {
+  bool promoted = false;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (mixed && Kt.r < C.r_fp64) {
       float o[8];
       metric_christoffel_fp64(C, x[0], x[1], x[2], u[0], u[1], u[2], u[3], Kt.r, Kt.D, o);
       f = o[0];
@@ -226,14 +229,10 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
       gam[2] = o[6];
       gam[3] = o[7];
       ++n64;
-    } else {
-      christoffel_uu<T>(Kt, X, Y, Z, C.a, u, gam);
-      f = Kt.f;
-      k0 = Kt.k0;
-      k1 = Kt.k1;
-      k2 = Kt.k2;
+      promoted = true;
     }
-  } else {
+  }
+  if (!promoted) {
     christoffel_uu<T>(Kt, X, Y, Z, C.a, u, gam);
     f = Kt.f;
     k0 = Kt.k0;
@@ -248,24 +247,18 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
 }
 
 // Integrand of Eq. 18, sqrt(g_II g_JJ - g_IJ^2) = sqrt(1 + f (k_I^2 + k_J^2)), at a grid
-// position.  FP32-mixed: near the hole the quartic root is taken in FP64.
-template <typename T, bool MIXED>
-__device__ __forceinline__ T area_integrand(const Consts<T>& C, T px, T py, T pz, int K, unsigned& n64) {
+// position (the FP64 path; the FP32 paths use deposit_lattice).
+template <typename T>
+__device__ __forceinline__ T area_integrand(const Consts<T>& C, T px, T py, T pz, int K) {
   const T X = px - C.xc, Y = py - C.yc, Z = pz - C.zc;
   T D;
-  T r2 = kerr_r2<T>(X, Y, Z, C.a, &D);
-  if constexpr (MIXED) {
-    if (r2 < C.r2_fp64) {
-      r2 = quartic_fp64(C, px, py, pz, r2, D);
-      ++n64;
-    }
-  }
+  const T r2 = kerr_r2<T>(X, Y, Z, C.a, &D);
   return area_density<T>(X, Y, Z, C.m, C.a, r2, K);
 }
 
 // AREA of Eq. 18 over [Is, If] x [Js, Jf] in the plane x^K = xK.
-template <typename T, int Q, bool MIXED>
-__device__ __forceinline__ T area(const Consts<T>& C, int K, T xK, T Is, T If, T Js, T Jf, unsigned& n64) {
+template <typename T, int Q>
+__device__ __forceinline__ T area(const Consts<T>& C, int K, T xK, T Is, T If, T Js, T Jf) {
   T s = T(0);
   const T ci = T(0.5) * (Is + If), hi = T(0.5) * (If - Is);
   const T cj = T(0.5) * (Js + Jf), hj = T(0.5) * (Jf - Js);
@@ -279,7 +272,7 @@ __device__ __forceinline__ T area(const Consts<T>& C, int K, T xK, T Is, T If, T
       const T px = sel3(K, xK, xj, xi);
       const T py = sel3(K, xi, xK, xj);
       const T pz = sel3(K, xj, xi, xK);
-      s += (T)Gauss<Q>::w(p) * (T)Gauss<Q>::w(q) * area_integrand<T, MIXED>(C, px, py, pz, K, n64);
+      s += (T)Gauss<Q>::w(p) * (T)Gauss<Q>::w(q) * area_integrand<T>(C, px, py, pz, K);
     }
   return s * T(0.25) * (If - Is) * (Jf - Js);
 }
@@ -289,9 +282,9 @@ __device__ __forceinline__ T area(const Consts<T>& C, int K, T xK, T Is, T If, T
 // increment instead of inheriting the rounding of the stored positions.  With |dx| < 1 the
 // relay point min(min(a,b)+1, max(max(a,b), mid)) is the midpoint when the cell does not
 // change along an axis and the shared face otherwise.
-template <typename T, int Q, bool MIXED>
+template <typename T, int Q>
 __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const Consts<T>& C, const T x0[3],
-                                        const T dx[3], T qg, T inv_dt, unsigned& flags, unsigned& n64) {
+                                        const T dx[3], T qg, T inv_dt, unsigned& flags) {
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
   T s1[3], s2[3];
@@ -326,10 +319,10 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
       const T PI = sel3(K, P[1], P[2], P[0]);
       const T PJ = sel3(K, P[2], P[0], P[1]);
       const T i0 = (T)sel3(K, cy, cz, cx), j0 = (T)sel3(K, cz, cx, cy);
-      const T A00 = area<T, Q, MIXED>(C, K, PK, PI, i0 + T(1), PJ, j0 + T(1), n64);
-      const T A10 = area<T, Q, MIXED>(C, K, PK, i0, PI, PJ, j0 + T(1), n64);
-      const T A01 = area<T, Q, MIXED>(C, K, PK, PI, i0 + T(1), j0, PJ, n64);
-      const T A11 = area<T, Q, MIXED>(C, K, PK, i0, PI, j0, PJ, n64);
+      const T A00 = area<T, Q>(C, K, PK, PI, i0 + T(1), PJ, j0 + T(1));
+      const T A10 = area<T, Q>(C, K, PK, i0, PI, PJ, j0 + T(1));
+      const T A01 = area<T, Q>(C, K, PK, PI, i0 + T(1), j0, PJ);
+      const T A11 = area<T, Q>(C, K, PK, i0, PI, j0, PJ);
       const T FA = A00 + A10 + A01 + A11;
       const T W00 = A00 / FA, W10 = A10 / FA, W01 = A01 / FA, W11 = A11 / FA;
       const long long stI = sel3(K, sy, sz, 1ll), stJ = sel3(K, sz, 1ll, sy);
@@ -342,6 +335,18 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
   }
 }
 
+// A quadrature node that the far-field formula of deposit_lattice does not cover (FP32-mixed
+// warps only): the p <= 0 branch of the quartic (the cancellation-free form), and the FP64
+// policy where the FP32 r is below r_fp64 (or always, with promote).  Returns r^2 and whether
+// it came from FP64.  Out of line: far-field warps never call it.
+__device__ __noinline__ float2 node_slow(const Consts<float>& C, float p, float q, float ax, float ay, float az,
+                                         bool promote) {
+  const float D = sqrtf(fmaf(p, p, 4.f * q));
+  float r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
+  if (promote || !(r2 >= C.r2_fp64)) return make_float2(quartic_fp64(C, ax, ay, az, r2, D), 1.f);
+  return make_float2(r2, 0.f);
+}
+
 // FP32 deposit (the zig-zag split, fluxes and Eq. 18 weights of deposit() below) evaluated on a
 // per-face node lattice: the Q x Q Gauss nodes of the four sub-rectangles of a face make a
 // 2Q x 2Q lattice in (x^I, x^J), so node coordinates, their squares and the spin terms are
@@ -351,15 +356,15 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
 //   1 - k_y^2 = (rho^4 - (r y + a x)^2) / rho^4,  rho^2 = r^2 + a^2.
 // With (I, J) = (K+1, K+2) mod 3: K = 0 -> (x, y, z) = (x^K, x^I, x^J); K = 1 -> (x^J, x^K, x^I);
 // K = 2 -> (x^I, x^J, x^K).
-// MIXED = false is the far-field form: every node has R > |a| (the classification of the split
-// push guarantees it), so the quartic takes its p = R^2 - a^2 > 0 branch and every root
-// argument is positive.  MIXED = true takes either branch of the quartic, the flat limit r = 0,
-// and the FP64 policy: a node whose FP32 r is below r_fp64 gets its r^2 from quartic_fp64 at
-// its FP32 coordinates.
-template <int Q, bool MIXED>
+// Every node first takes the far-field form: for a particle outside the near radius every node
+// has R > |a|, so the quartic takes its p = R^2 - a^2 > 0 branch and every root argument is
+// positive.  With mixed (a warp-uniform flag) a node with p <= 0 or an FP32 r below r_fp64 is
+// handed to node_slow (the FP64 policy, quartic_fp64 at the node's FP32 coordinates), and r = 0
+// gives the flat limit; one code path serves far-field and mixed warps alike.
+template <int Q>
 __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<float>& F, const Consts<float>& C,
                                                 const float x0[3], const float dx[3], float qg, float inv_dt,
-                                                unsigned& flags, unsigned& n64) {
+                                                unsigned& flags, unsigned& n64, bool mixed) {
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
   float s1[3], s2[3];
@@ -424,21 +429,17 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
           const float p = pK + XI2 + XJ[jb] * XJ[jb];
           const float Z = z_is_K ? XK : (z_is_I ? XI[ia] : XJ[jb]);
           const float q = C.a2 * Z * Z;
-          float r2, val;
-          if constexpr (!MIXED) {
-            const float D2 = fmaf(p, p, 4.f * q);
-            r2 = 0.5f * (p + D2 * rsqrtf(D2));
-          } else {
-            const float D = sqrtf(fmaf(p, p, 4.f * q));
-            r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
-            if (!(r2 >= C.r2_fp64)) {
-              const float ax = sel3(K, PK, AJ[jb], AI[ia]), ay = sel3(K, AI[ia], PK, AJ[jb]);
-              const float az = sel3(K, AJ[jb], AI[ia], PK);
-              r2 = quartic_fp64(C, ax, ay, az, r2, D);
-              ++n64;
-            }
+          const float D2 = fmaf(p, p, 4.f * q);
+          float r2 = 0.5f * (p + D2 * rsqrtf(D2));
+          float val;
+          if (mixed && (!(p > 0.f) || !(r2 >= C.r2_fp64))) {
+            const float ax = sel3(K, PK, AJ[jb], AI[ia]), ay = sel3(K, AI[ia], PK, AJ[jb]);
+            const float az = sel3(K, AJ[jb], AI[ia], PK);
+            const float2 rs = node_slow(C, p, q, ax, ay, az, p > 0.f);
+            r2 = rs.x;
+            n64 += (unsigned)rs.y;
           }
-          if (MIXED && !(r2 > 0.f)) {
+          if (mixed && !(r2 > 0.f)) {
             val = 1.f;  // the flat limit r = 0
           } else {
             const float r = r2 * rsqrtf(r2);
@@ -476,10 +477,12 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
 
 // One particle-step of particle i: RK4 push, deposit, removal flag and sort key (written to
 // *key_out: P.key + i, or a side array where another kernel still reads P.key concurrently).
-template <typename T, int Q, bool MIXED, bool FAR = false>
+// mixed (T = float): the FP32-mixed policy applies to this warp's particles (a warp-uniform
+// flag; false only where every particle lies outside near_radius).  T = double ignores it.
+template <typename T, int Q>
 __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F, const Particles<T>& P,
                                               const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
-                                              unsigned& n64, uint32_t* key_out) {
+                                              unsigned& n64, uint32_t* key_out, bool mixed) {
   T x0[4], u0[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -499,7 +502,7 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
   bool fb = false;
 #pragma unroll 1
   for (int stage = 0; stage < 4; ++stage) {
-    accel<T, MIXED>(g, F, C, xs, us, a, flags, n64);
+    accel<T>(g, F, C, xs, us, a, flags, n64, mixed);
     if (stage == 0) h = C.dt / gamma_step<T>(u0[3], a[3], C.inv_c, C.dt, &fb);
     const T wgt = (stage == 0 || stage == 3) ? T(1) : T(2);
     const T frac = (stage == 2) ? h : T(0.5) * h;
@@ -530,12 +533,10 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
   // deposit, J = rho gamma v
   if (finite && C.qmacro != T(0)) {
     const T gbar = C.gamma_in_j ? (u0[3] + u1[3]) / (T(2) * C.c) : T(1);
-    if constexpr (FAR)
-      deposit_lattice<Q, false>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
-    else if constexpr (MIXED)
-      deposit_lattice<Q, true>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
+    if constexpr (sizeof(T) == sizeof(float))
+      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed);
     else
-      deposit<T, Q, MIXED>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64);
+      deposit<T, Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {

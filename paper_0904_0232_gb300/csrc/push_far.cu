@@ -50,15 +50,15 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
     const uint32_t k = P.key[i];
     active = k != kDead && k != kNear;
   }
-  if (active) push_particle<float, Q, false, true>(g, F, P, C, i, st, flags, n64, P.key + i);
+  if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false);
   warp_status(st, flags, n64, active);
 }
 
-// One kernel for every particle, the path chosen per warp: a warp none of whose particles is
+// One kernel for every particle, the policy chosen per warp: a warp none of whose particles is
 // near (R(x_n) >= near_radius, the same criterion as the classification) takes the far-field
-// code; a warp with any near particle takes the FP32-mixed code with the FP64 policy.  Particles
-// are cell-sorted, so warps are nearly always homogeneous, and the near warps share every SM
-// with far warps: FP64 and FP32 work proceed side by side on their own pipes.
+// code; a warp with any near particle takes the FP32-mixed code.  Particles are cell-sorted, so
+// warps are nearly always homogeneous, and the near warps share every SM with far warps: FP64
+// and FP32 work proceed side by side on their own pipes.
 template <int Q, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
@@ -72,10 +72,12 @@ __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const F
     const float X = P.x[0][i] - C.xc, Y = P.x[1][i] - C.yc, Z = P.x[2][i] - C.zc;
     near = X * X + Y * Y + Z * Z < r_near2;
   }
+  // two inlined copies, each with the flag a constant: the far-field copy has no out-of-line
+  // calls at all (a call site in the loop would cost every warp registers and stack traffic)
   if (__any_sync(0xffffffffu, near)) {
-    if (active) push_particle<float, Q, true>(g, F, P, C, i, st, flags, n64, P.key + i);
+    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, true);
   } else {
-    if (active) push_particle<float, Q, false, true>(g, F, P, C, i, st, flags, n64, P.key + i);
+    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false);
   }
   warp_status(st, flags, n64, active);
 }
