@@ -401,40 +401,51 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float PI = sel3(K, P[1], P[2], P[0]), PJ = sel3(K, P[2], P[0], P[1]);
       const float i0 = (float)sel3(K, cy, cz, cx), j0 = (float)sel3(K, cz, cx, cy);
       const float cI = sel3(K, cen[1], cen[2], cen[0]), cJ = sel3(K, cen[2], cen[0], cen[1]);
-      // node lattice: sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J); AI, AJ the
-      // nodes' grid coordinates, XI, XJ relative to the centre
-      float AI[2 * Q], AJ[2 * Q], XI[2 * Q], XJ[2 * Q], wI[2], wJ[2];
+      // node lattice: sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J); AJ the nodes'
+      // grid coordinates along J, XJ relative to the centre.  The rows (along I) run in a rolled
+      // loop, the nodes of a row unrolled: a quarter of the code of a fully unrolled lattice, so
+      // the far-field and FP32-mixed copies of a kernel fit the instruction cache together.
+      const float wI0 = PI - i0, wI1 = i0 + 1.f - PI;
+      float AJ[2 * Q], XJ[2 * Q], wJ[2];
 #pragma unroll
       for (int sub = 0; sub < 2; ++sub) {
-        const float lo_i = sub ? PI : i0, hi_i = sub ? i0 + 1.f : PI;
         const float lo_j = sub ? PJ : j0, hi_j = sub ? j0 + 1.f : PJ;
-        wI[sub] = hi_i - lo_i;
         wJ[sub] = hi_j - lo_j;
 #pragma unroll
         for (int p = 0; p < Q; ++p) {
-          AI[sub * Q + p] = 0.5f * (lo_i + hi_i) + 0.5f * wI[sub] * (float)Gauss<Q>::x(p);
           AJ[sub * Q + p] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p);
-          XI[sub * Q + p] = AI[sub * Q + p] - cI;
           XJ[sub * Q + p] = AJ[sub * Q + p] - cJ;
         }
       }
       const bool z_is_K = K == 2, z_is_I = K == 1;
       const float pK = XK * XK - C.a2;
-      float S[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
+      float S00 = 0.f, S01 = 0.f, S10 = 0.f, S11 = 0.f;  // S[sub I][sub J]
+#pragma unroll 1
       for (int ia = 0; ia < 2 * Q; ++ia) {
-        const float XI2 = XI[ia] * XI[ia];
+        const int si = ia >= Q ? 1 : 0, pi = ia - si * Q;
+        float gx = (float)Gauss<Q>::x(0), gw = (float)Gauss<Q>::w(0);
+#pragma unroll
+        for (int t = 1; t < Q; ++t)
+          if (pi == t) {
+            gx = (float)Gauss<Q>::x(t);
+            gw = (float)Gauss<Q>::w(t);
+          }
+        const float lo_i = si ? PI : i0, w_i = si ? wI1 : wI0;
+        const float AIa = lo_i + 0.5f * w_i + 0.5f * w_i * gx;
+        const float XIa = AIa - cI;
+        const float XI2 = XIa * XIa;
+        float row0 = 0.f, row1 = 0.f;
 #pragma unroll
         for (int jb = 0; jb < 2 * Q; ++jb) {
           const float p = pK + XI2 + XJ[jb] * XJ[jb];
-          const float Z = z_is_K ? XK : (z_is_I ? XI[ia] : XJ[jb]);
+          const float Z = z_is_K ? XK : (z_is_I ? XIa : XJ[jb]);
           const float q = C.a2 * Z * Z;
           const float D2 = fmaf(p, p, 4.f * q);
           float r2 = 0.5f * (p + D2 * rsqrtf(D2));
           float val;
           if (mixed && (!(p > 0.f) || !(r2 >= C.r2_fp64))) {
-            const float ax = sel3(K, PK, AJ[jb], AI[ia]), ay = sel3(K, AI[ia], PK, AJ[jb]);
-            const float az = sel3(K, AJ[jb], AI[ia], PK);
+            const float ax = sel3(K, PK, AJ[jb], AIa), ay = sel3(K, AIa, PK, AJ[jb]);
+            const float az = sel3(K, AJ[jb], AIa, PK);
             const float2 rs = node_slow(C, p, q, ax, ay, az, p > 0.f);
             r2 = rs.x;
             n64 += (unsigned)rs.y;
@@ -448,7 +459,7 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
             if (K == 2) {
               fperp = __fdividef(C.two_m * r * (r2 - Z * Z), sig);
             } else {
-              const float num = fmaf(r, XK, K == 0 ? -C.a * XI[ia] : C.a * XJ[jb]);
+              const float num = fmaf(r, XK, K == 0 ? -C.a * XIa : C.a * XJ[jb]);
               const float rho2 = r2 + C.a2;
               const float rho4 = rho2 * rho2;
               fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
@@ -456,9 +467,21 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
             const float v = 1.f + fperp;
             val = v * rsqrtf(v);
           }
-          S[ia / Q][jb / Q] += (float)(Gauss<Q>::w(ia % Q) * Gauss<Q>::w(jb % Q)) * val;
+          if (jb < Q)
+            row0 += (float)Gauss<Q>::w(jb % Q) * val;
+          else
+            row1 += (float)Gauss<Q>::w(jb % Q) * val;
+        }
+        if (si == 0) {
+          S00 += gw * row0;
+          S01 += gw * row1;
+        } else {
+          S10 += gw * row0;
+          S11 += gw * row1;
         }
       }
+      const float wI[2] = {wI0, wI1};
+      const float S[2][2] = {{S00, S01}, {S10, S11}};
       // sub-rectangle areas; a node's weight is the area of the sub-rectangle opposite it
       const float A00 = S[1][1] * 0.25f * wI[1] * wJ[1];
       const float A10 = S[0][1] * 0.25f * wI[0] * wJ[1];
