@@ -45,9 +45,10 @@ ALG_FLOPS = {1: 3570, 2: 6600, 3: 11640}
 # Nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 
-# DRAM traffic of one push_deposit launch per particle, from an ncu capture (profiles/),
-# valid for the kernel source whose hash is recorded with it.
-PUSH_TRAFFIC = {"sha": "b10997ac32049e48", "bytes_per_particle": 1223.29e6 / 15.6e6}
+# DRAM bytes per particle-step of the push kernel (dram__bytes_read + dram__bytes_write of one
+# launch over its particles), from an ncu capture at the bench size, valid for the push sources
+# whose hash is recorded with it.
+PUSH_TRAFFIC = {"sha": "95be05176c50f531", "bytes_per_particle": 1239.66e6 / 15.61e6}
 
 
 def kernel_sha():

@@ -47,7 +47,7 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
-  grpic_tuning tune{4, 4, 1, 1, 0};
+  grpic_tuning tune{5, 4, 1, 1, 0};
   void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T

@@ -517,7 +517,7 @@ class Simulation:
     def profile(self, reset=False):
         return grpic_get_profile(self.handle, reset)
 
-    def set_tuning(self, far_min_blocks=4, near_blocks_per_sm=4, sort_interval=1, overlap=1, split=0):
+    def set_tuning(self, far_min_blocks=5, near_blocks_per_sm=4, sort_interval=1, overlap=1, split=0):
         grpic_set_tuning(self.handle, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split)
 
     def tuning(self):

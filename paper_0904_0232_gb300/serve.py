@@ -69,21 +69,43 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     finally:
         grpic_server_destroy(server)
     lat = np.array(lat)
-    return {"rate": rate, "arrivals": len(arrivals), "completed": int(lat.size),
+    # runs still queued or running when the wall-clock bound stopped the loop: their latency is
+    # at least (end - arrival), and arrivals not yet submitted count from their arrival time
+    cens = np.array([wall - a for a in pending.values()] + [wall - a for a in arrivals[nxt:] if a <= wall])
+    allv = np.concatenate([lat, cens]) if cens.size else lat
+    return {"rate": rate, "arrivals": len(arrivals), "completed": int(lat.size), "unfinished": int(cens.size),
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "p50_s_lower_bound_all": float(np.percentile(allv, 50)) if allv.size else None,
+            "p99_s_lower_bound_all": float(np.percentile(allv, 99)) if allv.size else None,
             "particle_steps_per_s": psteps / wall if wall > 0 else 0.0, "wall_s": wall}
+
+
+# Request mixes: grid edge, particles per cell per species, timesteps (each drawn uniformly), with
+# m in [1, 4] cells and a in [0, 0.99] m.  "full": the serving configuration's ranges; "light": a
+# mix one GPU serves without a growing queue at a few requests per second.
+MIXES = {
+    "full": dict(grids=(32, 48, 64, 96, 128), ppc=(1, 64), steps=(50, 500)),
+    "light": dict(grids=(32, 48, 64), ppc=(1, 8), steps=(50, 200)),
+}
 
 
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--rate", type=float, nargs="+", default=[2.0])
-    p.add_argument("--duration", type=float, default=10.0)
+    p.add_argument("--duration", type=float, default=10.0, help="seconds of Poisson arrivals per rate")
+    p.add_argument("--mix", choices=sorted(MIXES), default="light")
     p.add_argument("--budget-gb", type=float, default=100.0)
     p.add_argument("--slots", type=int, default=64)
+    p.add_argument("--max-wall", type=float, default=None, help="stop waiting for completions after this")
+    p.add_argument("--seed", type=int, default=0)
     args = p.parse_args()
     for r in args.rate:
-        print(json.dumps(serve_poisson(r, args.duration, int(args.budget_gb * 1e9), args.slots)), flush=True)
+        res = serve_poisson(r, args.duration, int(args.budget_gb * 1e9), args.slots, seed=args.seed,
+                            max_wall=args.max_wall, **MIXES[args.mix])
+        res.update(mix=args.mix, mix_ranges=MIXES[args.mix], budget_gb=args.budget_gb, slots=args.slots,
+                   arrival_window_s=args.duration)
+        print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

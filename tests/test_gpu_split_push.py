@@ -170,7 +170,7 @@ def test_tuning_validation():
     for bad in [(3, 2, 1, 1, 0), (7, 2, 1, 1, 0), (5, 0, 1, 1, 0), (5, 2, 0, 1, 0), (5, 2, 1, 2, 0), (5, 2, 1, 1, 2)]:
         with pytest.raises(GrpicError):
             sim.set_tuning(*bad)
-    assert sim.tuning()["far_min_blocks"] == 4
+    assert sim.tuning()["far_min_blocks"] == 5
 
 
 def test_seeded_fp64_ops_against_ieee():
