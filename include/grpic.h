@@ -298,6 +298,10 @@ grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t
  * chooses).  Takes effect at the next grpic_batch_step, which captures the graph again. */
 grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm);
 
+/* Status of one instance after the last grpic_batch_step (which returns the first instance error
+ * but reads every instance's device status): GRPIC_OK, or the error that instance reported. */
+grpic_status grpic_batch_ctx_status(const grpic_ctx* ctx);
+
 grpic_status grpic_batch_destroy(grpic_batch* b);
 
 /* ---------------------------------------------------------------------------------------
@@ -335,7 +339,9 @@ grpic_status grpic_server_create(size_t hbm_budget, int max_slots, grpic_alloc_f
  * GRPIC_ERR_INVALID for a bad request or one whose precision/quadrature/flags differ. */
 grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* ticket);
 
-/* Admit what fits, advance every running run one timestep, retire finished runs.
+/* Admit what fits, advance every running run one timestep, retire finished runs.  A run whose
+ * own step fails (non-finite state, a move of a cell or more) is retired with that status
+ * (grpic_poll returns it); the others go on.  The tick itself fails only on a CUDA error.
  * *running / *queued (may be NULL) receive the counts after the tick. */
 grpic_status grpic_server_tick(grpic_server* s, int* running, int* queued);
 

@@ -57,7 +57,8 @@ struct grpic_ctx {
   SortScratch sort{};
   SpeciesStore sp[kMaxSpecies];
   long long steps = 0;
-  long long pushes = 0;  // push stages run: particle x^4 is stored relative to c dt * pushes
+  long long pushes = 0;
+  grpic_status step_status = GRPIC_OK;  // status of this context after the last batched step  // push stages run: particle x^4 is stored relative to c dt * pushes
   int since_sort = 0;
   grpic_stats totals{};
   // tracing
@@ -1076,12 +1077,17 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
       c->sp[s].shadow_pending = false;
     }
   }
+  // every context's status is read (and kept in its step_status), so one failed instance does
+  // not hide the state of the others; the first error is returned
+  grpic_status first = GRPIC_OK;
   for (grpic_ctx* c : b->ctxs) {
-    const grpic_status st = read_status(c);
-    if (st != GRPIC_OK) return st;
+    c->step_status = read_status(c);
+    if (first == GRPIC_OK) first = c->step_status;
   }
-  return GRPIC_OK;
+  return first;
 }
+
+grpic_status grpic_batch_ctx_status(const grpic_ctx* c) { return c ? c->step_status : GRPIC_ERR_INVALID; }
 
 grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm) {
   if (!b || blocks_per_sm < 1 || blocks_per_sm > 32) return GRPIC_ERR_INVALID;

@@ -295,12 +295,19 @@ grpic_status grpic_server_tick(grpic_server* s, int* running, int* queued) {
       result = grpic_batch_create(ctxs.data(), (int)ctxs.size(), nullptr, &s->batch);
       s->dirty = false;
     }
-    if (result == GRPIC_OK) result = grpic_batch_step(s->batch, 1);
+    bool batch_ok = result == GRPIC_OK;
+    if (batch_ok) {
+      const grpic_status st = grpic_batch_step(s->batch, 1);
+      // instance errors are per run; anything else (a CUDA error) fails every running run
+      batch_ok = st == GRPIC_OK || st == GRPIC_ERR_CFL || st == GRPIC_ERR_NONFINITE || st == GRPIC_ERR_INVALID;
+      if (!batch_ok) result = st;
+    }
     std::vector<Run*> still;
     for (Run* r : s->running) {
       r->remaining -= 1;
-      if (result != GRPIC_OK) r->err = result;
-      if (r->remaining <= 0 || result != GRPIC_OK) {
+      const grpic_status own = batch_ok ? grpic_batch_ctx_status(r->ctx) : result;
+      if (own != GRPIC_OK) r->err = own;
+      if (r->remaining <= 0 || own != GRPIC_OK) {
         r->state = GRPIC_RUN_DONE;
         s->dirty = true;
       } else {

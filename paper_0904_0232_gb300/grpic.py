@@ -111,6 +111,7 @@ EXPORTS = {
     "grpic_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grpic_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "grpic_batch_set_blocks_per_sm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grpic_batch_ctx_status": (ctypes.c_int, [ctypes.c_void_p]),
     "grpic_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -393,11 +394,14 @@ def grpic_server_tick(server):
     return r.value, q.value
 
 
-def grpic_poll(server, ticket):
-    """(state, ctx handle or None); raises if the finished run failed."""
+def grpic_poll(server, ticket, with_status=False):
+    """(state, ctx handle or None); raises if the finished run failed, unless with_status, which
+    returns (state, ctx, status) instead (status GRPIC_OK, or the run's own error)."""
     st = ctypes.c_int(0)
     ctx = ctypes.c_void_p()
     code = load_library().grpic_poll(server, int(ticket), ctypes.byref(st), ctypes.byref(ctx))
+    if with_status:
+        return st.value, ctx.value, (GRPIC_OK if code == 7 else code)
     if code not in (GRPIC_OK, 7):
         raise GrpicError(code, "grpic_poll")
     return st.value, ctx.value
@@ -418,9 +422,10 @@ def grpic_server_destroy(server):
 
 
 def make_request(n, m, a, ppc, nsteps, seed, precision="fp32_mixed", c=1.0, dt=0.4, B=(0.0, 0.0, 0.05),
-                 species=((-1.0,), (1.0,)), wp_dt=0.1, u_th=0.1, r_min=None, quad_order=2):
+                 species=((-1.0,), (1.0,)), wp_dt=0.025, u_th=0.1, r_min=None, quad_order=2):
     """A run request: n^3 grid, pair plasma (q/m = -1, +1) by default, macro charge for the
-    stated omega_p dt at ppc particles per cell per species."""
+    stated omega_p dt at ppc particles per cell per species (0.025 by default: charge separation
+    near the hole stays bounded over 500 steps there, larger values overshoot the step limit)."""
     prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
     qms = [sp[0] for sp in species]
     q = (wp_dt / dt) ** 2 / (4.0 * np.pi * max(ppc, 1) * sum(abs(v) for v in qms))

@@ -12,8 +12,9 @@ import time
 
 import numpy as np
 
-from .grpic import (GRPIC_RUN_DONE, grpic_get_stats, grpic_poll, grpic_request_bytes, grpic_server_create,
-                    grpic_server_destroy, grpic_server_release, grpic_server_tick, grpic_submit, make_request)
+from .grpic import (GRPIC_OK, GRPIC_RUN_DONE, STATUS_NAMES, grpic_get_stats, grpic_poll, grpic_request_bytes,
+                    grpic_server_create, grpic_server_destroy, grpic_server_release, grpic_server_tick,
+                    grpic_submit, make_request)
 
 
 def sample_requests(n, seed, grids=(32, 48, 64), ppc=(1, 8), steps=(50, 200), m=(1.0, 4.0), spin_max=0.99):
@@ -42,6 +43,7 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     server = grpic_server_create(budget_bytes, slots)
     pending = {}   # ticket -> arrival time
     lat = []
+    failed = []
     psteps = 0
     nxt = 0
     t0 = time.perf_counter()
@@ -58,10 +60,15 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
                 grpic_server_tick(server)
                 done_now = time.perf_counter() - t0
                 for tk in list(pending):
-                    state, ctx = grpic_poll(server, tk)
+                    state, ctx, status = grpic_poll(server, tk, with_status=True)
                     if state == GRPIC_RUN_DONE:
-                        psteps += grpic_get_stats(ctx)["particle_steps"]
-                        lat.append(done_now - pending.pop(tk))
+                        if ctx:
+                            psteps += grpic_get_stats(ctx)["particle_steps"]
+                        if status == GRPIC_OK:
+                            lat.append(done_now - pending.pop(tk))
+                        else:
+                            failed.append(STATUS_NAMES.get(status, status))
+                            pending.pop(tk)
                         grpic_server_release(server, tk)
             else:
                 time.sleep(min(0.001, max(0.0, arrivals[nxt] - now)) if nxt < len(arrivals) else 0)
@@ -74,6 +81,7 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     cens = np.array([wall - a for a in pending.values()] + [wall - a for a in arrivals[nxt:] if a <= wall])
     allv = np.concatenate([lat, cens]) if cens.size else lat
     return {"rate": rate, "arrivals": len(arrivals), "completed": int(lat.size), "unfinished": int(cens.size),
+            "failed": len(failed), "failed_status": sorted(set(failed)),
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "p50_s_lower_bound_all": float(np.percentile(allv, 50)) if allv.size else None,
