@@ -215,6 +215,8 @@ grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t count
  *   near_blocks_per_sm: persistent blocks per SM of the near-hole kernel (>= 1)
  *   sort_interval:      counting sort every k timesteps (>= 1)
  *   overlap:            split = 1 only, as above
+ *   j_tile:             split = 0, Q = 2: 1 accumulates J per block in a shared-memory FP32 tile over
+ *                       the nodes the block's particles can reach, added to the FP64 J once per node
  * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */
 typedef struct {
   int far_min_blocks;
@@ -222,6 +224,7 @@ typedef struct {
   int sort_interval;
   int overlap;
   int split;
+  int j_tile;
 } grpic_tuning;
 grpic_status grpic_set_tuning(grpic_ctx* ctx, const grpic_tuning* t);
 grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);
@@ -280,11 +283,14 @@ typedef struct grpic_batch grpic_batch;
 
 /* Group n contexts with the same precision, quadrature order and field-update form.  The
  * batch builds one device descriptor per instance and tables of (instance, work block) items
- * for every stage; each batched stage is a persistent grid-stride launch over such a table,
- * and one step's stage sequence is captured once in a CUDA graph on a stream the batch owns
- * (`stream` is unused).  The contexts stay owned by the caller and must outlive the batch; the
- * batch is built for the particle counts loaded at creation (re-create it after loading more).
- * Every batched step sorts.  Returns GRPIC_ERR_INVALID for mismatched contexts. */
+ * for every stage; each batched stage is one launch over such a table (persistent grid-stride
+ * for the field and sort stages, one block per item for the push), and one step's stage sequence
+ * is captured once in a CUDA graph on a stream the batch owns (`stream` is unused).  The
+ * contexts stay owned by the caller and must outlive every grpic_batch_step and
+ * grpic_batch_info of the batch; grpic_batch_destroy touches none of them (the batch keeps its own
+ * copy of the first context's allocator).  The batch is built for the particle counts loaded at
+ * creation (re-create it after loading more).  Every batched step sorts.  Returns
+ * GRPIC_ERR_INVALID for mismatched contexts. */
 grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grpic_batch** out);
 
 /* Advance every instance nsteps timesteps (graph replays), ordered after each context's pending

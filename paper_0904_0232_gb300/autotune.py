@@ -2,7 +2,8 @@
 whether the FP32-mixed push runs as one kernel with a per-warp choice of code or split into
 near-hole and far-field kernels, the register budget of the far-field code (resident blocks
 per SM), the persistent blocks per SM of the near-hole kernel, whether that kernel overlaps the
-far one on a second stream, and the sort interval.
+far one on a second stream, whether the per-warp kernel accumulates J in shared-memory tiles, and
+the sort interval.
 
 Coordinate descent: starting from the current choice, each knob in turn is set to each of its
 values while the others stay fixed, and the fastest is kept; two rounds.  A trial times
@@ -21,6 +22,7 @@ import os
 
 CHOICES = {
     "split": (0, 1),
+    "j_tile": (0, 1),
     "far_min_blocks": (4, 5, 6),
     "near_blocks_per_sm": (1, 2, 4),
     "overlap": (0, 1),

@@ -47,7 +47,7 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
-  grpic_tuning tune{5, 4, 1, 1, 0};
+  grpic_tuning tune{5, 4, 1, 1, 0, 0};
   void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T
@@ -164,7 +164,7 @@ void enqueue_select_push(grpic_ctx* c) {
     if (!S.loaded || S.n == 0) continue;
     refresh_count(S);
     launch_push_select(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
-                       c->tune.far_min_blocks, c->stream);
+                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->stream);
     c->launches += 1;
   }
 }
@@ -805,7 +805,7 @@ grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
   if (!c || !t) return GRPIC_ERR_INVALID;
   if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
       t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1) ||
-      (t->split != 0 && t->split != 1))
+      (t->split != 0 && t->split != 1) || (t->j_tile != 0 && t->j_tile != 1))
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   c->cfg.sort_interval = t->sort_interval;
@@ -850,6 +850,11 @@ grpic_status grpic_get_profile(grpic_ctx* c, double times_ms[6], int64_t counts[
 // ---- batched engine ----------------------------------------------------------------------------
 struct grpic_batch {
   std::vector<grpic_ctx*> ctxs;
+  // the batch's own copy of the device allocator (its tables must be freed with it even after
+  // the contexts it was built from are gone)
+  grpic_alloc_fn alloc = nullptr;
+  grpic_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
   cudaStream_t stream = nullptr;  // created by the batch: capturable, ordered with the contexts by events
   bool mixed = false, literal = false;
   int quad = 2;
@@ -872,9 +877,23 @@ struct grpic_batch {
 namespace {
 
 void* batch_alloc(grpic_batch* b, size_t bytes) {
-  void* p = dev_alloc(b->ctxs[0], bytes);
+  void* p = nullptr;
+  if (b->alloc) {
+    p = b->alloc(bytes, b->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
   if (p) b->allocs.push_back(p);
   return p;
+}
+
+void batch_free(grpic_batch* b, void* p) {
+  if (!p) return;
+  if (b->free_fn)
+    b->free_fn(p, b->alloc_user);
+  else
+    cudaFree(p);
 }
 
 template <typename T>
@@ -1008,6 +1027,9 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
       return GRPIC_ERR_INVALID;
   grpic_batch* b = new grpic_batch();
   b->ctxs.assign(ctxs, ctxs + n);
+  b->alloc = ctxs[0]->cfg.alloc;
+  b->free_fn = ctxs[0]->cfg.free_fn;
+  b->alloc_user = ctxs[0]->cfg.alloc_user;
   b->mixed = ctxs[0]->mixed;
   b->quad = ctxs[0]->g.quad_order;
   b->literal = literal_fields(ctxs[0]);
@@ -1112,7 +1134,7 @@ grpic_status grpic_batch_destroy(grpic_batch* b) {
   if (!b) return GRPIC_ERR_INVALID;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void* p : b->allocs) dev_free(b->ctxs[0], p);
+  for (void* p : b->allocs) batch_free(b, p);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;

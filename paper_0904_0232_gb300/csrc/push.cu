@@ -56,10 +56,10 @@ __global__ void k_near_keys(uint32_t* __restrict__ key, const uint32_t* __restri
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) key[list[j]] = keys[j];
 }
 
-// Batched: grid-stride over (instance * 4 + species, block) work items; each block belongs to
-// one instance and species, so the warp-level status stays per instance.  The block's instance
-// descriptor is staged in shared memory and reloaded only when the instance changes (a CTA's
-// consecutive grid-stride blocks mostly stay inside one instance).  FP32-mixed: each warp takes
+// Batched: (instance * 4 + species, block) work items, one per CTA as launched (the loop also
+// serves a smaller grid); each block belongs to one instance and species, so the warp-level
+// status stays per instance.  The instance descriptor is staged in shared memory, reloaded only
+// when the instance changes.  FP32-mixed: each warp takes
 // the far-field code unless one of its particles lies within the instance's near_radius.
 template <typename T, int Q, bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>* __restrict__ desc,
@@ -249,7 +249,10 @@ void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uin
 
 template <typename T, bool MIXED>
 void launch_batch_push_q(const BatchTables<T>& bt, int quad_order, cudaStream_t stream) {
-  const unsigned nb = (unsigned)std::min(bt.npart, bt.persist_blocks);
+  // one block per work item: each block stages its instance descriptor once, and the hardware
+  // scheduler balances instances of very different cost (a persistent grid-stride loop would
+  // cross instance boundaries, and reload the descriptor, at nearly every item)
+  const unsigned nb = (unsigned)bt.npart;
   if (bt.npart == 0) return;
   if (quad_order == 1)
     k_push_deposit_batch<T, 1, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);

@@ -54,6 +54,14 @@ struct Gauss<3> {
   __device__ static constexpr double w(int i) { return i == 1 ? 8.0 / 9.0 : 5.0 / 9.0; }
 };
 
+// A block's shared-memory tile of J (FP32; three component planes of nx * ny * nz nodes starting
+// at node (ox, oy, oz)), or tile == nullptr: deposits go straight to the global FP64 J.
+struct JTile {
+  float* tile = nullptr;
+  int ox = 0, oy = 0, oz = 0;
+  int nx = 0, ny = 0, nz = 0;
+};
+
 // Constants of one push launch in the arithmetic type T, built once on the host (once per
 // block in the batched kernel), plus their FP64 values for the promoted evaluations.
 template <typename T>
@@ -103,6 +111,11 @@ __host__ __device__ inline Consts<T> make_consts(const Grid& g, const Species& s
 
 __device__ __forceinline__ double to_f64(float v) { return widen(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
+
+template <typename T>
+__device__ __forceinline__ T lerp(T a, T b, T w) {
+  return fma(w, b - a, a);
+}
 
 template <typename T>
 __device__ __forceinline__ T sel3(int i, T a, T b, T c) {
@@ -195,18 +208,13 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
     const int i0 = hx ? ih[0] : ii[0], j0 = hy ? ih[1] : ii[1], k0 = hz ? ih[2] : ii[2];
     const T w0 = hx ? wh[0] : wi[0], w1 = hy ? wh[1] : wi[1], w2 = hz ? wh[2] : wi[2];
     const T* arr = comp < 3 ? F.d[comp] : F.b[comp - 3];
-    const long long base = ((long long)k0 * g.ny + j0) * g.nx + i0;
-    T s = T(0);
-#pragma unroll
-    for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-      for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-        for (int di = 0; di < 2; ++di) {
-          const T W = (di ? w0 : T(1) - w0) * (dj ? w1 : T(1) - w1) * (dk ? w2 : T(1) - w2);
-          s += W * __ldg(arr + base + dk * sz + dj * sy + di);
-        }
-    val[comp] = s;
+    const T* q = arr + (((long long)k0 * g.ny + j0) * g.nx + i0);
+    // trilinear as nested linear interpolations (the weight products expanded, 7 lerps)
+    const T c00 = lerp(__ldg(q), __ldg(q + 1), w0);
+    const T c10 = lerp(__ldg(q + sy), __ldg(q + sy + 1), w0);
+    const T c01 = lerp(__ldg(q + sz), __ldg(q + sz + 1), w0);
+    const T c11 = lerp(__ldg(q + sz + sy), __ldg(q + sz + sy + 1), w0);
+    val[comp] = lerp(lerp(c00, c10, w1), lerp(c01, c11, w1), w2);
   }
   const T d[3] = {val[0], val[1], val[2]};
   const T b[3] = {val[3], val[4], val[5]};
@@ -364,7 +372,7 @@ __device__ __noinline__ float2 node_slow(const Consts<float>& C, float p, float 
 template <int Q>
 __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<float>& F, const Consts<float>& C,
                                                 const float x0[3], const float dx[3], float qg, float inv_dt,
-                                                unsigned& flags, unsigned& n64, bool mixed) {
+                                                unsigned& flags, unsigned& n64, bool mixed, const JTile& jt) {
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
   float s1[3], s2[3];
@@ -406,19 +414,26 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       // loop, the nodes of a row unrolled: a quarter of the code of a fully unrolled lattice, so
       // the far-field and FP32-mixed copies of a kernel fit the instruction cache together.
       const float wI0 = PI - i0, wI1 = i0 + 1.f - PI;
-      float AJ[2 * Q], XJ[2 * Q], wJ[2];
+      // Per node the quartic needs p = R^2 - a^2 and q = a^2 z^2, k_K's numerator the spin term
+      // -a x^I (K = 0) or +a x^J (K = 1); z is x^K, x^I or x^J (K = 2, 1, 0).  Each of these is a
+      // sum of a face constant, a row term and a column term, formed once: a node adds them.
+      const float pK = XK * XK - C.a2;
+      const float qK = K == 2 ? C.a2 * XK * XK : 0.f;
+      float AJ[2 * Q], XJ[2 * Q], pJ[2 * Q], qJ[2 * Q], tJ[2 * Q], wJ[2];
 #pragma unroll
       for (int sub = 0; sub < 2; ++sub) {
         const float lo_j = sub ? PJ : j0, hi_j = sub ? j0 + 1.f : PJ;
         wJ[sub] = hi_j - lo_j;
 #pragma unroll
         for (int p = 0; p < Q; ++p) {
-          AJ[sub * Q + p] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p);
-          XJ[sub * Q + p] = AJ[sub * Q + p] - cJ;
+          const int jb = sub * Q + p;
+          AJ[jb] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p);
+          XJ[jb] = AJ[jb] - cJ;
+          pJ[jb] = XJ[jb] * XJ[jb];
+          qJ[jb] = K == 0 ? C.a2 * pJ[jb] : 0.f;
+          tJ[jb] = K == 1 ? C.a * XJ[jb] : 0.f;
         }
       }
-      const bool z_is_K = K == 2, z_is_I = K == 1;
-      const float pK = XK * XK - C.a2;
       float S00 = 0.f, S01 = 0.f, S10 = 0.f, S11 = 0.f;  // S[sub I][sub J]
 #pragma unroll 1
       for (int ia = 0; ia < 2 * Q; ++ia) {
@@ -434,12 +449,14 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
         const float AIa = lo_i + 0.5f * w_i + 0.5f * w_i * gx;
         const float XIa = AIa - cI;
         const float XI2 = XIa * XIa;
+        const float pRow = pK + XI2;
+        const float qRow = qK + (K == 1 ? C.a2 * XI2 : 0.f);
+        const float tRow = K == 0 ? -C.a * XIa : 0.f;
         float row0 = 0.f, row1 = 0.f;
 #pragma unroll
         for (int jb = 0; jb < 2 * Q; ++jb) {
-          const float p = pK + XI2 + XJ[jb] * XJ[jb];
-          const float Z = z_is_K ? XK : (z_is_I ? XIa : XJ[jb]);
-          const float q = C.a2 * Z * Z;
+          const float p = pRow + pJ[jb];
+          const float q = qRow + qJ[jb];
           const float D2 = fmaf(p, p, 4.f * q);
           float r2 = 0.5f * (p + D2 * rsqrtf(D2));
           float val;
@@ -457,9 +474,9 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
             const float sig = fmaf(r2, r2, q);
             float fperp;
             if (K == 2) {
-              fperp = __fdividef(C.two_m * r * (r2 - Z * Z), sig);
+              fperp = __fdividef(C.two_m * r * (r2 - XK * XK), sig);
             } else {
-              const float num = fmaf(r, XK, K == 0 ? -C.a * XIa : C.a * XJ[jb]);
+              const float num = fmaf(r, XK, tRow + tJ[jb]);
               const float rho2 = r2 + C.a2;
               const float rho4 = rho2 * rho2;
               fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
@@ -488,12 +505,25 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float A01 = S[1][0] * 0.25f * wI[1] * wJ[0];
       const float A11 = S[0][0] * 0.25f * wI[0] * wJ[0];
       const float rFA = __fdividef(1.f, A00 + A10 + A01 + A11);
-      const long long stI = sel3(K, sy, sz, 1ll), stJ = sel3(K, sz, 1ll, sy);
-      double* JK = sel3(K, F.J[0], F.J[1], F.J[2]);
-      atomicAdd(JK + base, widen(flux * (A00 * rFA)));
-      atomicAdd(JK + base + stI, widen(flux * (A10 * rFA)));
-      atomicAdd(JK + base + stJ, widen(flux * (A01 * rFA)));
-      atomicAdd(JK + base + stI + stJ, widen(flux * (A11 * rFA)));
+      // the face's four nodes: into the block's J tile when they lie in it, else into global J
+      const int tx = cx - jt.ox, ty = cy - jt.oy, tz = cz - jt.oz;
+      if (jt.tile && (unsigned)tx < (unsigned)(jt.nx - 1) && (unsigned)ty < (unsigned)(jt.ny - 1) &&
+          (unsigned)tz < (unsigned)(jt.nz - 1)) {
+        const int tsy = jt.nx, tsz = jt.nx * jt.ny;
+        const int tI = sel3(K, tsy, tsz, 1), tJ = sel3(K, tsz, 1, tsy);
+        float* TK = jt.tile + K * tsz * jt.nz + (tz * jt.ny + ty) * jt.nx + tx;
+        atomicAdd(TK, flux * (A00 * rFA));
+        atomicAdd(TK + tI, flux * (A10 * rFA));
+        atomicAdd(TK + tJ, flux * (A01 * rFA));
+        atomicAdd(TK + tI + tJ, flux * (A11 * rFA));
+      } else {
+        const long long stI = sel3(K, sy, sz, 1ll), stJ = sel3(K, sz, 1ll, sy);
+        double* JK = sel3(K, F.J[0], F.J[1], F.J[2]);
+        atomicAdd(JK + base, widen(flux * (A00 * rFA)));
+        atomicAdd(JK + base + stI, widen(flux * (A10 * rFA)));
+        atomicAdd(JK + base + stJ, widen(flux * (A01 * rFA)));
+        atomicAdd(JK + base + stI + stJ, widen(flux * (A11 * rFA)));
+      }
     }
   }
 }
@@ -505,7 +535,8 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
 template <typename T, int Q>
 __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F, const Particles<T>& P,
                                               const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
-                                              unsigned& n64, uint32_t* key_out, bool mixed) {
+                                              unsigned& n64, uint32_t* key_out, bool mixed,
+                                              const JTile& jt = JTile()) {
   T x0[4], u0[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -557,7 +588,7 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
   if (finite && C.qmacro != T(0)) {
     const T gbar = C.gamma_in_j ? (u0[3] + u1[3]) / (T(2) * C.c) : T(1);
     if constexpr (sizeof(T) == sizeof(float))
-      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed);
+      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed, jt);
     else
       deposit<T, Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
   }

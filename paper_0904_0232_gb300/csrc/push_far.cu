@@ -59,7 +59,15 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
 // code; a warp with any near particle takes the FP32-mixed code.  Particles are cell-sorted, so
 // warps are nearly always homogeneous, and the near warps share every SM with far warps: FP64
 // and FP32 work proceed side by side on their own pipes.
-template <int Q, int MINB>
+//
+// TILE: the block accumulates J in a shared-memory FP32 tile over the nodes its particles can
+// reach -- [cmin - 1, cmax + 2] per axis, cmin..cmax the cells of the block's x_n (|dx| < 1) --
+// and adds the nonzero entries to the global FP64 J once at the end (one atomic per node instead
+// of one per contribution).  A block whose tile would exceed kJTileFloats, and any face outside
+// the tile, deposits straight to global J.
+constexpr int kJTileFloats = 3072;
+
+template <int Q, int MINB, bool TILE>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
                                                            float r_near2, DevStatus* st) {
@@ -68,18 +76,77 @@ __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const F
   bool active = i < P.n && i < (long long)(*P.n_dev);
   if (active) active = P.key[i] != kDead;
   bool near = false;
+  float x0[3] = {0.f, 0.f, 0.f};
   if (active) {
-    const float X = P.x[0][i] - C.xc, Y = P.x[1][i] - C.yc, Z = P.x[2][i] - C.zc;
+    x0[0] = P.x[0][i];
+    x0[1] = P.x[1][i];
+    x0[2] = P.x[2][i];
+    const float X = x0[0] - C.xc, Y = x0[1] - C.yc, Z = x0[2] - C.zc;
     near = X * X + Y * Y + Z * Z < r_near2;
+  }
+  JTile jt;
+  if constexpr (TILE) {
+    __shared__ float s_tile[kJTileFloats];
+    __shared__ int s_lo[3][4], s_hi[3][4];
+    __shared__ JTile s_jt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int c = (int)floorf(x0[ax]);
+      const int lo = __reduce_min_sync(0xffffffffu, active ? c : 0x7fffffff);
+      const int hi = __reduce_max_sync(0xffffffffu, active ? c : -0x7fffffff);
+      if (lane == 0) {
+        s_lo[ax][warp] = lo;
+        s_hi[ax][warp] = hi;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int lo[3], hi[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        lo[ax] = min(min(s_lo[ax][0], s_lo[ax][1]), min(s_lo[ax][2], s_lo[ax][3]));
+        hi[ax] = max(max(s_hi[ax][0], s_hi[ax][1]), max(s_hi[ax][2], s_hi[ax][3]));
+      }
+      JTile t;
+      if (lo[0] <= hi[0]) {
+        t.ox = lo[0] - 1;
+        t.oy = lo[1] - 1;
+        t.oz = lo[2] - 1;
+        t.nx = hi[0] - lo[0] + 4;
+        t.ny = hi[1] - lo[1] + 4;
+        t.nz = hi[2] - lo[2] + 4;
+        if ((long long)3 * t.nx * t.ny * t.nz <= kJTileFloats) t.tile = s_tile;
+      }
+      s_jt = t;
+    }
+    __syncthreads();
+    jt = s_jt;
+    if (jt.tile)
+      for (int e = threadIdx.x; e < 3 * jt.nx * jt.ny * jt.nz; e += blockDim.x) s_tile[e] = 0.f;
+    __syncthreads();
   }
   // two inlined copies, each with the flag a constant: the far-field copy has no out-of-line
   // calls at all (a call site in the loop would cost every warp registers and stack traffic)
   if (__any_sync(0xffffffffu, near)) {
-    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, true);
+    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, true, jt);
   } else {
-    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false);
+    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false, jt);
   }
   warp_status(st, flags, n64, active);
+  if constexpr (TILE) {
+    __syncthreads();
+    if (jt.tile) {
+      const int plane = jt.nx * jt.ny * jt.nz;
+      for (int e = threadIdx.x; e < 3 * plane; e += blockDim.x) {
+        const float v = jt.tile[e];
+        if (v == 0.f) continue;
+        const int comp = e / plane, rem = e - comp * plane;
+        const int ix = jt.ox + rem % jt.nx, iy = jt.oy + (rem / jt.nx) % jt.ny, iz = jt.oz + rem / (jt.nx * jt.ny);
+        if (ix < g.nx && iy < g.ny && iz < g.nz)
+          atomicAdd(F.J[comp] + ((long long)iz * g.ny + iy) * g.nx + ix, widen(v));
+      }
+    }
+  }
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -117,20 +184,24 @@ void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<floa
 }
 
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, cudaStream_t stream) {
+                        DevStatus* st, int minb, bool tile, cudaStream_t stream) {
   if (P.n <= 0) return;
   const unsigned nb = blocks_for(P.n, 128);
   const Consts<float> C = make_consts<float>(g, sp);
   const double rn = near_radius(g);
   const float r_near2 = (float)(rn * rn);
   if (g.quad_order == 1)
-    k_push_select<1, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
   else if (g.quad_order == 3)
-    k_push_select<3, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+  else if (tile && minb >= 5)
+    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+  else if (tile)
+    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
   else if (minb >= 5)
-    k_push_select<2, 5><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
   else
-    k_push_select<2, 4><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
 }
 
 }  // namespace grpic

@@ -315,7 +315,9 @@ grpic_status grpic_server_tick(grpic_server* s, int* running, int* queued) {
       }
     }
     s->running.swap(still);
-    if (s->running.empty() && s->batch) {
+    // a batch built over runs that have now finished refers to contexts the caller may release
+    // before the next tick: drop it now (the next tick builds one over the running runs)
+    if ((s->dirty || s->running.empty()) && s->batch) {
       grpic_batch_destroy(s->batch);
       s->batch = nullptr;
     }

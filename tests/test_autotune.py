@@ -6,15 +6,15 @@ from paper_0904_0232_gb300 import autotune
 class FakeSim:
     def __init__(self, cost):
         self.cost = cost
-        self.t = dict(far_min_blocks=5, near_blocks_per_sm=2, sort_interval=1, overlap=1, split=0)
+        self.t = dict(far_min_blocks=5, near_blocks_per_sm=2, sort_interval=1, overlap=1, split=0, j_tile=0)
         self.calls = 0
 
     def tuning(self):
         return dict(self.t)
 
-    def set_tuning(self, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split):
+    def set_tuning(self, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
         self.t = dict(far_min_blocks=far_min_blocks, near_blocks_per_sm=near_blocks_per_sm,
-                      sort_interval=sort_interval, overlap=overlap, split=split)
+                      sort_interval=sort_interval, overlap=overlap, split=split, j_tile=j_tile)
 
 
 def timer(sim, steps):
@@ -22,29 +22,30 @@ def timer(sim, steps):
     return sim.cost(**sim.t)
 
 
-def separable(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split):
+def separable(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
     return ({4: 3.0, 5: 1.0, 6: 2.0}[far_min_blocks] + {1: 0.5, 2: 0.7, 4: 0.2}[near_blocks_per_sm]
-            + {1: 0.9, 2: 0.3, 4: 0.4}[sort_interval] + {0: 0.05, 1: 0.0}[overlap] + {0: 0.1, 1: 0.0}[split])
+            + {1: 0.9, 2: 0.3, 4: 0.4}[sort_interval] + {0: 0.05, 1: 0.0}[overlap] + {0: 0.1, 1: 0.0}[split]
+            + {0: 0.0, 1: 0.02}[j_tile])
 
 
 def test_coordinate_descent_finds_separable_minimum(tmp_path):
     sim = FakeSim(separable)
     r = autotune.tune(sim, "w", cache=str(tmp_path / "t.json"), timer=timer, device="fake")
-    assert r["tuning"] == dict(far_min_blocks=5, near_blocks_per_sm=4, sort_interval=2, overlap=1, split=1)
+    assert r["tuning"] == dict(far_min_blocks=5, near_blocks_per_sm=4, sort_interval=2, overlap=1, split=1, j_tile=0)
     assert sim.t == r["tuning"] and not r["cached"]
     assert abs(r["ms_per_step"] - separable(**r["tuning"])) < 1e-12
 
 
 def test_coupled_cost_second_round(tmp_path):
     # the best near setting depends on the far setting: one round is not enough
-    def coupled(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split):
+    def coupled(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
         table = {(4, 1): 1.0, (4, 2): 5.0, (4, 4): 5.0, (5, 1): 5.0, (5, 2): 3.0, (5, 4): 5.0,
                  (6, 1): 5.0, (6, 2): 5.0, (6, 4): 0.5}
         return table[(far_min_blocks, near_blocks_per_sm)] + 0.1 * sort_interval + 0.01 * overlap
     sim = FakeSim(coupled)
     r = autotune.tune(sim, "c", cache=str(tmp_path / "t.json"), timer=timer, device="fake", rounds=3)
-    best = min(coupled(f, n, 1, 0, 0) for f in (4, 5, 6) for n in (1, 2, 4))
-    assert r["ms_per_step"] <= coupled(5, 2, 1, 1, 0)  # never worse than the start
+    best = min(coupled(f, n, 1, 0, 0, 0) for f in (4, 5, 6) for n in (1, 2, 4))
+    assert r["ms_per_step"] <= coupled(5, 2, 1, 1, 0, 0)  # never worse than the start
     assert r["tuning"]["sort_interval"] == 1
     assert r["ms_per_step"] >= best
 

@@ -102,3 +102,23 @@ def test_refused_requests():
     with pytest.raises(GrpicError):
         grpic_submit(server, make_request(n=20, m=1.0, a=0.5, ppc=1, nsteps=2, seed=2, precision="fp64"))
     grpic_server_destroy(server)
+
+
+def test_release_while_others_run():
+    """A finished run released at once (its context destroyed) while others keep running: the
+    server must not touch the released context again."""
+    server = grpic_server_create(int(4e9), 8)
+    ta = grpic_submit(server, make_request(n=20, m=1.0, a=0.5, ppc=1, nsteps=2, seed=41))
+    tb = grpic_submit(server, make_request(n=24, m=1.5, a=1.0, ppc=1, nsteps=8, seed=42))
+    tc = grpic_submit(server, make_request(n=20, m=2.0, a=0.0, ppc=2, nsteps=5, seed=43))
+    done = set()
+    for _ in range(20):
+        grpic_server_tick(server)
+        for tk in (ta, tb, tc):
+            if tk not in done and grpic_poll(server, tk)[0] == GRPIC_RUN_DONE:
+                done.add(tk)
+                grpic_server_release(server, tk)
+        if len(done) == 3:
+            break
+    assert done == {ta, tb, tc}
+    grpic_server_destroy(server)

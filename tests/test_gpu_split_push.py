@@ -104,16 +104,18 @@ def test_split_equals_single_kernel(mode):
         assert np.abs(xs - xq).max() <= 1e-5 * np.abs(xq).max()
 
 
-@pytest.mark.parametrize("far,near,overlap,split", [(4, 1, 1, 1), (5, 2, 0, 1), (6, 3, 1, 1), (5, 4, 0, 1),
-                                                   (4, 4, 1, 0), (5, 4, 1, 0)])
-def test_tuning_variants_agree(far, near, overlap, split):
+@pytest.mark.parametrize("far,near,overlap,split,j_tile", [(4, 1, 1, 1, 0), (5, 2, 0, 1, 0), (6, 3, 1, 1, 0),
+                                                          (5, 4, 0, 1, 0), (4, 4, 1, 0, 0), (5, 4, 1, 0, 0),
+                                                          (4, 4, 1, 0, 1), (5, 4, 1, 0, 1)])
+def test_tuning_variants_agree(far, near, overlap, split, j_tile):
     wl = _workload(seed=33)
     ref = oracle_start(wl)
     base = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
     var = gpu_from_oracle(ref, wl, "fp32_mixed")
-    var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap, split=split)
+    var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap, split=split,
+                   j_tile=j_tile)
     assert var.tuning() == dict(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap,
-                                split=split)
+                                split=split, j_tile=j_tile)
     _push_once(base)
     _push_once(var)
     (pb, Jb, sb), (pv, Jv, sv) = _state(base), _state(var)
@@ -167,7 +169,8 @@ def test_tuning_validation():
     wl = _workload(seed=35)
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, "fp32_mixed")
-    for bad in [(3, 2, 1, 1, 0), (7, 2, 1, 1, 0), (5, 0, 1, 1, 0), (5, 2, 0, 1, 0), (5, 2, 1, 2, 0), (5, 2, 1, 1, 2)]:
+    for bad in [(3, 2, 1, 1, 0), (7, 2, 1, 1, 0), (5, 0, 1, 1, 0), (5, 2, 0, 1, 0), (5, 2, 1, 2, 0), (5, 2, 1, 1, 2),
+                (5, 2, 1, 1, 0, 2)]:
         with pytest.raises(GrpicError):
             sim.set_tuning(*bad)
     assert sim.tuning()["far_min_blocks"] == 5
@@ -183,3 +186,27 @@ def test_seeded_fp64_ops_against_ieee():
 def test_integer_conversions_match_hardware():
     bad = grpic_check_conversions(1 << 24)
     assert bad == dict(widen=0, narrow=0)
+
+
+def test_j_tile_against_oracle_and_over_steps():
+    wl = _workload(seed=37)
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, "fp32_mixed")
+    sim.set_tuning(j_tile=1)
+    plain = gpu_from_oracle(ref, wl, "fp32_mixed")
+    ref.zero_j()
+    ref.push_deposit()
+    _push_once(sim)
+    _push_once(plain)
+    _, _, J = sim.get_fields()
+    _, _, Jr = ref.get_fields()
+    _, _, Jp = plain.get_fields()
+    assert rel_l2(J, Jr) <= TOL["fp32_mixed"]["J"] * 10
+    # FP32 partial sums per block instead of one FP64 add per contribution: within FP32 rounding
+    assert rel_l2(J, Jp) <= 1e-6
+    sim.step(3)
+    plain.step(3)
+    (ps, Js, _), (pp, Jq, _) = _state(sim), _state(plain)
+    for (xs, us, i_s), (xq, uq, iq) in zip(ps, pp):
+        assert np.array_equal(i_s, iq)
+        assert np.abs(xs - xq).max() <= 1e-5 * np.abs(xq).max()
