@@ -217,6 +217,8 @@ grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t count
  *   overlap:            split = 1 only, as above
  *   j_tile:             split = 0, Q = 2: 1 accumulates J per block in a shared-memory FP32 tile over
  *                       the nodes the block's particles can reach, added to the FP64 J once per node
+ *   spread:             split = 0: 1 maps blocks to particle chunks by a permutation, spreading the
+ *                       near-hole (FP64-heavy) chunks over the launch; 0 keeps them in order
  * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */
 typedef struct {
   int far_min_blocks;
@@ -225,6 +227,7 @@ typedef struct {
   int overlap;
   int split;
   int j_tile;
+  int spread;
 } grpic_tuning;
 grpic_status grpic_set_tuning(grpic_ctx* ctx, const grpic_tuning* t);
 grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);

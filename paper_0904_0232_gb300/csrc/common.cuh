@@ -122,7 +122,7 @@ void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uin
 // Unsplit alternative: one launch, far-field or FP32-mixed code chosen per warp by the same
 // near_radius criterion.
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, cudaStream_t stream);
+                        DevStatus* st, int minb, bool tile, bool spread, cudaStream_t stream);
 
 template <typename T>
 void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,

@@ -47,7 +47,7 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
-  grpic_tuning tune{5, 4, 1, 1, 0, 0};
+  grpic_tuning tune{4, 4, 1, 1, 0, 0, 1};
   void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
   double* J = nullptr;     // 3 planes
   void* mc = nullptr;      // 24 planes of T
@@ -164,7 +164,7 @@ void enqueue_select_push(grpic_ctx* c) {
     if (!S.loaded || S.n == 0) continue;
     refresh_count(S);
     launch_push_select(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
-                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->stream);
+                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->tune.spread != 0, c->stream);
     c->launches += 1;
   }
 }
@@ -805,7 +805,8 @@ grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
   if (!c || !t) return GRPIC_ERR_INVALID;
   if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
       t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1) ||
-      (t->split != 0 && t->split != 1) || (t->j_tile != 0 && t->j_tile != 1))
+      (t->split != 0 && t->split != 1) || (t->j_tile != 0 && t->j_tile != 1) ||
+      (t->spread != 0 && t->spread != 1))
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   c->cfg.sort_interval = t->sort_interval;

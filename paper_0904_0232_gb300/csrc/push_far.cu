@@ -67,11 +67,16 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
 // the tile, deposits straight to global J.
 constexpr int kJTileFloats = 3072;
 
+// perm: the block -> particle-chunk map is chunk = blockIdx.x * perm mod gridDim.x (perm coprime
+// to gridDim.x; 1 = in order).  Cell-sorted particles put the FP64-heavy chunks near the hole in
+// one contiguous run; a permutation spreads them over the whole launch, so the FP64 pipes of all
+// SMs share that work alongside FP32 work instead of a few SMs at a time doing mostly FP64.
 template <int Q, int MINB, bool TILE>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
-                                                           float r_near2, DevStatus* st) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+                                                           float r_near2, unsigned perm, DevStatus* st) {
+  const unsigned chunk = (unsigned)(((unsigned long long)blockIdx.x * perm) % gridDim.x);
+  const long long i = chunk * (long long)blockDim.x + threadIdx.x;
   unsigned flags = 0, n64 = 0;
   bool active = i < P.n && i < (long long)(*P.n_dev);
   if (active) active = P.key[i] != kDead;
@@ -183,25 +188,42 @@ void launch_push_far(const Grid& g, const Fields<float>& F, const Particles<floa
     k_push_far<2, 5><<<nb, 128, 0, stream>>>(g, F, P, C, st);
 }
 
+unsigned coprime_multiplier(unsigned n) {
+  // a multiplier near 0.618 n (well spread) that is coprime to n
+  if (n <= 2) return 1;
+  unsigned m = (unsigned)(0.6180339887 * n) | 1u;
+  auto gcd = [](unsigned a, unsigned b) {
+    while (b) {
+      const unsigned t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  while (gcd(m, n) != 1) m += 2;
+  return m % n;
+}
+
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, cudaStream_t stream) {
+                        DevStatus* st, int minb, bool tile, bool spread, cudaStream_t stream) {
   if (P.n <= 0) return;
   const unsigned nb = blocks_for(P.n, 128);
   const Consts<float> C = make_consts<float>(g, sp);
   const double rn = near_radius(g);
   const float r_near2 = (float)(rn * rn);
+  const unsigned perm = spread ? coprime_multiplier(nb) : 1u;
   if (g.quad_order == 1)
-    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else if (g.quad_order == 3)
-    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else if (tile && minb >= 5)
-    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else if (tile)
-    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else if (minb >= 5)
-    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else
-    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, st);
+    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
 }
 
 }  // namespace grpic

@@ -6,15 +6,15 @@ from paper_0904_0232_gb300 import autotune
 class FakeSim:
     def __init__(self, cost):
         self.cost = cost
-        self.t = dict(far_min_blocks=5, near_blocks_per_sm=2, sort_interval=1, overlap=1, split=0, j_tile=0)
+        self.t = dict(far_min_blocks=5, near_blocks_per_sm=2, sort_interval=1, overlap=1, split=0, j_tile=0, spread=0)
         self.calls = 0
 
     def tuning(self):
         return dict(self.t)
 
-    def set_tuning(self, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
+    def set_tuning(self, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile, spread):
         self.t = dict(far_min_blocks=far_min_blocks, near_blocks_per_sm=near_blocks_per_sm,
-                      sort_interval=sort_interval, overlap=overlap, split=split, j_tile=j_tile)
+                      sort_interval=sort_interval, overlap=overlap, split=split, j_tile=j_tile, spread=spread)
 
 
 def timer(sim, steps):
@@ -22,7 +22,7 @@ def timer(sim, steps):
     return sim.cost(**sim.t)
 
 
-def separable(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
+def separable(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile, spread=0):
     return ({4: 3.0, 5: 1.0, 6: 2.0}[far_min_blocks] + {1: 0.5, 2: 0.7, 4: 0.2}[near_blocks_per_sm]
             + {1: 0.9, 2: 0.3, 4: 0.4}[sort_interval] + {0: 0.05, 1: 0.0}[overlap] + {0: 0.1, 1: 0.0}[split]
             + {0: 0.0, 1: 0.02}[j_tile])
@@ -31,14 +31,15 @@ def separable(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split,
 def test_coordinate_descent_finds_separable_minimum(tmp_path):
     sim = FakeSim(separable)
     r = autotune.tune(sim, "w", cache=str(tmp_path / "t.json"), timer=timer, device="fake")
-    assert r["tuning"] == dict(far_min_blocks=5, near_blocks_per_sm=4, sort_interval=2, overlap=1, split=1, j_tile=0)
+    assert r["tuning"] == dict(far_min_blocks=5, near_blocks_per_sm=4, sort_interval=2, overlap=1, split=1, j_tile=0,
+                               spread=0)
     assert sim.t == r["tuning"] and not r["cached"]
     assert abs(r["ms_per_step"] - separable(**r["tuning"])) < 1e-12
 
 
 def test_coupled_cost_second_round(tmp_path):
     # the best near setting depends on the far setting: one round is not enough
-    def coupled(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile):
+    def coupled(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile, spread=0):
         table = {(4, 1): 1.0, (4, 2): 5.0, (4, 4): 5.0, (5, 1): 5.0, (5, 2): 3.0, (5, 4): 5.0,
                  (6, 1): 5.0, (6, 2): 5.0, (6, 4): 0.5}
         return table[(far_min_blocks, near_blocks_per_sm)] + 0.1 * sort_interval + 0.01 * overlap
