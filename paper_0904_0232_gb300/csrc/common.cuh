@@ -93,6 +93,54 @@ struct Species {
   double qm, qmacro;
 };
 
+// Constants of one push launch in the arithmetic type T, built once on the host (for the batch:
+// once per instance and species, in its descriptor), plus their FP64 values for the promoted
+// evaluations of the FP32-mixed policy.
+template <typename T>
+struct Consts {
+  T xc, yc, zc, m, a;        // centre of mass, mass, spin
+  T a2, two_m;               // a^2, 2m
+  T c, dt, inv_dt, inv_c, cdt;
+  T qm, qmacro;              // q/m (Lorentz term of Eq. 15), macro-particle charge (deposit)
+  T rcheck2;                 // removal screen: r^2 below this -> FP64 test against r_+
+  float r_fp64, r2_fp64;     // FP32-mixed: promote where the FP32 r is below r_fp64
+  bool massive;              // m > 0
+  bool gamma_in_j;           // J = rho gamma v (else the plain Umeda flux)
+  double dxc, dyc, dzc, dm, da, da2, r_plus;
+};
+
+template <typename T>
+__host__ __device__ inline Consts<T> make_consts(const Grid& g, const Species& sp) {
+  Consts<T> C;
+  C.xc = (T)g.xc;
+  C.yc = (T)g.yc;
+  C.zc = (T)g.zc;
+  C.m = (T)g.m;
+  C.a = (T)g.a;
+  C.a2 = C.a * C.a;
+  C.two_m = T(2) * C.m;
+  C.c = (T)g.c;
+  C.dt = (T)g.dt;
+  C.inv_dt = T(1) / (T)g.dt;
+  C.inv_c = T(1) / (T)g.c;
+  C.cdt = (T)(g.c * g.dt);
+  C.qm = (T)sp.qm;
+  C.qmacro = (T)sp.qmacro;
+  C.rcheck2 = (T)(1.2 * g.r_plus * g.r_plus + 1.0);
+  C.r_fp64 = (float)g.r_fp64;
+  C.r2_fp64 = C.r_fp64 > 0.f ? C.r_fp64 * C.r_fp64 : -1.f;  // negative: never promote
+  C.massive = g.m > 0.0;
+  C.gamma_in_j = (g.flags & 1u) == 0;
+  C.dxc = g.xc;
+  C.dyc = g.yc;
+  C.dzc = g.zc;
+  C.dm = g.m;
+  C.da = g.a;
+  C.da2 = g.a * g.a;
+  C.r_plus = g.r_plus;
+  return C;
+}
+
 template <typename T>
 void launch_push_deposit(const Grid& g, const Fields<T>& F, const Particles<T>& P, const Species& sp,
                          DevStatus* st, bool mixed, double t_offset, cudaStream_t stream);
@@ -119,6 +167,8 @@ void launch_push_near(const Grid& g, const Fields<float>& F, const Particles<flo
                       cudaStream_t stream);
 void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uint32_t* keys, const int* count,
                       int nblocks, cudaStream_t stream);
+// A multiplier coprime to n near 0.618 n: blockIdx * m mod n permutes n work items evenly.
+unsigned coprime_multiplier(unsigned n);
 // Unsplit alternative: one launch, far-field or FP32-mixed code chosen per warp by the same
 // near_radius criterion.
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
@@ -154,6 +204,8 @@ struct BlockEntry {
 
 template <typename T>
 struct SpeciesDesc {
+  Consts<T> C;          // launch constants of this (instance, species)
+  float r_near2;        // near_radius^2 of the instance (FP32-mixed far-field criterion)
   double qm, qmacro;
   Particles<T> buf[2];  // the two ping-pong buffers (n = work upper bound, n_dev = live count)
   int* cur;             // device int: index of the current buffer

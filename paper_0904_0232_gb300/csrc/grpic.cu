@@ -953,6 +953,9 @@ grpic_status batch_build(grpic_batch* b) {
       SD.active = S.loaded ? 1 : 0;
       SD.qm = S.qm;
       SD.qmacro = S.qmacro;
+      SD.C = make_consts<T>(g, Species{S.qm, S.qmacro});
+      const double rn = near_radius(g);
+      SD.r_near2 = (float)(rn * rn);
       SD.cur = b->cur + 4 * i + s;
       SD.bin_base = 0;
       if (!S.loaded) continue;

@@ -21,6 +21,13 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit(const Grid g, const Fie
   warp_status(st, flags, n64, active);
 }
 
+// Block-cooperative copy of a trivially copyable struct (a multiple of 4 bytes) into shared memory.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, size_t bytes) {
+  unsigned* d = static_cast<unsigned*>(dst);
+  const unsigned* s = static_cast<const unsigned*>(src);
+  for (unsigned w = threadIdx.x; w < bytes / 4; w += blockDim.x) d[w] = s[w];
+}
+
 // Near-hole pass of the split FP32-mixed push: the particles listed by the classification
 // (whose stages and quadrature nodes may fall inside r < r_fp64).  Persistent blocks take
 // 128-entry chunks of the list from a cursor (count[1]) until it is exhausted: the FP64 work
@@ -56,59 +63,56 @@ __global__ void k_near_keys(uint32_t* __restrict__ key, const uint32_t* __restri
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) key[list[j]] = keys[j];
 }
 
-// Batched: (instance * 4 + species, block) work items, one per CTA as launched (the loop also
-// serves a smaller grid); each block belongs to one instance and species, so the warp-level
-// status stays per instance.  The instance descriptor is staged in shared memory, reloaded only
-// when the instance changes.  FP32-mixed: each warp takes
-// the far-field code unless one of its particles lies within the instance's near_radius.
+// Batched: one CTA per (instance * 4 + species, block) work item; each block belongs to one
+// instance and species, so the warp-level status stays per instance.  The block stages its
+// instance descriptor (with the host-built launch constants) in shared memory.  The block -> item map is the same
+// coprime permutation as k_push_select's (perm; 1 = in order), spreading FP64-heavy items.
+// FP32-mixed: each warp takes the far-field code unless one of its particles lies within the
+// instance's near_radius.
 template <typename T, int Q, bool MIXED>
 __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>* __restrict__ desc,
-                                                                 const BlockEntry* __restrict__ blk, int nblk) {
+                                                                 const BlockEntry* __restrict__ blk, int nblk,
+                                                                 unsigned perm) {
   __shared__ Grid sg;
   __shared__ Fields<T> sF;
-  __shared__ Particles<T> sP;
-  __shared__ Consts<T> sC;
+  __shared__ SpeciesDesc<T> sS;
   __shared__ DevStatus* sst;
-  __shared__ float s_rnear2;
-  int loaded = -1;
-  for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
-    const BlockEntry e = blk[bi];
-    if (e.inst != loaded) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const InstDesc<T>& D = desc[e.inst >> 2];
-        const SpeciesDesc<T>& S = D.sp[e.inst & 3];
-        sg = D.g;
-        sF = D.F;
-        sP = S.buf[*S.cur];
-        sC = make_consts<T>(D.g, Species{S.qm, S.qmacro});
-        sst = D.st;
-        const double rn = near_radius(D.g);
-        s_rnear2 = (float)(rn * rn);
-      }
-      __syncthreads();
-      loaded = e.inst;
-    }
-    const long long i = (long long)e.block * blockDim.x + threadIdx.x;
-    unsigned flags = 0, n64 = 0;
-    bool active = i < sP.n && i < (long long)(*sP.n_dev);
-    if (active) active = sP.key[i] != kDead;
-    bool mixed = false;
-    if constexpr (MIXED) {
-      bool near = false;
-      if (active) {
-        const float X = sP.x[0][i] - sC.xc, Y = sP.x[1][i] - sC.yc, Z = sP.x[2][i] - sC.zc;
-        near = X * X + Y * Y + Z * Z < s_rnear2;
-      }
-      mixed = __any_sync(0xffffffffu, near);
-    }
-    if (mixed) {  // two inlined copies with a constant flag (see k_push_select)
-      if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, true);
-    } else {
-      if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, false);
-    }
-    warp_status(sst, flags, n64, active);
+  __shared__ int s_cur;
+  const int bi = (int)(((unsigned long long)blockIdx.x * perm) % (unsigned)nblk);
+  const BlockEntry e = blk[bi];
+  // stage the descriptor parts this block needs with one coalesced copy by all threads (the
+  // launch constants were built on the host)
+  const InstDesc<T>& D = desc[e.inst >> 2];
+  copy_words(&sg, &D.g, sizeof(Grid));
+  copy_words(&sF, &D.F, sizeof(Fields<T>));
+  copy_words(&sS, &D.sp[e.inst & 3], sizeof(SpeciesDesc<T>));
+  if (threadIdx.x == 0) {
+    sst = D.st;
+    s_cur = *D.sp[e.inst & 3].cur;
   }
+  __syncthreads();
+  const Particles<T>& sP = sS.buf[s_cur];
+  const Consts<T>& sC = sS.C;
+  const float s_rnear2 = sS.r_near2;
+  const long long i = (long long)e.block * blockDim.x + threadIdx.x;
+  unsigned flags = 0, n64 = 0;
+  bool active = i < sP.n && i < (long long)(*sP.n_dev);
+  if (active) active = sP.key[i] != kDead;
+  bool mixed = false;
+  if constexpr (MIXED) {
+    bool near = false;
+    if (active) {
+      const float X = sP.x[0][i] - sC.xc, Y = sP.x[1][i] - sC.yc, Z = sP.x[2][i] - sC.zc;
+      near = X * X + Y * Y + Z * Z < s_rnear2;
+    }
+    mixed = __any_sync(0xffffffffu, near);
+  }
+  if (mixed) {  // two inlined copies with a constant flag (see k_push_select)
+    if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, true);
+  } else {
+    if (active) push_particle<T, Q>(sg, sF, sP, sC, i, sst, flags, n64, sP.key + i, false);
+  }
+  warp_status(sst, flags, n64, active);
 }
 
 // ---- load / unload ---------------------------------------------------------------------
@@ -250,16 +254,16 @@ void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uin
 template <typename T, bool MIXED>
 void launch_batch_push_q(const BatchTables<T>& bt, int quad_order, cudaStream_t stream) {
   // one block per work item: each block stages its instance descriptor once, and the hardware
-  // scheduler balances instances of very different cost (a persistent grid-stride loop would
-  // cross instance boundaries, and reload the descriptor, at nearly every item)
+  // scheduler balances instances of very different cost
   const unsigned nb = (unsigned)bt.npart;
   if (bt.npart == 0) return;
+  const unsigned perm = coprime_multiplier(nb);
   if (quad_order == 1)
-    k_push_deposit_batch<T, 1, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+    k_push_deposit_batch<T, 1, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, perm);
   else if (quad_order == 3)
-    k_push_deposit_batch<T, 3, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+    k_push_deposit_batch<T, 3, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, perm);
   else
-    k_push_deposit_batch<T, 2, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart);
+    k_push_deposit_batch<T, 2, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, perm);
 }
 
 template <>

@@ -62,52 +62,6 @@ struct JTile {
   int nx = 0, ny = 0, nz = 0;
 };
 
-// Constants of one push launch in the arithmetic type T, built once on the host (once per
-// block in the batched kernel), plus their FP64 values for the promoted evaluations.
-template <typename T>
-struct Consts {
-  T xc, yc, zc, m, a;        // centre of mass, mass, spin
-  T a2, two_m;               // a^2, 2m
-  T c, dt, inv_dt, inv_c, cdt;
-  T qm, qmacro;              // q/m (Lorentz term of Eq. 15), macro-particle charge (deposit)
-  T rcheck2;                 // removal screen: r^2 below this -> FP64 test against r_+
-  float r_fp64, r2_fp64;     // FP32-mixed: promote where the FP32 r is below r_fp64
-  bool massive;              // m > 0
-  bool gamma_in_j;           // J = rho gamma v (else the plain Umeda flux)
-  double dxc, dyc, dzc, dm, da, da2, r_plus;
-};
-
-template <typename T>
-__host__ __device__ inline Consts<T> make_consts(const Grid& g, const Species& sp) {
-  Consts<T> C;
-  C.xc = (T)g.xc;
-  C.yc = (T)g.yc;
-  C.zc = (T)g.zc;
-  C.m = (T)g.m;
-  C.a = (T)g.a;
-  C.a2 = C.a * C.a;
-  C.two_m = T(2) * C.m;
-  C.c = (T)g.c;
-  C.dt = (T)g.dt;
-  C.inv_dt = T(1) / (T)g.dt;
-  C.inv_c = T(1) / (T)g.c;
-  C.cdt = (T)(g.c * g.dt);
-  C.qm = (T)sp.qm;
-  C.qmacro = (T)sp.qmacro;
-  C.rcheck2 = (T)(1.2 * g.r_plus * g.r_plus + 1.0);
-  C.r_fp64 = (float)g.r_fp64;
-  C.r2_fp64 = C.r_fp64 > 0.f ? C.r_fp64 * C.r_fp64 : -1.f;  // negative: never promote
-  C.massive = g.m > 0.0;
-  C.gamma_in_j = (g.flags & 1u) == 0;
-  C.dxc = g.xc;
-  C.dyc = g.yc;
-  C.dzc = g.zc;
-  C.dm = g.m;
-  C.da = g.a;
-  C.da2 = g.a * g.a;
-  C.r_plus = g.r_plus;
-  return C;
-}
 
 __device__ __forceinline__ double to_f64(float v) { return widen(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
