@@ -71,9 +71,10 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=10)
     p.add_argument("--fp32-compare-steps", type=int, default=200,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
-    p.add_argument("--workload", choices=["kerr128", "batch"], default="kerr128",
+    p.add_argument("--workload", choices=["kerr128", "batch", "disk384"], default="kerr128",
                    help="kerr128: the single-instance Kerr electron-ion workload; batch: many small "
-                        "instances advanced by the batched engine")
+                        "instances advanced by the batched engine; disk384: the 384^3 disk/corona plasma "
+                        "(~1e9 particles, generated on the device)")
     p.add_argument("--single-kernel-steps", type=int, default=200,
                    help="steps of the comparison run with the single mixed push kernel; 0 skips it")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
@@ -525,6 +526,51 @@ def run_batch(args, dist):
     return line
 
 
+def run_disk(args, dist):
+    """The largest configuration: Kerr a = 0.95 m, m = 8, 384^3, accretion disk in a corona,
+    ~1e9 particles generated on the device, FP32-mixed; particle-steps/s over K steps."""
+    import torch
+
+    from paper_0904_0232_gb300 import synth_disk
+    from paper_0904_0232_gb300.build import build
+    from paper_0904_0232_gb300.grpic import Simulation
+
+    torch.cuda.set_device(dist.local)
+    build()
+    wl = synth_disk.kerr_disk_corona(n=args.grid if args.grid != 128 else 384, seed=3)
+    npart = wl.n_particles
+    sim = Simulation(wl.n, wl.n, wl.n, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", quad_order=args.quad)
+    sim.set_tuning(sort_interval=args.sort_interval)
+    sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
+    for s, sp in enumerate(wl.species):
+        sim.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.u4, sp.ids, umode=sp.umode)
+    geo = dict(n=wl.n, m=wl.m, a=wl.a, n0=round(wl.n0, 1))
+    del wl, sp
+    torch.cuda.empty_cache()
+    sim.set_profiling(True)
+    sim.step(args.warmup)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    ms, psteps, prof, launches = timed_steps(sim, args.steps, dist)
+    clk = clocks.stop()
+    st = sim.stats()
+    sim.close()
+    value = dist.sum(psteps) / (dist.max(ms) * 1e-3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dist.max(ms) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 quartic/metric/Christoffel where r < 4m; FP64 J)",
+            "data": "synthetic (device-generated disk + corona)",
+            "config": {"workload": f"kerr_disk_corona_{geo['n']}: Kerr a=0.95m, m={geo['m']:g} cells, {geo['n']}^3, "
+                                   "Keplerian disk (|z|<0.1 r_cyl, 6m..150 cells, density ~1/r) in a 1% corona, "
+                                   "e-/ion (mass ratio 20), B_z=0.1, dt=0.4",
+                       "particles": npart, "inner_edge_particles_per_cell": geo["n0"],
+                       "sort_interval": args.sort_interval},
+            "gpu_launches": int(launches),
+            "stage_ms_per_step": {k: round(v[0] / max(1, args.steps), 4) for k, v in prof.items()},
+            "clocks": clk,
+            "stats": {k: st[k] for k in ("removed_horizon", "removed_outer", "gamma_fallbacks", "fp64_evals")}}
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -532,6 +578,8 @@ def main():
         line = run_reference(args, dist)
     elif args.workload == "batch":
         line = run_batch(args, dist)
+    elif args.workload == "disk384":
+        line = run_disk(args, dist)
     else:
         line = run_gpu(args, dist)
     if dist.rank == 0 and line is not None:

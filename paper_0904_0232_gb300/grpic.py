@@ -251,12 +251,24 @@ def grpic_num_particles(ctx, species):
     return n.value
 
 
-def grpic_get_particles(ctx, species):
+def grpic_get_particles(ctx, species, device=False):
+    """(x4, u4, ids) of a species: numpy arrays, or CUDA tensors (float64, float64, int32) with
+    device=True (no host copy)."""
     n = grpic_num_particles(ctx, species)
+    nn = ctypes.c_int64(n)
+    if device:
+        torch = _torch()
+        x4 = torch.empty((4, n), dtype=torch.float64, device="cuda")
+        u4 = torch.empty((4, n), dtype=torch.float64, device="cuda")
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        _check(ctx, load_library().grpic_get_particles(ctx, int(species), ctypes.byref(nn),
+                                                       ctypes.c_void_p(x4.data_ptr()), ctypes.c_void_p(u4.data_ptr()),
+                                                       ctypes.c_void_p(ids.data_ptr()), GRPIC_MEM_DEVICE),
+               "grpic_get_particles")
+        return x4[:, :nn.value], u4[:, :nn.value], ids[:nn.value]
     x4 = np.zeros((4, n))
     u4 = np.zeros((4, n))
     ids = np.zeros(n, dtype=np.uint32)
-    nn = ctypes.c_int64(n)
     _check(ctx, load_library().grpic_get_particles(ctx, int(species), ctypes.byref(nn),
                                                    x4.ctypes.data_as(ctypes.c_void_p),
                                                    u4.ctypes.data_as(ctypes.c_void_p),
@@ -511,8 +523,8 @@ class Simulation:
     def get_fields(self):
         return grpic_get_fields(self.handle, self.shape)
 
-    def get_particles(self, species):
-        return grpic_get_particles(self.handle, species)
+    def get_particles(self, species, device=False):
+        return grpic_get_particles(self.handle, species, device=device)
 
     def num_particles(self, species):
         return grpic_num_particles(self.handle, species)
