@@ -200,6 +200,20 @@ grpic_status grpic_set_profiling(grpic_ctx* ctx, int on);
 grpic_status grpic_get_profile(grpic_ctx* ctx, double times_ms[6], int64_t counts[6], int64_t* kernel_launches,
                                int reset);
 
+/* Charge density at the nodes (Sec. 3.3 CIC weights, which det g = -1 makes trilinear) of the
+ * particles as they stand: rho = sum q_macro W(x), or with with_gamma = 1 the time component of
+ * J = rho gamma v (Sec. 4) over c, sum q_macro (u^4/c) W(x).  rho: ncell doubles in the field
+ * layout (z-major, x fastest), host or device memory (mem).  Synchronises. */
+grpic_status grpic_charge_density(grpic_ctx* ctx, int with_gamma, double* rho, int mem);
+
+/* Gauss-law residual at the nodes, div E - 4 pi rho, with E^a = -d^a (= -F^{a4}) and backward
+ * differences of the edge-centred d, rho from grpic_charge_density (no gamma).  With the
+ * gamma-free deposit (GRPIC_NO_GAMMA_IN_J) in flat space it changes over a step by exactly
+ * -4 pi times the deposit's 3-D continuity defect (zero for moves within a plane), a live check
+ * of the current.  res (may be NULL): ncell doubles, host or device (mem); max_abs (may be
+ * NULL): max |residual| over the nodes [2, n-3]^3.  Synchronises. */
+grpic_status grpic_gauss_residual(grpic_ctx* ctx, double* res, int mem, double* max_abs);
+
 /* Launch-shape choices of a context (not in the paper; what the autotuner chooses).
  * FP32_MIXED contexts tell "near" particles, R(x_n) < r_fp64 + |a| + 4 cells (some RK4 stage
  * or quadrature node of theirs may fall inside r < r_fp64, where the FP64 policy applies), from

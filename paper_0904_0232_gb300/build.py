@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrpic.so")
-SOURCES = ["grpic.cu", "fields.cu", "push.cu", "push_far.cu", "sort.cu", "peak.cu", "static_sort.cu", "server.cu"]
+SOURCES = ["grpic.cu", "fields.cu", "push.cu", "push_far.cu", "sort.cu", "peak.cu", "static_sort.cu", "server.cu",
+           "diag.cu"]
 HEADERS = ["common.cuh", "metric.cuh", "push_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 path of the push tolerates the hardware's approximate single-precision divide and

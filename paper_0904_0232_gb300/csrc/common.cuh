@@ -181,6 +181,15 @@ template <typename T>
 void launch_unload_particles(const Particles<T>& P, long long n, double* x4, double* u4, uint32_t* ids,
                              double ct_now, cudaStream_t stream);
 
+// Diagnostics (diag.cu): CIC charge density (times gamma with with_gamma) added into rho, and
+// the Gauss residual div E - 4 pi rho with the max |residual| over nodes [lo, n-1-lo]^3.
+template <typename T>
+void launch_charge_density(const Particles<T>& P, double q, const Grid& g, bool with_gamma, double* rho,
+                           cudaStream_t stream);
+template <typename T>
+void launch_gauss(const Fields<T>& F, const double* rho, const Grid& g, int lo, double* res,
+                  unsigned long long* maxabs, cudaStream_t stream);
+
 // Counting sort by cell of one species; removed particles (key == kDead) are dropped.
 // counts: nbins+1 ints, offsets: nbins+1 ints, blocks: scan scratch; n_out: device int.
 struct SortScratch {

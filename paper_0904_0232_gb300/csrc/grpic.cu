@@ -156,6 +156,17 @@ bool split_push(const grpic_ctx* c) {
   return c->mixed && c->g.r_fp64 > 0.0 && !(c->cfg.flags & GRPIC_SINGLE_PUSH_KERNEL);
 }
 
+// rho (FP64, nodes) of every loaded species into device memory `rho` (zeroed first).
+template <typename T>
+void enqueue_rho(grpic_ctx* c, bool with_gamma, double* rho) {
+  cudaMemsetAsync(rho, 0, sizeof(double) * (size_t)c->g.ncell, c->stream);
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    launch_charge_density<T>(particles_view<T>(c, s, S.cur), S.qmacro, c->g, with_gamma, rho, c->stream);
+  }
+}
+
 // Unsplit FP32-mixed push: one launch per species, far-field or mixed code chosen per warp.
 void enqueue_select_push(grpic_ctx* c) {
   Fields<float> F = fields_view<float>(c);
@@ -799,6 +810,58 @@ grpic_status grpic_get_stats(grpic_ctx* c, grpic_stats* out) {
     out->n_alive[q] = v;
   }
   return GRPIC_OK;
+}
+
+grpic_status grpic_charge_density(grpic_ctx* c, int with_gamma, double* rho, int mem) {
+  if (!c || !rho) return GRPIC_ERR_INVALID;
+  double* d = rho;
+  void* tmp = nullptr;
+  if (mem != GRPIC_MEM_DEVICE) {
+    d = static_cast<double*>(tmp = dev_alloc(c, sizeof(double) * (size_t)c->g.ncell));
+    if (!d) return fail(c, GRPIC_ERR_OOM, "charge density staging");
+  }
+  if (c->mixed)
+    enqueue_rho<float>(c, with_gamma != 0, d);
+  else
+    enqueue_rho<double>(c, with_gamma != 0, d);
+  if (mem != GRPIC_MEM_DEVICE)
+    cudaMemcpyAsync(rho, d, sizeof(double) * (size_t)c->g.ncell, cudaMemcpyDeviceToHost, c->stream);
+  grpic_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "charge density");
+  dev_free(c, tmp);
+  return st;
+}
+
+grpic_status grpic_gauss_residual(grpic_ctx* c, double* res, int mem, double* max_abs) {
+  if (!c || (!res && !max_abs)) return GRPIC_ERR_INVALID;
+  const size_t nc = (size_t)c->g.ncell;
+  double* rho = static_cast<double*>(dev_alloc(c, sizeof(double) * nc));
+  double* r = res;
+  void* rtmp = nullptr;
+  if (res && mem != GRPIC_MEM_DEVICE) r = static_cast<double*>(rtmp = dev_alloc(c, sizeof(double) * nc));
+  unsigned long long* mx = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+  if (!rho || !mx || (res && !r)) {
+    dev_free(c, rho);
+    dev_free(c, rtmp);
+    dev_free(c, mx);
+    return fail(c, GRPIC_ERR_OOM, "gauss residual staging");
+  }
+  cudaMemsetAsync(mx, 0, sizeof(unsigned long long), c->stream);
+  if (c->mixed) {
+    enqueue_rho<float>(c, false, rho);
+    launch_gauss<float>(fields_view<float>(c), rho, c->g, 2, r, mx, c->stream);
+  } else {
+    enqueue_rho<double>(c, false, rho);
+    launch_gauss<double>(fields_view<double>(c), rho, c->g, 2, r, mx, c->stream);
+  }
+  if (res && mem != GRPIC_MEM_DEVICE) cudaMemcpyAsync(res, r, sizeof(double) * nc, cudaMemcpyDeviceToHost, c->stream);
+  unsigned long long bits = 0;
+  cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+  grpic_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "gauss residual");
+  if (st == GRPIC_OK && max_abs) std::memcpy(max_abs, &bits, sizeof(double));
+  dev_free(c, rho);
+  dev_free(c, rtmp);
+  dev_free(c, mx);
+  return st;
 }
 
 grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {

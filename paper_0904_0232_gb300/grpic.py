@@ -89,6 +89,9 @@ EXPORTS = {
     "grpic_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int]),
+    "grpic_charge_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_gauss_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double)]),
     "grpic_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_tuning)]),
     "grpic_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(grpic_tuning)]),
     "grpic_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -310,6 +313,23 @@ def grpic_get_profile(ctx, reset=False):
     _check(ctx, load_library().grpic_get_profile(ctx, ms, cnt, ctypes.byref(nl), int(bool(reset))),
            "grpic_get_profile")
     return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(6)}, nl.value
+
+
+def grpic_charge_density(ctx, shape, with_gamma=False):
+    """(nz, ny, nx) float64 charge density at the nodes (J^4 / c with with_gamma)."""
+    rho = np.zeros(shape)
+    _check(ctx, load_library().grpic_charge_density(ctx, int(bool(with_gamma)), rho.ctypes.data_as(ctypes.c_void_p),
+                                                    GRPIC_MEM_HOST), "grpic_charge_density")
+    return rho
+
+
+def grpic_gauss_residual(ctx, shape=None):
+    """(residual field or None, max |residual| over [2, n-3]^3)."""
+    mx = ctypes.c_double(0.0)
+    res = np.zeros(shape) if shape is not None else None
+    _check(ctx, load_library().grpic_gauss_residual(ctx, None if res is None else res.ctypes.data_as(ctypes.c_void_p),
+                                                    GRPIC_MEM_HOST, ctypes.byref(mx)), "grpic_gauss_residual")
+    return res, mx.value
 
 
 def grpic_set_tuning(ctx, far_min_blocks, near_blocks_per_sm, sort_interval, overlap=1, split=0, j_tile=0,
@@ -545,3 +565,9 @@ class Simulation:
 
     def tuning(self):
         return grpic_get_tuning(self.handle)
+
+    def charge_density(self, with_gamma=False):
+        return grpic_charge_density(self.handle, self.shape, with_gamma)
+
+    def gauss_residual(self, field=True):
+        return grpic_gauss_residual(self.handle, self.shape if field else None)
