@@ -66,6 +66,15 @@ struct JTile {
 __device__ __forceinline__ double to_f64(float v) { return widen(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
+// Packed FP32 pairs: one instruction performs the operation on both lanes, each lane rounded as
+// the scalar operation would be.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+
 template <typename T>
 __device__ __forceinline__ T lerp(T a, T b, T w) {
   return fma(w, b - a, a);
@@ -97,6 +106,24 @@ __device__ __forceinline__ double quartic_newton(const Consts<float>& C, double 
   return kerr_r2<double, SeededOps64>(X, Y, Z, C.da, &D);
 }
 
+// The non-negative root of Eq. 6 as r^2 in FP64 from p = R^2 - a^2 and q = a^2 z^2 (the
+// cancellation-free branch form), for a quadrature node whose Newton start was poor.
+__device__ __noinline__ double quartic_closed64(double p, double q) {
+  const double D = SeededOps64::root(fma(p, p, 4.0 * q));
+  return p >= 0.0 ? 0.5 * (p + D) : SeededOps64::div(2.0 * q, D - p);
+}
+
+// FP64 r^2 of a quadrature node from its FP64 p and q, by the Newton step of quartic_newton from
+// the FP32 root s0 (FP32 D0), rounded to FP32.
+__device__ __forceinline__ float node_newton64(double p, double q, float s0, float D0) {
+  if (s0 > 0.f && D0 > 0.f) {
+    const double S = widen(s0);
+    const float corr = narrow(fma(S, S - p, -q)) / D0;
+    if (fabsf(corr) <= 1e-5f * s0) return narrow(S - widen(corr));
+  }
+  return narrow(quartic_closed64(p, q));
+}
+
 // FP64 metric and Christoffel contraction at a grid position (the FP32-mixed policy near the
 // hole), from the FP32 r and D of the same point: r^2 by quartic_newton, D = 2 r^2 - p (the
 // derivative of the quartic at its root), reciprocals and roots by SeededOps64; f, k and the
@@ -118,14 +145,6 @@ __device__ __noinline__ void metric_christoffel_fp64(const Consts<float>& C, flo
   out[5] = narrow(gd[1]);
   out[6] = narrow(gd[2]);
   out[7] = narrow(gd[3]);
-}
-
-// FP64 root of the quartic (Eq. 6) at a quadrature node near the hole (absolute FP32 node
-// coordinates px, py, pz), as r^2 rounded to FP32.
-__device__ __noinline__ float quartic_fp64(const Consts<float>& C, float px, float py, float pz, float s0,
-                                           float D0) {
-  double p;
-  return narrow(quartic_newton(C, widen(px) - C.dxc, widen(py) - C.dyc, widen(pz) - C.dzc, s0, D0, &p));
 }
 
 // a~ at (x, u): gather, convert, Lorentz - Christoffel.
@@ -164,11 +183,23 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
     const T* arr = comp < 3 ? F.d[comp] : F.b[comp - 3];
     const T* q = arr + (((long long)k0 * g.ny + j0) * g.nx + i0);
     // trilinear as nested linear interpolations (the weight products expanded, 7 lerps)
-    const T c00 = lerp(__ldg(q), __ldg(q + 1), w0);
-    const T c10 = lerp(__ldg(q + sy), __ldg(q + sy + 1), w0);
-    const T c01 = lerp(__ldg(q + sz), __ldg(q + sz + 1), w0);
-    const T c11 = lerp(__ldg(q + sz + sy), __ldg(q + sz + sy + 1), w0);
-    val[comp] = lerp(lerp(c00, c10, w1), lerp(c01, c11, w1), w2);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // the lerps along x of the (z0, z1) pairs at y0 and at y1, then along y, as packed pairs;
+      // b - a = fma(a, -1, b) exactly, so each lane equals the scalar lerp
+      const float2 a0 = make_float2(__ldg(q), __ldg(q + sz)), a1 = make_float2(__ldg(q + 1), __ldg(q + sz + 1));
+      const float2 b0 = make_float2(__ldg(q + sy), __ldg(q + sz + sy));
+      const float2 b1 = make_float2(__ldg(q + sy + 1), __ldg(q + sz + sy + 1));
+      const float2 cy0 = fma2(f2(w0), fma2(a0, f2(-1.f), a1), a0);
+      const float2 cy1 = fma2(f2(w0), fma2(b0, f2(-1.f), b1), b0);
+      const float2 cz = fma2(f2(w1), fma2(cy0, f2(-1.f), cy1), cy0);
+      val[comp] = lerp(cz.x, cz.y, w2);
+    } else {
+      const T c00 = lerp(__ldg(q), __ldg(q + 1), w0);
+      const T c10 = lerp(__ldg(q + sy), __ldg(q + sy + 1), w0);
+      const T c01 = lerp(__ldg(q + sz), __ldg(q + sz + 1), w0);
+      const T c11 = lerp(__ldg(q + sz + sy), __ldg(q + sz + sy + 1), w0);
+      val[comp] = lerp(lerp(c00, c10, w1), lerp(c01, c11, w1), w2);
+    }
   }
   const T d[3] = {val[0], val[1], val[2]};
   const T b[3] = {val[3], val[4], val[5]};
@@ -297,22 +328,75 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
   }
 }
 
-// A quadrature node that the far-field formula of deposit_lattice does not cover (FP32-mixed
-// warps only): the p <= 0 branch of the quartic (the cancellation-free form), and the FP64
-// policy where the FP32 r is below r_fp64 (or always, with promote).  Returns r^2 and whether
-// it came from FP64.  Out of line: far-field warps never call it.
-__device__ __noinline__ float2 node_slow(const Consts<float>& C, float p, float q, float ax, float ay, float az,
-                                         bool promote) {
-  const float D = sqrtf(fmaf(p, p, 4.f * q));
-  float r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
-  if (promote || !(r2 >= C.r2_fp64)) return make_float2(quartic_fp64(C, ax, ay, az, r2, D), 1.f);
-  return make_float2(r2, 0.f);
+// The per-face quantities of deposit_lattice and the per-node terms they are built from (one
+// definition, so that the deferred near-hole nodes see exactly the values of the main loop).
+struct FaceLattice {
+  int K;
+  float PK, XK, PI, PJ, i0, j0, cI, cJ, wI0, wI1, pK, qK;
+};
+
+// Grid coordinate along I of lattice row ia = si * Q + pi, and the row terms of p, q and the
+// spin term of k_K's numerator.
+template <int Q>
+__device__ __forceinline__ float row_coord(const FaceLattice& L, int si, int pi) {
+  float gx = (float)Gauss<Q>::x(0);
+#pragma unroll
+  for (int t = 1; t < Q; ++t)
+    if (pi == t) gx = (float)Gauss<Q>::x(t);
+  const float lo_i = si ? L.PI : L.i0, w_i = si ? L.wI1 : L.wI0;
+  return lo_i + 0.5f * w_i + 0.5f * w_i * gx;
+}
+__device__ __forceinline__ void row_terms(const Consts<float>& C, const FaceLattice& L, float AIa, float& pRow,
+                                          float& qRow, float& tRow) {
+  const float XIa = AIa - L.cI;
+  const float XI2 = XIa * XIa;
+  pRow = L.pK + XI2;
+  qRow = L.qK + (L.K == 1 ? C.a2 * XI2 : 0.f);
+  tRow = L.K == 0 ? -C.a * XIa : 0.f;
+}
+// Column jb = sj * Q + pj: grid coordinate along J and the column terms.
+template <int Q>
+__device__ __forceinline__ float col_coord(const FaceLattice& L, int jb) {
+  const int sub = jb >= Q ? 1 : 0, pj = jb - sub * Q;
+  float gx = (float)Gauss<Q>::x(0);
+#pragma unroll
+  for (int t = 1; t < Q; ++t)
+    if (pj == t) gx = (float)Gauss<Q>::x(t);
+  const float lo_j = sub ? L.PJ : L.j0, hi_j = sub ? L.j0 + 1.f : L.PJ;
+  return 0.5f * (lo_j + hi_j) + 0.5f * (hi_j - lo_j) * gx;
+}
+__device__ __forceinline__ void col_terms(const Consts<float>& C, const FaceLattice& L, float AJ, float& pJ,
+                                          float& qJ, float& tJ) {
+  const float XJ = AJ - L.cJ;
+  pJ = XJ * XJ;
+  qJ = L.K == 0 ? C.a2 * pJ : 0.f;
+  tJ = L.K == 1 ? C.a * XJ : 0.f;
+}
+
+// Eq. 18 integrand at one node from its r^2 (scalar form, for the deferred nodes).
+__device__ __forceinline__ float node_value(const Consts<float>& C, const FaceLattice& L, float r2, float q,
+                                            float t) {
+  if (!(r2 > 0.f)) return 1.f;  // the flat limit r = 0
+  const float r = r2 * rsqrtf(r2);
+  const float sig = fmaf(r2, r2, q);
+  float fperp;
+  if (L.K == 2) {
+    fperp = __fdividef(C.two_m * r * (r2 - L.XK * L.XK), sig);
+  } else {
+    const float num = fmaf(r, L.XK, t);
+    const float rho2 = r2 + C.a2;
+    const float rho4 = rho2 * rho2;
+    fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
+  }
+  const float v = 1.f + fperp;
+  return v * rsqrtf(v);
 }
 
 // FP32 deposit (the zig-zag split, fluxes and Eq. 18 weights of deposit() below) evaluated on a
 // per-face node lattice: the Q x Q Gauss nodes of the four sub-rectangles of a face make a
 // 2Q x 2Q lattice in (x^I, x^J), so node coordinates, their squares and the spin terms are
-// formed once per face, roots are v * rsqrt(v) and each node needs one reciprocal.
+// formed once per face (column terms) or row (row terms), roots are v * rsqrt(v) and each node
+// needs one reciprocal.  Adjacent nodes of a row go through the formula as a packed pair.
 //   Integrand: 1 + f (1 - k_K^2) with f = 2 m r^3 / Sigma, Sigma = r^4 + a^2 z^2, and
 //   1 - k_z^2 = (r^2 - z^2) / r^2;  1 - k_x^2 = (rho^4 - (r x - a y)^2) / rho^4,
 //   1 - k_y^2 = (rho^4 - (r y + a x)^2) / rho^4,  rho^2 = r^2 + a^2.
@@ -321,12 +405,14 @@ __device__ __noinline__ float2 node_slow(const Consts<float>& C, float p, float 
 // Every node first takes the far-field form: for a particle outside the near radius every node
 // has R > |a|, so the quartic takes its p = R^2 - a^2 > 0 branch and every root argument is
 // positive.  With mixed (a warp-uniform flag) a node with p <= 0 or an FP32 r below r_fp64 is
-// handed to node_slow (the FP64 policy, quartic_fp64 at the node's FP32 coordinates), and r = 0
-// gives the flat limit; one code path serves far-field and mixed warps alike.
+// left out of the sums and marked; after the lattice each marked node is evaluated again -- the
+// cancellation-free form of the root, then the FP64 policy (node_newton64 on FP64 p and q) where
+// it applies; r = 0 gives the flat limit -- and added.  The main loop has no call in it.
 template <int Q>
 __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<float>& F, const Consts<float>& C,
                                                 const float x0[3], const float dx[3], float qg, float inv_dt,
                                                 unsigned& flags, unsigned& n64, bool mixed, const JTile& jt) {
+  static_assert(4 * Q * Q <= 64, "node mask");
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
   float s1[3], s2[3];
@@ -358,101 +444,158 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float dK = sel3(K, dseg[0], dseg[1], dseg[2]);
       if (dK == 0.f) continue;
       const float flux = qg * dK * inv_dt;
-      const float PK = sel3(K, P[0], P[1], P[2]);
-      const float XK = PK - sel3(K, cen[0], cen[1], cen[2]);
-      const float PI = sel3(K, P[1], P[2], P[0]), PJ = sel3(K, P[2], P[0], P[1]);
-      const float i0 = (float)sel3(K, cy, cz, cx), j0 = (float)sel3(K, cz, cx, cy);
-      const float cI = sel3(K, cen[1], cen[2], cen[0]), cJ = sel3(K, cen[2], cen[0], cen[1]);
-      // node lattice: sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J); AJ the nodes'
-      // grid coordinates along J, XJ relative to the centre.  The rows (along I) run in a rolled
-      // loop, the nodes of a row unrolled: a quarter of the code of a fully unrolled lattice, so
-      // the far-field and FP32-mixed copies of a kernel fit the instruction cache together.
-      const float wI0 = PI - i0, wI1 = i0 + 1.f - PI;
+      FaceLattice L;
+      L.K = K;
+      L.PK = sel3(K, P[0], P[1], P[2]);
+      L.XK = L.PK - sel3(K, cen[0], cen[1], cen[2]);
+      L.PI = sel3(K, P[1], P[2], P[0]);
+      L.PJ = sel3(K, P[2], P[0], P[1]);
+      L.i0 = (float)sel3(K, cy, cz, cx);
+      L.j0 = (float)sel3(K, cz, cx, cy);
+      L.cI = sel3(K, cen[1], cen[2], cen[0]);
+      L.cJ = sel3(K, cen[2], cen[0], cen[1]);
+      // sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J)
+      L.wI0 = L.PI - L.i0;
+      L.wI1 = L.i0 + 1.f - L.PI;
+      const float wJ[2] = {L.PJ - L.j0, L.j0 + 1.f - L.PJ};
       // Per node the quartic needs p = R^2 - a^2 and q = a^2 z^2, k_K's numerator the spin term
       // -a x^I (K = 0) or +a x^J (K = 1); z is x^K, x^I or x^J (K = 2, 1, 0).  Each of these is a
-      // sum of a face constant, a row term and a column term, formed once: a node adds them.
-      const float pK = XK * XK - C.a2;
-      const float qK = K == 2 ? C.a2 * XK * XK : 0.f;
-      float AJ[2 * Q], XJ[2 * Q], pJ[2 * Q], qJ[2 * Q], tJ[2 * Q], wJ[2];
+      // sum of a face constant, a row term and a column term.
+      L.pK = L.XK * L.XK - C.a2;
+      L.qK = K == 2 ? C.a2 * L.XK * L.XK : 0.f;
+      float2 pJ2[Q], qJ2[Q], tJ2[Q];
 #pragma unroll
-      for (int sub = 0; sub < 2; ++sub) {
-        const float lo_j = sub ? PJ : j0, hi_j = sub ? j0 + 1.f : PJ;
-        wJ[sub] = hi_j - lo_j;
-#pragma unroll
-        for (int p = 0; p < Q; ++p) {
-          const int jb = sub * Q + p;
-          AJ[jb] = 0.5f * (lo_j + hi_j) + 0.5f * wJ[sub] * (float)Gauss<Q>::x(p);
-          XJ[jb] = AJ[jb] - cJ;
-          pJ[jb] = XJ[jb] * XJ[jb];
-          qJ[jb] = K == 0 ? C.a2 * pJ[jb] : 0.f;
-          tJ[jb] = K == 1 ? C.a * XJ[jb] : 0.f;
-        }
+      for (int k = 0; k < Q; ++k) {
+        float pa, qa, ta, pb, qb, tb;
+        col_terms(C, L, col_coord<Q>(L, 2 * k), pa, qa, ta);
+        col_terms(C, L, col_coord<Q>(L, 2 * k + 1), pb, qb, tb);
+        pJ2[k] = make_float2(pa, pb);
+        qJ2[k] = make_float2(qa, qb);
+        tJ2[k] = make_float2(ta, tb);
       }
-      float S00 = 0.f, S01 = 0.f, S10 = 0.f, S11 = 0.f;  // S[sub I][sub J]
+      const float nzz = -(L.XK * L.XK);
+      // acc[si][k]: lane-wise sums over the rows of sub-interval si, node pair k of a row
+      float2 acc[2][Q];
+#pragma unroll
+      for (int si = 0; si < 2; ++si)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc[si][k] = f2(0.f);
+      unsigned long long slow = 0ull;  // marked nodes, bit (si * Q + pi) * 2Q + jb
 #pragma unroll 1
-      for (int ia = 0; ia < 2 * Q; ++ia) {
-        const int si = ia >= Q ? 1 : 0, pi = ia - si * Q;
-        float gx = (float)Gauss<Q>::x(0), gw = (float)Gauss<Q>::w(0);
+      for (int pi = 0; pi < Q; ++pi) {
+        float gw = (float)Gauss<Q>::w(0);
 #pragma unroll
         for (int t = 1; t < Q; ++t)
-          if (pi == t) {
-            gx = (float)Gauss<Q>::x(t);
-            gw = (float)Gauss<Q>::w(t);
-          }
-        const float lo_i = si ? PI : i0, w_i = si ? wI1 : wI0;
-        const float AIa = lo_i + 0.5f * w_i + 0.5f * w_i * gx;
-        const float XIa = AIa - cI;
-        const float XI2 = XIa * XIa;
-        const float pRow = pK + XI2;
-        const float qRow = qK + (K == 1 ? C.a2 * XI2 : 0.f);
-        const float tRow = K == 0 ? -C.a * XIa : 0.f;
-        float row0 = 0.f, row1 = 0.f;
+          if (pi == t) gw = (float)Gauss<Q>::w(t);
 #pragma unroll
-        for (int jb = 0; jb < 2 * Q; ++jb) {
-          const float p = pRow + pJ[jb];
-          const float q = qRow + qJ[jb];
-          const float D2 = fmaf(p, p, 4.f * q);
-          float r2 = 0.5f * (p + D2 * rsqrtf(D2));
-          float val;
-          if (mixed && (!(p > 0.f) || !(r2 >= C.r2_fp64))) {
-            const float ax = sel3(K, PK, AJ[jb], AIa), ay = sel3(K, AIa, PK, AJ[jb]);
-            const float az = sel3(K, AJ[jb], AIa, PK);
-            const float2 rs = node_slow(C, p, q, ax, ay, az, p > 0.f);
-            r2 = rs.x;
-            n64 += (unsigned)rs.y;
-          }
-          if (mixed && !(r2 > 0.f)) {
-            val = 1.f;  // the flat limit r = 0
-          } else {
-            const float r = r2 * rsqrtf(r2);
-            const float sig = fmaf(r2, r2, q);
-            float fperp;
+        for (int si = 0; si < 2; ++si) {
+          float pRow, qRow, tRow;
+          row_terms(C, L, row_coord<Q>(L, si, pi), pRow, qRow, tRow);
+          const float2 pR = f2(pRow), qR = f2(qRow), tR = f2(tRow);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            const float2 p = add2(pR, pJ2[k]);
+            const float2 q = add2(qR, qJ2[k]);
+            const float2 D2 = fma2(p, p, mul2(f2(4.f), q));
+            const float2 r2 = mul2(f2(0.5f), fma2(D2, rsqrt2(D2), p));
+            const float2 r = mul2(r2, rsqrt2(r2));
+            const float2 sig = fma2(r2, r2, q);
+            float2 numer, den;
             if (K == 2) {
-              fperp = __fdividef(C.two_m * r * (r2 - XK * XK), sig);
+              numer = mul2(mul2(f2(C.two_m), r), add2(r2, f2(nzz)));
+              den = sig;
             } else {
-              const float num = fmaf(r, XK, tRow + tJ[jb]);
-              const float rho2 = r2 + C.a2;
-              const float rho4 = rho2 * rho2;
-              fperp = __fdividef(C.two_m * r * r2 * fmaf(-num, num, rho4), rho4 * sig);
+              // rho^4 - num^2 over rho^4 Sigma, both negated: (num^2 - rho^4) / (-rho^4 Sigma)
+              const float2 num = fma2(r, f2(L.XK), add2(tR, tJ2[k]));
+              const float2 rho2 = add2(r2, f2(C.a2));
+              const float2 nrho4 = mul2(rho2, fma2(r2, f2(-1.f), f2(-C.a2)));
+              numer = mul2(mul2(mul2(f2(C.two_m), r), r2), fma2(num, num, nrho4));
+              den = mul2(nrho4, sig);
             }
-            const float v = 1.f + fperp;
-            val = v * rsqrtf(v);
+            const float2 v = fma2(numer, rcp2(den), f2(1.f));
+            float2 val = mul2(v, rsqrt2(v));
+            if (mixed) {
+              const int bit = (si * Q + pi) * 2 * Q + 2 * k;
+              if (!(p.x > 0.f) || !(r2.x >= C.r2_fp64)) {
+                val.x = 0.f;
+                slow |= 1ull << bit;
+              }
+              if (!(p.y > 0.f) || !(r2.y >= C.r2_fp64)) {
+                val.y = 0.f;
+                slow |= 1ull << (bit + 1);
+              }
+            }
+            if (Q == 2) {
+              acc[si][k] = add2(acc[si][k], val);  // unit Gauss weights
+            } else {
+              const float2 w = make_float2(gw * (float)Gauss<Q>::w((2 * k) % Q),
+                                           gw * (float)Gauss<Q>::w((2 * k + 1) % Q));
+              acc[si][k] = fma2(w, val, acc[si][k]);
+            }
           }
-          if (jb < Q)
-            row0 += (float)Gauss<Q>::w(jb % Q) * val;
-          else
-            row1 += (float)Gauss<Q>::w(jb % Q) * val;
-        }
-        if (si == 0) {
-          S00 += gw * row0;
-          S01 += gw * row1;
-        } else {
-          S10 += gw * row0;
-          S11 += gw * row1;
         }
       }
-      const float wI[2] = {wI0, wI1};
-      const float S[2][2] = {{S00, S01}, {S10, S11}};
+      // S[si][sj]: the weighted integrand sums of the four sub-rectangles
+      float S[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+      for (int si = 0; si < 2; ++si)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          S[si][(2 * k) >= Q ? 1 : 0] += acc[si][k].x;
+          S[si][(2 * k + 1) >= Q ? 1 : 0] += acc[si][k].y;
+        }
+      // The marked nodes of FP32-mixed warps.  p and q in FP64 are sums of FP64 face, row and
+      // column terms, like their FP32 counterparts: the face and row terms are formed once.
+      if (slow) {
+        const double cK = sel3(K, C.dxc, C.dyc, C.dzc), cI = sel3(K, C.dyc, C.dzc, C.dxc);
+        const double cJ = sel3(K, C.dzc, C.dxc, C.dyc);
+        const double XK64 = widen(L.PK) - cK;
+        const double pK64 = fma(XK64, XK64, -C.da2);
+        const double qK64 = K == 2 ? C.da2 * XK64 * XK64 : 0.0;
+        int row = -1;
+        double pRow64 = 0.0, qRow64 = 0.0;
+        do {
+          const int b = __ffsll((long long)slow) - 1;
+          slow &= slow - 1ull;
+          const int ia = b / (2 * Q), jb = b - ia * 2 * Q;
+          const int si = ia / Q, pi = ia - si * Q;
+          const float AIa = row_coord<Q>(L, si, pi), AJ = col_coord<Q>(L, jb);
+          float pRow, qRow, tRow, pJ, qJ, tJ;
+          row_terms(C, L, AIa, pRow, qRow, tRow);
+          col_terms(C, L, AJ, pJ, qJ, tJ);
+          const float p = pRow + pJ, q = qRow + qJ;
+          // FP32 root by the cancellation-free form; FP64 where the policy asks for it (a node
+          // with p > 0 was marked only for that)
+          const float D = sqrtf(fmaf(p, p, 4.f * q));
+          float r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
+          if (p > 0.f || !(r2 >= C.r2_fp64)) {
+            if (ia != row) {
+              row = ia;
+              const double XI64 = widen(AIa) - cI;
+              pRow64 = fma(XI64, XI64, pK64);
+              qRow64 = K == 1 ? C.da2 * XI64 * XI64 : qK64;
+            }
+            const double XJ64 = widen(AJ) - cJ;
+            const double p64 = fma(XJ64, XJ64, pRow64);
+            const double q64 = K == 0 ? C.da2 * XJ64 * XJ64 : qRow64;
+            r2 = node_newton64(p64, q64, r2, D);
+            ++n64;
+          }
+          float w = (float)Gauss<Q>::w(0), wj = (float)Gauss<Q>::w(0);
+#pragma unroll
+          for (int t = 1; t < Q; ++t) {
+            if (pi == t) w = (float)Gauss<Q>::w(t);
+            if (jb % Q == t) wj = (float)Gauss<Q>::w(t);
+          }
+          const float add = w * wj * node_value(C, L, r2, q, tRow + tJ);
+          const int sj = jb >= Q ? 1 : 0;
+          S[0][0] += (si == 0 && sj == 0) ? add : 0.f;
+          S[0][1] += (si == 0 && sj == 1) ? add : 0.f;
+          S[1][0] += (si == 1 && sj == 0) ? add : 0.f;
+          S[1][1] += (si == 1 && sj == 1) ? add : 0.f;
+        } while (slow);
+      }
+      const float wI[2] = {L.wI0, L.wI1};
       // sub-rectangle areas; a node's weight is the area of the sub-rectangle opposite it
       const float A00 = S[1][1] * 0.25f * wI[1] * wJ[1];
       const float A10 = S[0][1] * 0.25f * wI[0] * wJ[1];
@@ -482,8 +625,23 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
   }
 }
 
-// One particle-step of particle i: RK4 push, deposit, removal flag and sort key (written to
-// *key_out: P.key + i, or a side array where another kernel still reads P.key concurrently).
+// A load that the compiler may neither hoist nor merge with an earlier one: push_particle reads
+// x_n and u_n again at every RK4 stage (they stay in L1) instead of holding them in registers
+// across the stage evaluations, which leaves registers for more resident warps.
+__device__ __forceinline__ float reload(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double reload(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+// One particle-step of particle i: RK4 push, new state stored, removal flag and sort key
+// (written to *key_out: P.key + i, or a side array where another kernel still reads P.key
+// concurrently), then the deposit of the move (which needs only x_n and the increment).
 // mixed (T = float): the FP32-mixed policy applies to this warp's particles (a warp-uniform
 // flag; false only where every particle lies outside near_radius).  T = double ignores it.
 template <typename T, int Q>
@@ -491,18 +649,13 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
                                               const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
                                               unsigned& n64, uint32_t* key_out, bool mixed,
                                               const JTile& jt = JTile()) {
-  T x0[4], u0[4];
+  // RK4 in proper time: stages at offsets 0, h/2, h/2, h; h = dt / gamma_1 (Eq. 16).  x^4 does
+  // not enter a~ (the metric is stationary), so the stages carry x^1..x^3 only.
+  T xs[3], us[4], a[4], sx[4], su[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    x0[q] = P.x[q][i];
-    u0[q] = P.u[q][i];
-  }
-  // RK4 in proper time: stages at offsets 0, h/2, h/2, h; h = dt / gamma_1 (Eq. 16)
-  T xs[4], us[4], a[4], sx[4], su[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    xs[q] = x0[q];
-    us[q] = u0[q];
+    if (q < 3) xs[q] = P.x[q][i];
+    us[q] = P.u[q][i];
     sx[q] = T(0);
     su[q] = T(0);
   }
@@ -511,26 +664,31 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
 #pragma unroll 1
   for (int stage = 0; stage < 4; ++stage) {
     accel<T>(g, F, C, xs, us, a, flags, n64, mixed);
-    if (stage == 0) h = C.dt / gamma_step<T>(u0[3], a[3], C.inv_c, C.dt, &fb);
+    if (stage == 0) h = C.dt / gamma_step<T>(us[3], a[3], C.inv_c, C.dt, &fb);
     const T wgt = (stage == 0 || stage == 3) ? T(1) : T(2);
     const T frac = (stage == 2) ? h : T(0.5) * h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       sx[q] += wgt * us[q];
       su[q] += wgt * a[q];
-      xs[q] = x0[q] + frac * us[q];
-      us[q] = u0[q] + frac * a[q];
+      if (q < 3) xs[q] = reload(P.x[q] + i) + frac * us[q];
+      us[q] = reload(P.u[q] + i) + frac * a[q];
     }
   }
-  T x1[4], u1[4], dx[4];
+  T x0[3], x1[4], u1[4], dx[3];
   const T h6 = h / T(6);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    dx[q] = h6 * sx[q];
-    x1[q] = x0[q] + dx[q];
-    u1[q] = u0[q] + h6 * su[q];
+    const T xq = reload(P.x[q] + i), d = h6 * sx[q];
+    if (q < 3) {
+      x0[q] = xq;
+      dx[q] = d;
+    }
+    x1[q] = xq + d;
+    u1[q] = reload(P.u[q] + i) + h6 * su[q];
   }
   x1[3] -= C.cdt;  // x^4 is stored relative to c t
+  const T gbar = C.gamma_in_j ? (reload(P.u[3] + i) + u1[3]) / (T(2) * C.c) : T(1);
   bool finite = true;
 #pragma unroll
   for (int q = 0; q < 4; ++q) finite = finite && isfinite(x1[q]) && isfinite(u1[q]);
@@ -538,14 +696,6 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
 #pragma unroll
   for (int q = 0; q < 3; ++q)
     if (!(fabs(x1[q] - x0[q]) < T(1))) flags |= ST_CFL;
-  // deposit, J = rho gamma v
-  if (finite && C.qmacro != T(0)) {
-    const T gbar = C.gamma_in_j ? (u0[3] + u1[3]) / (T(2) * C.c) : T(1);
-    if constexpr (sizeof(T) == sizeof(float))
-      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed, jt);
-    else
-      deposit<T, Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
-  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     P.x[q][i] = x1[q];
@@ -578,6 +728,13 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
     *key_out = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
   }
   if (fb) atomicAdd(&st->fallbacks, 1ull);
+  // deposit, J = rho gamma v
+  if (finite && C.qmacro != T(0)) {
+    if constexpr (sizeof(T) == sizeof(float))
+      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed, jt);
+    else
+      deposit<T, Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
+  }
 }
 
 // Warp-aggregated status: flags, FP64 evaluations and particle-steps of the warp's lanes.
