@@ -29,6 +29,7 @@ NO_GAMMA_IN_J = 1
 NO_GAMMA_TERMS = 2
 FROZEN_FIELDS = 4
 LITERAL_HALF_STEPS = 8
+RK4_AS_PRINTED = 16  # ablation only: the printed RK4 steps (Sec. 3.3) with x_n, u_n added to the finals
 
 OK, ERR_INVALID, ERR_CFL, ERR_NONFINITE = 0, 1, 4, 5
 

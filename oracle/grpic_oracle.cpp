@@ -59,8 +59,11 @@
  *       without bound near the horizon.
  *
  * Parity status: every function is pinned by a CPU test against closed forms, invariants
- * or brute force.  The literal RK4 coefficients printed in Sec. 3.3 are not implemented:
- * no reading of them is consistent (parity unpinned for that literal form).
+ * or brute force.  The RK4 steps exactly as printed in Sec. 3.3 have no consistent reading
+ * (parity unpinned for that literal form).  For an ablation ORC_RK4_AS_PRINTED takes the
+ * printed steps with only the missing x_n and u_n added to the final sums (stage proper-time
+ * steps dt/(2 gamma_1), dt/gamma_2, dt/gamma_3, dt/(2 gamma_4); trapezoid stage velocities);
+ * its stage weights add up to 5/6 of a step, which the tests show.
  *
  * Array layout at this boundary: a grid array is nz*ny*nx doubles, index (k*ny + j)*nx + i.
  * Particle arrays are planar: x4 holds x^1[0..n), x^2[0..n), x^3[0..n), x^4[0..n); u4 alike.
@@ -91,6 +94,7 @@ enum {
   ORC_NO_GAMMA_TERMS = 2u,  // skip the (identically zero) Christoffel terms of Eq. 11
   ORC_FROZEN_FIELDS = 4u,   // test-particle runs: the cycle does not advance the fields
   ORC_LITERAL_HALF_STEPS = 8u,  // each B half-step and the E step explicit in their own start values
+  ORC_RK4_AS_PRINTED = 16u,     // ablation: the printed RK4 steps, finals with x_n, u_n added
 };
 
 // ---------------------------------------------------------------------------------------
@@ -823,6 +827,12 @@ struct Ctx {
       x0[al] = s.x[al][p];
       u0[al] = s.u[al][p];
     }
+    double x1[4], u1[4];
+    if (cfg.flags & ORC_RK4_AS_PRINTED) {
+      const int e = rk4_as_printed(x0, u0, s.qm, fallbacks, x1, u1);
+      if (e != ORC_OK) return e;
+      return finish_push(s, p, x0, x1, u1, Jt, remove, horizon);
+    }
     double k1u[4], k2u[4], k3u[4], k4u[4];
     double k1x[4], k2x[4], k3x[4], k4x[4];
     if (!accel(x0, u0, s.qm, k1u)) return ORC_ERR_CFL;
@@ -850,16 +860,60 @@ struct Ctx {
     }
     for (int al = 0; al < 4; ++al) k4x[al] = us[al];
     if (!accel(xs, us, s.qm, k4u)) return ORC_ERR_CFL;
-    double x1[4], u1[4];
     for (int al = 0; al < 4; ++al) {
       x1[al] = x0[al] + h / 6.0 * (k1x[al] + 2.0 * k2x[al] + 2.0 * k3x[al] + k4x[al]);
       u1[al] = u0[al] + h / 6.0 * (k1u[al] + 2.0 * k2u[al] + 2.0 * k3u[al] + k4u[al]);
     }
+    return finish_push(s, p, x0, x1, u1, Jt, remove, horizon);
+  }
+
+  // The RK4 steps of Sec. 3.3 as printed, for the ablation (ORC_RK4_AS_PRINTED).  Stage k has
+  // the trapezoid velocity ut_k = (u_n + u_k)/2 (ut_1 = u_n), position x_n + ut_k dtau_{k-1}, the
+  // acceleration a_k = a~(x_k, ut_k) and gamma_k = f(ut_k^4, a_k^4) (Eq. 16); u_{k+1} = u_n + a_k
+  // dtau_k; dtau_1 = dt/(2 gamma_1), dtau_2 = dt/gamma_2, dtau_3 = dt/gamma_3,
+  // dtau_4 = dt/(2 gamma_4).  The final sums are taken as increments of x_n and u_n.
+  int rk4_as_printed(const double x0[4], const double u0[4], double qm, long long* fallbacks, double x1[4],
+                     double u1[4]) const {
+    const double dt = cfg.dt, c = cfg.c;
+    double ut[4][4], a[4][4], dtau[4];
+    double xk[4], uk[4];
+    for (int k = 0; k < 4; ++k) {
+      for (int al = 0; al < 4; ++al) {
+        if (k == 0) {
+          ut[k][al] = u0[al];
+          xk[al] = x0[al];
+        } else {
+          uk[al] = u0[al] + a[k - 1][al] * dtau[k - 1];
+          ut[k][al] = 0.5 * (u0[al] + uk[al]);
+        }
+      }
+      if (k > 0)
+        for (int al = 0; al < 4; ++al) xk[al] = x0[al] + ut[k][al] * dtau[k - 1];
+      if (!accel(xk, ut[k], qm, a[k])) return ORC_ERR_CFL;
+      int fb = 0;
+      const double g = gamma_f(ut[k][3], a[k][3], c, dt, &fb);
+      *fallbacks += fb;
+      dtau[k] = (k == 0 || k == 3) ? dt / (2.0 * g) : dt / g;
+    }
+    for (int al = 0; al < 4; ++al) {
+      x1[al] = x0[al] + (ut[0][al] * dtau[0] + 2.0 * (ut[1][al] * dtau[1] + ut[2][al] * dtau[2]) +
+                         ut[3][al] * dtau[3]) / 6.0;
+      u1[al] = u0[al] + (a[0][al] * dtau[0] + 2.0 * (a[1][al] * dtau[1] + a[2][al] * dtau[2]) +
+                         a[3][al] * dtau[3]) / 6.0;
+    }
+    return ORC_OK;
+  }
+
+  // After the RK4 step: checks, deposit of x_n -> x_{n+1}, new state, removal flag.
+  int finish_push(Species& s, size_t p, const double x0[4], const double x1[4], const double u1[4],
+                  std::vector<double>* Jt, bool* remove, bool* horizon) const {
+    const double c = cfg.c;
+    const double u0_4 = s.u[3][p];
     for (int al = 0; al < 4; ++al)
       if (!std::isfinite(x1[al]) || !std::isfinite(u1[al])) return ORC_ERR_NONFINITE;
     for (int ax = 0; ax < 3; ++ax)
       if (std::fabs(x1[ax] - x0[ax]) >= 1.0) return ORC_ERR_CFL;
-    const double gbar = (cfg.flags & ORC_NO_GAMMA_IN_J) ? 1.0 : (u0[3] + u1[3]) / (2.0 * c);
+    const double gbar = (cfg.flags & ORC_NO_GAMMA_IN_J) ? 1.0 : (u0_4 + u1[3]) / (2.0 * c);
     if (s.qmacro != 0.0)
       if (!deposit(x0, x1, s.qmacro, gbar, Jt)) return ORC_ERR_CFL;
     for (int al = 0; al < 4; ++al) {

@@ -26,7 +26,7 @@ def oracle_start(wl, threads=0, quad_order=2, flags=0, fields=None, r_excise=0.0
     else:
         ref.set_fields(*fields)
     for s, sp in enumerate(wl.species):
-        ref.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=1)
+        ref.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=sp.umode)
     return ref
 
 

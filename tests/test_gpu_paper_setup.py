@@ -1,0 +1,46 @@
+"""The application set-up of Sec. 6 (synth.kerr_jet_disk: 64 x 64 x 128 cells, c = 0.05, dt = 1,
+a = 0.95 m, contravariant B_z = 30, electron-positron pairs with |q/m| = 1e-3, a Keplerian disk of
+0.8 million particles in a free-falling corona): the whole workload, ~0.97 million particles in
+four species, against the oracle over three whole cycles, in FP64 and FP32-mixed.
+"""
+import numpy as np
+import pytest
+
+from parity_util import TOL, dilate, gpu_from_oracle, oracle_start, particle_errors, rel_l2_masked
+from test_gpu_parity import check_j
+from paper_0904_0232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_paper_setup_full_steps(prec):
+    wl = synth.kerr_jet_disk()
+    assert 0.95e6 < wl.n_particles < 1.0e6
+    ref = oracle_start(wl)
+    sim = gpu_from_oracle(ref, wl, prec)
+    tol = TOL[prec]
+    ns = len(wl.species)
+    seen = np.zeros((wl.nz, wl.ny, wl.nx), dtype=bool)
+    for step in range(3):
+        ref.step(1)
+        sim.step(1)
+        for s in range(ns):
+            ex, e4, eu = particle_errors(sim, ref, s, mask=dilate(seen, 1))
+            assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
+        d, b, J = sim.get_fields()
+        dr, br, Jr = ref.get_fields()
+        seen = dilate(seen, 3) | check_j(J, Jr, ref, ns, prec, 4 ** step)
+        assert rel_l2_masked(b, br, seen) <= tol["fields"] * 4 ** step
+        assert rel_l2_masked(d, dr, seen) <= max(tol["fields"], tol["J"]) * 4 ** step
+    st, sr = sim.stats(), ref.stats()
+    assert st["removed_horizon"] == sr["removed_horizon"] and st["removed_outer"] == sr["removed_outer"]
+    if prec == "fp32_mixed":
+        assert st["fp64_evals"] > 0

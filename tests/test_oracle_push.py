@@ -10,8 +10,9 @@ import pytest
 import oracle as O
 
 
-def _test_particle_run(N, m, a, dt, x_rel, u, nsteps, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0), qm=0.0, c=1.0):
-    o = O.Oracle(N, N, N, m, a, c, dt, flags=O.FROZEN_FIELDS, threads=1)
+def _test_particle_run(N, m, a, dt, x_rel, u, nsteps, B=(0.0, 0.0, 0.0), E=(0.0, 0.0, 0.0), qm=0.0, c=1.0,
+                       flags=0):
+    o = O.Oracle(N, N, N, m, a, c, dt, flags=O.FROZEN_FIELDS | flags, threads=1)
     o.init_uniform_field(E=E, B=B)
     Xc = o.centre
     x4 = np.array([[Xc[0] + x_rel[0]], [Xc[1] + x_rel[1]], [Xc[2] + x_rel[2]], [0.0]])
@@ -24,13 +25,14 @@ def _test_particle_run(N, m, a, dt, x_rel, u, nsteps, B=(0.0, 0.0, 0.0), E=(0.0,
     return traj
 
 
-def _gyration_error(dt):
+def _gyration_error(dt, flags=0):
     """m = 0, uniform contravariant B_z, E = 0: u_perp rotates at (q/m) B per unit proper time."""
     c, qm, B0, u0 = 1.0, 1.0, 0.5, 0.6
     u4 = c * np.sqrt(1 + (u0 / c) ** 2)
     T = 6.0
     n = int(round(T / dt))
-    traj = _test_particle_run(24, 0.0, 0.0, dt, (0.0, 0.0, 0.0), (u0, 0.0, 0.0, u4), n, B=(0, 0, B0), qm=qm)
+    traj = _test_particle_run(24, 0.0, 0.0, dt, (0.0, 0.0, 0.0), (u0, 0.0, 0.0, u4), n, B=(0, 0, B0), qm=qm,
+                              flags=flags)
     x, u = traj[-1]
     tau = n * dt / (u4 / c)
     w = qm * B0
@@ -47,6 +49,28 @@ def test_flat_gyration_closed_form_and_order():
     order_x = np.log2(e1x / e2x)
     assert 3.8 < order_u < 4.2, order_u
     assert 3.8 < order_x < 4.2, order_x
+
+
+def test_rk4_as_printed_ablation():
+    """The RK4 steps of Sec. 3.3 as printed (finals taken as increments of x_n and u_n; oracle
+    switch RK4_AS_PRINTED).  With m = 0, E = 0 and a uniform B_z nothing changes u^4, so every
+    gamma_k of Eq. 16 is u^4/c and the printed stage steps dt/(2 gamma), dt/gamma, dt/gamma,
+    dt/(2 gamma) weighted 1, 2, 2, 1 over 6 advance proper time by 5/6 of dt/gamma: x^4 gains
+    5/6 c dt per step, and the gyration phase lags by a fixed fraction that no step size
+    removes (an inconsistent scheme).  The classical reading (A1) converges at fourth order
+    (test_flat_gyration_closed_form_and_order)."""
+    c, dt, u0 = 1.0, 0.4, 0.6
+    u4 = c * np.sqrt(1 + u0 ** 2)
+    traj = _test_particle_run(24, 0.0, 0.0, dt, (0.0, 0.0, 0.0), (u0, 0.0, 0.0, u4), 5, B=(0, 0, 0.5), qm=1.0,
+                              flags=O.RK4_AS_PRINTED)
+    for k, (x, u) in enumerate(traj, start=1):
+        assert x[3] == pytest.approx(k * 5.0 / 6.0 * c * dt, rel=1e-14)
+        assert u[3] == pytest.approx(u4, rel=1e-14)
+    e1u, _ = _gyration_error(0.4, O.RK4_AS_PRINTED)
+    e2u, _ = _gyration_error(0.2, O.RK4_AS_PRINTED)
+    c1u, _ = _gyration_error(0.4)
+    assert e1u > 1e3 * c1u
+    assert e2u > 0.5 * e1u  # halving dt does not shrink the error
 
 
 def test_lorentz_force_flat():
