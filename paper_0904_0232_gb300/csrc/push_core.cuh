@@ -114,12 +114,13 @@ __device__ __noinline__ double quartic_closed64(double p, double q) {
 }
 
 // FP64 r^2 of a quadrature node from its FP64 p and q, by the Newton step of quartic_newton from
-// the FP32 root s0 (FP32 D0), rounded to FP32.
+// the FP32 root s0 (FP32 D0), rounded to FP32.  With |corr| <= 1e-5 s0 the difference s0 - corr of
+// two FP32 numbers is exact in FP64, so its rounding to FP32 is the FP32 subtraction itself.
 __device__ __forceinline__ float node_newton64(double p, double q, float s0, float D0) {
   if (s0 > 0.f && D0 > 0.f) {
     const double S = widen(s0);
     const float corr = narrow(fma(S, S - p, -q)) / D0;
-    if (fabsf(corr) <= 1e-5f * s0) return narrow(S - widen(corr));
+    if (fabsf(corr) <= 1e-5f * s0) return s0 - corr;
   }
   return narrow(quartic_closed64(p, q));
 }
@@ -469,7 +470,7 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
         float pa, qa, ta, pb, qb, tb;
         col_terms(C, L, col_coord<Q>(L, 2 * k), pa, qa, ta);
         col_terms(C, L, col_coord<Q>(L, 2 * k + 1), pb, qb, tb);
-        pJ2[k] = make_float2(pa, pb);
+        pJ2[k] = make_float2(0.5f * pa, 0.5f * pb);
         qJ2[k] = make_float2(qa, qb);
         tJ2[k] = make_float2(ta, tb);
       }
@@ -491,13 +492,15 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
         for (int si = 0; si < 2; ++si) {
           float pRow, qRow, tRow;
           row_terms(C, L, row_coord<Q>(L, si, pi), pRow, qRow, tRow);
-          const float2 pR = f2(pRow), qR = f2(qRow), tR = f2(tRow);
+          const float2 pR = f2(0.5f * pRow), qR = f2(qRow), tR = f2(tRow);
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
+            // with h = p / 2 (the halves of the row and column terms, exact):
+            // r^2 = h + sqrt(h^2 + q), the root's p > 0 form
             const float2 p = add2(pR, pJ2[k]);
             const float2 q = add2(qR, qJ2[k]);
-            const float2 D2 = fma2(p, p, mul2(f2(4.f), q));
-            const float2 r2 = mul2(f2(0.5f), fma2(D2, rsqrt2(D2), p));
+            const float2 D2 = fma2(p, p, q);
+            const float2 r2 = fma2(D2, rsqrt2(D2), p);
             const float2 r = mul2(r2, rsqrt2(r2));
             const float2 sig = fma2(r2, r2, q);
             float2 numer, den;
