@@ -334,6 +334,9 @@ __device__ __forceinline__ void deposit(const Grid& g, const Fields<T>& F, const
 struct FaceLattice {
   int K;
   float PK, XK, PI, PJ, i0, j0, cI, cJ, wI0, wI1, pK, qK;
+  // factors of the row and column terms of q = a^2 z^2 and of the spin term of k_K's numerator
+  // (a^2, -a, a or 0 by K), so that every term is a product instead of a choice
+  float qI, tI, qJ, tJ;
 };
 
 // Grid coordinate along I of lattice row ia = si * Q + pi, and the row terms of p, q and the
@@ -345,15 +348,15 @@ __device__ __forceinline__ float row_coord(const FaceLattice& L, int si, int pi)
   for (int t = 1; t < Q; ++t)
     if (pi == t) gx = (float)Gauss<Q>::x(t);
   const float lo_i = si ? L.PI : L.i0, w_i = si ? L.wI1 : L.wI0;
-  return lo_i + 0.5f * w_i + 0.5f * w_i * gx;
+  return fmaf(0.5f * w_i, gx, lo_i + 0.5f * w_i);
 }
 __device__ __forceinline__ void row_terms(const Consts<float>& C, const FaceLattice& L, float AIa, float& pRow,
                                           float& qRow, float& tRow) {
   const float XIa = AIa - L.cI;
   const float XI2 = XIa * XIa;
   pRow = L.pK + XI2;
-  qRow = L.qK + (L.K == 1 ? C.a2 * XI2 : 0.f);
-  tRow = L.K == 0 ? -C.a * XIa : 0.f;
+  qRow = fmaf(L.qI, XI2, L.qK);
+  tRow = L.tI * XIa;
 }
 // Column jb = sj * Q + pj: grid coordinate along J and the column terms.
 template <int Q>
@@ -364,14 +367,14 @@ __device__ __forceinline__ float col_coord(const FaceLattice& L, int jb) {
   for (int t = 1; t < Q; ++t)
     if (pj == t) gx = (float)Gauss<Q>::x(t);
   const float lo_j = sub ? L.PJ : L.j0, hi_j = sub ? L.j0 + 1.f : L.PJ;
-  return 0.5f * (lo_j + hi_j) + 0.5f * (hi_j - lo_j) * gx;
+  return fmaf(0.5f * (hi_j - lo_j), gx, 0.5f * (lo_j + hi_j));
 }
 __device__ __forceinline__ void col_terms(const Consts<float>& C, const FaceLattice& L, float AJ, float& pJ,
                                           float& qJ, float& tJ) {
   const float XJ = AJ - L.cJ;
   pJ = XJ * XJ;
-  qJ = L.K == 0 ? C.a2 * pJ : 0.f;
-  tJ = L.K == 1 ? C.a * XJ : 0.f;
+  qJ = L.qJ * pJ;
+  tJ = L.tJ * XJ;
 }
 
 // Eq. 18 integrand at one node from its r^2 (scalar form, for the deferred nodes).
@@ -464,15 +467,18 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       // sum of a face constant, a row term and a column term.
       L.pK = L.XK * L.XK - C.a2;
       L.qK = K == 2 ? C.a2 * L.XK * L.XK : 0.f;
+      L.qI = K == 1 ? C.a2 : 0.f;
+      L.tI = K == 0 ? -C.a : 0.f;
+      L.qJ = K == 0 ? C.a2 : 0.f;
+      L.tJ = K == 1 ? C.a : 0.f;
       float2 pJ2[Q], qJ2[Q], tJ2[Q];
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
-        float pa, qa, ta, pb, qb, tb;
-        col_terms(C, L, col_coord<Q>(L, 2 * k), pa, qa, ta);
-        col_terms(C, L, col_coord<Q>(L, 2 * k + 1), pb, qb, tb);
-        pJ2[k] = make_float2(0.5f * pa, 0.5f * pb);
-        qJ2[k] = make_float2(qa, qb);
-        tJ2[k] = make_float2(ta, tb);
+        const float2 XJ = add2(make_float2(col_coord<Q>(L, 2 * k), col_coord<Q>(L, 2 * k + 1)), f2(-L.cJ));
+        const float2 sq = mul2(XJ, XJ);
+        pJ2[k] = mul2(f2(0.5f), sq);
+        qJ2[k] = mul2(f2(L.qJ), sq);
+        tJ2[k] = mul2(f2(L.tJ), XJ);
       }
       const float nzz = -(L.XK * L.XK);
       // acc[si][k]: lane-wise sums over the rows of sub-interval si, node pair k of a row
@@ -515,25 +521,25 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
               numer = mul2(mul2(mul2(f2(C.two_m), r), r2), fma2(num, num, nrho4));
               den = mul2(nrho4, sig);
             }
-            const float2 v = fma2(numer, rcp2(den), f2(1.f));
-            float2 val = mul2(v, rsqrt2(v));
+            float2 v = fma2(numer, rcp2(den), f2(1.f));
+            float2 rv = rsqrt2(v);
             if (mixed) {
               const int bit = (si * Q + pi) * 2 * Q + 2 * k;
               if (!(p.x > 0.f) || !(r2.x >= C.r2_fp64)) {
-                val.x = 0.f;
+                v.x = rv.x = 0.f;
                 slow |= 1ull << bit;
               }
               if (!(p.y > 0.f) || !(r2.y >= C.r2_fp64)) {
-                val.y = 0.f;
+                v.y = rv.y = 0.f;
                 slow |= 1ull << (bit + 1);
               }
             }
             if (Q == 2) {
-              acc[si][k] = add2(acc[si][k], val);  // unit Gauss weights
+              acc[si][k] = fma2(v, rv, acc[si][k]);  // unit Gauss weights
             } else {
               const float2 w = make_float2(gw * (float)Gauss<Q>::w((2 * k) % Q),
                                            gw * (float)Gauss<Q>::w((2 * k + 1) % Q));
-              acc[si][k] = fma2(w, val, acc[si][k]);
+              acc[si][k] = fma2(w, mul2(v, rv), acc[si][k]);
             }
           }
         }
