@@ -84,7 +84,7 @@ struct Kerr {
   S r, f;        // r of Eq. 6, f of Eq. 4
   S k0, k1, k2;  // spatial k_m (k_3 = 1)
   S D;           // sqrt((R^2 - a^2)^2 + 4 a^2 z^2) = d(quartic)/d(r^2)
-  S inv_r, inv_rho2, inv_sig;  // 1/r, 1/(r^2 + a^2), 1/(r^4 + a^2 z^2), shared with the derivatives
+  S inv_r, inv_rho2, inv_sig, inv_D;  // 1/r, 1/(r^2 + a^2), 1/(r^4 + a^2 z^2), 1/D, shared with the derivatives
   bool flat;     // r = 0 (the disk z = 0, R <= a): metric taken flat, its limit there
 };
 
@@ -120,6 +120,7 @@ __device__ __forceinline__ Kerr<S> kerr_from_r2(S x, S y, S z, S m, S a, S r2, S
   K.inv_r = Ops::rcp(K.r);
   K.inv_rho2 = Ops::rcp(r2 + a2);
   K.inv_sig = Ops::rcp(r2 * r2 + q);
+  K.inv_D = Ops::rcp(D);
   K.f = S(2) * m * K.r * r2 * K.inv_sig;
   K.k0 = (K.r * x - a * y) * K.inv_rho2;
   K.k1 = (K.r * y + a * x) * K.inv_rho2;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void christoffel_uu(const Kerr<S>& K, S x, S y, S z, 
   const S k0 = K.k0, k1 = K.k1, k2 = K.k2;
   const S r2 = r * r, a2 = a * a;
   const S inv_rho2 = K.inv_rho2;
-  const S inv_D = Ops::rcp(K.D);
+  const S inv_D = K.inv_D;
   const S inv_r = K.inv_r;
   // grad r from the implicit quartic: r_x = x r / D, r_y = y r / D, r_z = z (r^2 + a^2) / (r D)
   const S rx = x * r * inv_D;

@@ -75,6 +75,84 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
 
+// f and k of Eqs. 4-5 for a point whose quartic (Eq. 6) takes its p = R^2 - a^2 > 0 branch and
+// r > 0 (every stage of a far-field particle, R > |a|): with h = p / 2, r^2 = h + sqrt(h^2 + q)
+// and D = 2 sqrt(h^2 + q); the reciprocal square roots give 1/D and 1/r as well.
+__device__ __forceinline__ Kerr<float> kerr_far(float x, float y, float z, float m, float a) {
+  Kerr<float> K;
+  const float a2 = a * a;
+  const float q = a2 * z * z;
+  const float h = 0.5f * (x * x + y * y + z * z - a2);
+  const float Dh2 = fmaf(h, h, q);
+  const float rDh = rsqrtf(Dh2);
+  const float r2 = fmaf(Dh2, rDh, h);
+  K.flat = false;
+  K.D = 2.f * Dh2 * rDh;
+  K.inv_D = 0.5f * rDh;
+  K.inv_r = rsqrtf(r2);
+  K.r = r2 * K.inv_r;
+  K.inv_rho2 = __fdividef(1.f, r2 + a2);
+  K.inv_sig = __fdividef(1.f, fmaf(r2, r2, q));
+  K.f = 2.f * m * K.r * r2 * K.inv_sig;
+  K.k0 = (K.r * x - a * y) * K.inv_rho2;
+  K.k1 = (K.r * y + a * x) * K.inv_rho2;
+  K.k2 = z * K.inv_r;
+  return K;
+}
+
+// Gamma^a_mn u^m u^n of christoffel_uu (metric.cuh) in FP32, the x and y components of its
+// 3-vectors, and of each row of the Jacobian d_i k_j, as packed pairs.
+__device__ __forceinline__ void christoffel_uu_x2(const Kerr<float>& K, float x, float y, float z, float a,
+                                                  const float u[4], float out[4]) {
+  if (K.flat) {
+    out[0] = out[1] = out[2] = out[3] = 0.f;
+    return;
+  }
+  const float r = K.r, f = K.f, k2 = K.k2;
+  const float2 kxy = make_float2(K.k0, K.k1), xy = make_float2(x, y);
+  const float r2 = r * r, a2 = a * a;
+  const float inv_rho2 = K.inv_rho2, inv_D = K.inv_D, inv_r = K.inv_r, inv_sig = K.inv_sig;
+  // grad r (r_x, r_y) = (x, y) r / D, r_z = z (r^2 + a^2) / (r D); grad f as in christoffel_uu
+  const float2 rxy = mul2(xy, f2(r * inv_D));
+  const float rz = z * (r2 + a2) * inv_D * inv_r;
+  const float fr = f * (3.f * inv_r - 4.f * r2 * r * inv_sig);
+  const float2 fxy = mul2(f2(fr), rxy);
+  const float fz = fr * rz - 2.f * a2 * z * f * inv_sig;
+  // row i of J[i][j] = d_i k_j: (J[i][0], J[i][1]) packed, J[i][2] alone
+  const float ri[3] = {rxy.x, rxy.y, rz};
+  float2 J01[3];
+  float J2[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float tr = 2.f * r * ri[i];
+    const float2 c = i == 0 ? make_float2(r, a) : (i == 1 ? make_float2(-a, r) : make_float2(0.f, 0.f));
+    J01[i] = mul2(fma2(f2(-tr), kxy, fma2(xy, f2(ri[i]), c)), f2(inv_rho2));
+    J2[i] = ((i == 2 ? 1.f : 0.f) - k2 * ri[i]) * inv_r;
+  }
+  const float s = K.k0 * u[0] + K.k1 * u[1] + k2 * u[2] + u[3];
+  const float2 ufxy = mul2(make_float2(u[0], u[1]), fxy);
+  const float uf = ufxy.x + ufxy.y + u[2] * fz;
+  // D_j = u^i J[i][j], E_j = u^i J[j][i]
+  const float2 D01 = fma2(f2(u[0]), J01[0], fma2(f2(u[1]), J01[1], mul2(f2(u[2]), J01[2])));
+  const float D2 = u[0] * J2[0] + u[1] * J2[1] + u[2] * J2[2];
+  float E[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) E[j] = u[0] * J01[j].x + u[1] * J01[j].y + u[2] * J2[j];
+  const float uD = u[0] * D01.x + u[1] * D01.y + u[2] * D2;
+  const float c1 = uf * s + f * uD;
+  const float fs = f * s;
+  const float hs2 = 0.5f * s * s;
+  const float2 w01 =
+      fma2(f2(c1), kxy, fma2(f2(fs), D01, fma2(f2(-fs), make_float2(E[0], E[1]), mul2(f2(-hs2), fxy))));
+  const float w2 = c1 * k2 + fs * (D2 - E[2]) - hs2 * fz;
+  const float kw = K.k0 * w01.x + K.k1 * w01.y + k2 * w2 - c1;
+  const float2 o01 = fma2(f2(-f * kw), kxy, w01);
+  out[0] = o01.x;
+  out[1] = o01.y;
+  out[2] = w2 - f * k2 * kw;
+  out[3] = -c1 + f * kw;
+}
+
 template <typename T>
 __device__ __forceinline__ T lerp(T a, T b, T w) {
   return fma(w, b - a, a);
@@ -208,7 +286,13 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
   // --- metric and Christoffel contraction at the particle
   T f, k0, k1, k2, gam[4];
   const T X = x[0] - C.xc, Y = x[1] - C.yc, Z = x[2] - C.zc;
-  const Kerr<T> Kt = kerr_eval<T>(X, Y, Z, C.m, C.a);
+  Kerr<T> Kt;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // far-field warps: every stage has R > |a| (the quartic's p > 0 branch)
+    Kt = mixed ? kerr_eval<T>(X, Y, Z, C.m, C.a) : kerr_far(X, Y, Z, C.m, C.a);
+  } else {
+    Kt = kerr_eval<T>(X, Y, Z, C.m, C.a);
+  }
   bool promoted = false;
   if constexpr (sizeof(T) == sizeof(float)) {
     if (mixed && Kt.r < C.r_fp64) {
@@ -227,7 +311,10 @@ __device__ __forceinline__ void accel(const Grid& g, const Fields<T>& F, const C
     }
   }
   if (!promoted) {
-    christoffel_uu<T>(Kt, X, Y, Z, C.a, u, gam);
+    if constexpr (sizeof(T) == sizeof(float))
+      christoffel_uu_x2(Kt, X, Y, Z, C.a, u, gam);
+    else
+      christoffel_uu<T>(Kt, X, Y, Z, C.a, u, gam);
     f = Kt.f;
     k0 = Kt.k0;
     k1 = Kt.k1;
