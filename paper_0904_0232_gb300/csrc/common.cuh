@@ -40,7 +40,19 @@ struct Grid {
   double r_fp64;  // FP32-mixed: promote metric evaluations to FP64 where r < r_fp64
   int quad_order;
   unsigned flags;
+  // field-step constants, formed once on the host in both precisions: dx^4 = c dt and 4 pi / c
+  double dx4, four_pi_c;
+  float dx4_f, four_pi_c_f;
 };
+
+template <typename T>
+__host__ __device__ inline T grid_dx4(const Grid& g) {
+  if constexpr (sizeof(T) == sizeof(float)) return g.dx4_f; else return g.dx4;
+}
+template <typename T>
+__host__ __device__ inline T grid_four_pi_c(const Grid& g) {
+  if constexpr (sizeof(T) == sizeof(float)) return g.four_pi_c_f; else return g.four_pi_c;
+}
 
 // Field views.  Metric cache: for each of the 6 field locations of a cell, (f, k0, k1, k2)
 // as 4 planes -> mc[(loc*4 + q)*ncell + cell].  mask bit l of a cell: location l is advanced.

@@ -78,6 +78,13 @@ struct Box {
 __device__ __forceinline__ bool box_cell(const Grid& g, const Box& bx, long long t, int& i, int& j, int& k) {
   const long long per = (long long)bx.nxb * bx.nyb * bx.nzb;
   if (t >= per) return false;
+  if (per <= 0xffffffffll) {  // 32-bit division (a 64-bit one is a long software sequence)
+    const unsigned u = (unsigned)t, r = u / (unsigned)bx.nxb;
+    i = bx.lo + (int)(u - r * (unsigned)bx.nxb);
+    j = bx.lo + (int)(r % (unsigned)bx.nyb);
+    k = bx.lo + (int)(r / (unsigned)bx.nyb);
+    return true;
+  }
   i = bx.lo + (int)(t % bx.nxb);
   const long long r = t / bx.nxb;
   j = bx.lo + (int)(r % bx.nyb);
@@ -153,8 +160,8 @@ __device__ __forceinline__ void b_update_cell(const Grid& g, const Fields<T>& F,
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
-  const T dx4 = (T)(g.c * g.dt);
-  const T coef = (mode == 2) ? dx4 : dx4 / T(2);
+  const T dx4 = grid_dx4<T>(g);
+  const T coef = (mode == 2) ? dx4 : dx4 * T(0.5);
   const T* ev[3] = {F.s[0], F.s[1], F.s[2]};
   // (alpha, beta) of F_{alpha beta}: b_x = F_yz, b_y = F_zx, b_z = F_xy
   const int al[3] = {1, 2, 0}, be[3] = {2, 0, 1};
@@ -202,9 +209,9 @@ __device__ __forceinline__ void d_update_cell(const Grid& g, const Fields<T>& F,
   const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
   const long long c = cell_index(g, i, j, k);
   const uint8_t bits = F.mask[c];
-  const T dx4 = (T)(g.c * g.dt);
-  const T coef = predictor ? dx4 / T(2) : dx4;
-  const double four_pi_over_c = 4.0 * M_PI / g.c;
+  const T dx4 = grid_dx4<T>(g);
+  const T coef = predictor ? dx4 * T(0.5) : dx4;
+  const T four_pi_over_c = grid_four_pi_c<T>(g);
 #pragma unroll
   for (int al = 0; al < 3; ++al) {
     T* out = predictor ? F.dp[al] : F.d[al];
@@ -222,7 +229,13 @@ __device__ __forceinline__ void d_update_cell(const Grid& g, const Fields<T>& F,
       const T* hq = F.s[q];
       div += sgn * (hq[c] - hq[c - st[nu]]);
     }
-    const T src = (T)(four_pi_over_c * F.J[al][c]);
+    // FP32 fields: J rounded to FP32 with integer operations (this GPU's conversions run on its
+    // reduced-rate FP64 pipe), then scaled in FP32
+    T src;
+    if constexpr (sizeof(T) == sizeof(float))
+      src = narrow(F.J[al][c]) * four_pi_over_c;
+    else
+      src = four_pi_over_c * F.J[al][c];
     out[c] = F.d[al][c] + (src - div) * coef;
   }
 }

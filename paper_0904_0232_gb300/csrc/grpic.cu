@@ -459,6 +459,10 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.flags = cfg->flags;
   g.r_fp64 = (cfg->fp64_radius == 0.0 ? 4.0 : cfg->fp64_radius) * cfg->m;
   if (cfg->fp64_radius < 0.0) g.r_fp64 = -1.0;
+  g.dx4 = cfg->c * cfg->dt;
+  g.four_pi_c = 4.0 * M_PI / cfg->c;
+  g.dx4_f = (float)g.dx4;
+  g.four_pi_c_f = (float)g.four_pi_c;
 
   c->fields = dev_alloc(c, 15 * (size_t)ncell * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));

@@ -18,12 +18,20 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Lanes of a warp holding the same key (cell-sorted particles put several in one cell) share one
+// atomic: the lowest of them adds the group's size.  Returns the group; act = the lanes taking part.
+__device__ __forceinline__ unsigned key_peers(unsigned act, uint32_t k) { return __match_any_sync(act, k); }
+
 __global__ void k_hist(const uint32_t* __restrict__ key, long long n, const int* __restrict__ n_dev,
                        int* __restrict__ counts, long long dead_bin) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n || i >= (long long)(*n_dev)) return;
-  const uint32_t k = key[i];
-  atomicAdd(counts + (k == kDead ? dead_bin : (long long)k), 1);
+  const bool valid = i < n && i < (long long)(*n_dev);
+  const uint32_t k = valid ? key[i] : kDead;
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  const unsigned peers = key_peers(act, k);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicAdd(counts + (k == kDead ? dead_bin : (long long)k), __popc(peers));
 }
 
 // Inclusive scan of one value per thread across the block.
@@ -110,10 +118,17 @@ template <typename T>
 __global__ void k_scatter(const Particles<T> src, const Particles<T> dst, int* __restrict__ cursor,
                           long long dead_bin) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= src.n || i >= (long long)(*src.n_dev)) return;
-  const uint32_t k = src.key[i];
-  if (k == kDead) return;
-  const int pos = atomicAdd(cursor + k, 1);
+  bool valid = i < src.n && i < (long long)(*src.n_dev);
+  const uint32_t k = valid ? src.key[i] : kDead;
+  valid = valid && k != kDead;
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  // one atomic per group of lanes in the same cell; each lane takes its rank in the group
+  const unsigned peers = key_peers(act, k);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  int first = 0;
+  if (lane == leader) first = atomicAdd(cursor + k, __popc(peers));
+  const int pos = __shfl_sync(peers, first, leader) + __popc(peers & ((1u << lane) - 1u));
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     dst.x[q][pos] = src.x[q][i];
