@@ -67,15 +67,12 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
 // the tile, deposits straight to global J.
 constexpr int kJTileFloats = 3072;
 
-// perm: the block -> particle-chunk map is chunk = blockIdx.x * perm mod gridDim.x (perm coprime
-// to gridDim.x; 1 = in order).  Cell-sorted particles put the FP64-heavy chunks near the hole in
-// one contiguous run; a permutation spreads them over the whole launch, so the FP64 pipes of all
-// SMs share that work alongside FP32 work instead of a few SMs at a time doing mostly FP64.
+// perm: the block -> particle-chunk map (spread_chunk in common.cuh; 1 = in order).
 template <int Q, int MINB, bool TILE>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
                                                            float r_near2, unsigned perm, DevStatus* st) {
-  const unsigned chunk = (unsigned)(((unsigned long long)blockIdx.x * perm) % gridDim.x);
+  const unsigned chunk = spread_chunk(blockIdx.x, gridDim.x, perm);
   const long long i = chunk * (long long)blockDim.x + threadIdx.x;
   unsigned flags = 0, n64 = 0;
   bool active = i < P.n && i < (long long)(*P.n_dev);
@@ -211,7 +208,7 @@ void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<f
   const Consts<float> C = make_consts<float>(g, sp);
   const double rn = near_radius(g);
   const float r_near2 = (float)(rn * rn);
-  const unsigned perm = spread ? coprime_multiplier(nb) : 1u;
+  const unsigned perm = spread ? spread_multiplier(nb) : 1u;
   if (g.quad_order == 1)
     k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
   else if (g.quad_order == 3)
