@@ -299,7 +299,7 @@ def run_gpu(args, dist):
         tuned = {"tuning": None, "cached": False, "trials": 0, "ms_per_step": None}
     else:
         simt = make_sim(wl, "fp32_mixed", args)
-        tuned = autotune.tune(simt, sig, steps=4)
+        tuned = autotune.tune(simt, sig, steps=8)
         simt.close()
         del simt
         torch.cuda.empty_cache()
@@ -599,7 +599,7 @@ def run_jet(args, dist):
     tuning = None
     if not args.no_tune:
         simt = make()
-        tuning = autotune.tune(simt, f"kerr_jet_disk_64x64x128|Q{args.quad}|{wl.n_particles}", steps=4)["tuning"]
+        tuning = autotune.tune(simt, f"kerr_jet_disk_64x64x128|Q{args.quad}|{wl.n_particles}", steps=8)["tuning"]
         simt.close()
     sim = make(tuning)
     sim.set_profiling(True)

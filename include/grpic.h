@@ -231,9 +231,10 @@ grpic_status grpic_gauss_residual(grpic_ctx* ctx, double* res, int mem, double* 
  *   overlap:            split = 1 only, as above
  *   j_tile:             split = 0, Q = 2: 1 accumulates J per block in a shared-memory FP32 tile over
  *                       the nodes the block's particles can reach, added to the FP64 J once per node
- *   spread:             split = 0: 1 maps blocks to particle chunks by a permutation of groups of 16
- *                       consecutive chunks, spreading the near-hole (FP64-heavy) chunks over the launch
- *                       while each group keeps neighbouring cells together; 0 keeps them in order
+ *   spread:             split = 0: G = 1, 2, 4, ... 64 maps blocks to particle chunks by a permutation of
+ *                       groups of G consecutive chunks, spreading the near-hole (FP64-heavy) chunks over
+ *                       the launch while each group keeps neighbouring cells together (larger G: more
+ *                       L2 locality, less even FP64 load); 0 keeps them in order
  * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */
 typedef struct {
   int far_min_blocks;

@@ -22,7 +22,7 @@ import os
 
 CHOICES = {
     "split": (0, 1),
-    "spread": (0, 1),
+    "spread": (0, 1, 16),
     "j_tile": (0, 1),
     "far_min_blocks": (4, 5, 6),
     "near_blocks_per_sm": (1, 2, 4),

@@ -182,24 +182,32 @@ void launch_near_keys(const Particles<float>& P, const uint32_t* list, const uin
 // A multiplier coprime to n near 0.618 n: blockIdx * m mod n permutes n work items evenly.
 unsigned coprime_multiplier(unsigned n);
 
-// Block -> work-chunk map of the push launches: groups of kSpreadGroup consecutive chunks are
-// permuted, group g -> g * perm mod (number of full groups), perm coprime to that number (1 keeps
-// the order; a partial last group stays in place).  Cell-sorted particles put the FP64-heavy
-// chunks near the hole in one contiguous run; the permutation spreads them over the whole launch,
-// so the FP64 pipes of all SMs share that work alongside FP32 work, while the blocks of a group,
-// which run at about the same time, keep neighbouring cells together (their field stencils and J
-// nodes stay in L2).
-constexpr unsigned kSpreadGroup = 16;
-__device__ __forceinline__ unsigned spread_chunk(unsigned b, unsigned n, unsigned perm) {
-  const unsigned nfull = n / kSpreadGroup;
-  if (perm == 1u || b >= nfull * kSpreadGroup) return b;
-  return (unsigned)(((unsigned long long)(b / kSpreadGroup) * perm) % nfull) * kSpreadGroup + b % kSpreadGroup;
+// Block -> work-chunk map of the push launches: groups of 2^lg consecutive chunks are permuted,
+// group g -> g * perm mod (number of full groups), perm coprime to that number (1 keeps the order;
+// a partial last group stays in place).  Cell-sorted particles put the FP64-heavy chunks near the
+// hole in one contiguous run; the permutation spreads them over the whole launch, so the FP64
+// pipes of all SMs share that work alongside FP32 work, while the blocks of a group, which run at
+// about the same time, keep neighbouring cells together (their field stencils and J nodes stay in
+// L2).  Larger groups favour that locality, smaller ones the spreading of FP64 work.
+__device__ __forceinline__ unsigned spread_chunk(unsigned b, unsigned n, unsigned perm, int lg) {
+  const unsigned nfull = n >> lg;
+  if (perm == 1u || b >= (nfull << lg)) return b;
+  const unsigned mask = (1u << lg) - 1u;
+  return ((unsigned)(((unsigned long long)(b >> lg) * perm) % nfull) << lg) | (b & mask);
 }
-inline unsigned spread_multiplier(unsigned n) { return coprime_multiplier(n / kSpreadGroup); }
+inline unsigned spread_multiplier(unsigned n, int lg) { return coprime_multiplier(n >> lg); }
+// group size of the batched push
+constexpr int kBatchSpreadLog2 = 4;
+// log2 of a push spread group size (tuning value: 1, 2, 4, ... 64)
+inline int spread_log2(int group) {
+  int lg = 0;
+  while ((1 << lg) < group) ++lg;
+  return lg;
+}
 // Unsplit alternative: one launch, far-field or FP32-mixed code chosen per warp by the same
 // near_radius criterion.
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, bool spread, cudaStream_t stream);
+                        DevStatus* st, int minb, bool tile, int spread, cudaStream_t stream);
 
 template <typename T>
 void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,

@@ -175,7 +175,7 @@ void enqueue_select_push(grpic_ctx* c) {
     if (!S.loaded || S.n == 0) continue;
     refresh_count(S);
     launch_push_select(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
-                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->tune.spread != 0, c->stream);
+                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->tune.spread, c->stream);
     c->launches += 1;
   }
 }
@@ -873,7 +873,7 @@ grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
   if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
       t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1) ||
       (t->split != 0 && t->split != 1) || (t->j_tile != 0 && t->j_tile != 1) ||
-      (t->spread != 0 && t->spread != 1))
+      t->spread < 0 || t->spread > 64 || (t->spread & (t->spread - 1)) != 0)
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
   c->tune = *t;
   c->cfg.sort_interval = t->sort_interval;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
   __shared__ SpeciesDesc<T> sS;
   __shared__ DevStatus* sst;
   __shared__ int s_cur;
-  const int bi = (int)spread_chunk(blockIdx.x, (unsigned)nblk, perm);
+  const int bi = (int)spread_chunk(blockIdx.x, (unsigned)nblk, perm, kBatchSpreadLog2);
   const BlockEntry e = blk[bi];
   // stage the descriptor parts this block needs with one coalesced copy by all threads (the
   // launch constants were built on the host)
@@ -257,7 +257,7 @@ void launch_batch_push_q(const BatchTables<T>& bt, int quad_order, cudaStream_t 
   // scheduler balances instances of very different cost
   const unsigned nb = (unsigned)bt.npart;
   if (bt.npart == 0) return;
-  const unsigned perm = spread_multiplier(nb);
+  const unsigned perm = spread_multiplier(nb, kBatchSpreadLog2);
   if (quad_order == 1)
     k_push_deposit_batch<T, 1, MIXED><<<nb, 128, 0, stream>>>(bt.desc, bt.part, bt.npart, perm);
   else if (quad_order == 3)

@@ -71,8 +71,8 @@ constexpr int kJTileFloats = 3072;
 template <int Q, int MINB, bool TILE>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
-                                                           float r_near2, unsigned perm, DevStatus* st) {
-  const unsigned chunk = spread_chunk(blockIdx.x, gridDim.x, perm);
+                                                           float r_near2, unsigned perm, int lg, DevStatus* st) {
+  const unsigned chunk = spread_chunk(blockIdx.x, gridDim.x, perm, lg);
   const long long i = chunk * (long long)blockDim.x + threadIdx.x;
   unsigned flags = 0, n64 = 0;
   bool active = i < P.n && i < (long long)(*P.n_dev);
@@ -202,25 +202,26 @@ unsigned coprime_multiplier(unsigned n) {
 }
 
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, bool spread, cudaStream_t stream) {
+                        DevStatus* st, int minb, bool tile, int spread, cudaStream_t stream) {
   if (P.n <= 0) return;
   const unsigned nb = blocks_for(P.n, 128);
   const Consts<float> C = make_consts<float>(g, sp);
   const double rn = near_radius(g);
   const float r_near2 = (float)(rn * rn);
-  const unsigned perm = spread ? spread_multiplier(nb) : 1u;
+  const int lg = spread > 0 ? spread_log2(spread) : 0;
+  const unsigned perm = spread > 0 ? spread_multiplier(nb, lg) : 1u;
   if (g.quad_order == 1)
-    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
   else if (g.quad_order == 3)
-    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
   else if (tile && minb >= 5)
-    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
   else if (tile)
-    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
   else if (minb >= 5)
-    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
   else
-    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, st);
+    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
 }
 
 }  // namespace grpic

@@ -106,7 +106,8 @@ def test_split_equals_single_kernel(mode):
 
 @pytest.mark.parametrize("far,near,overlap,split,j_tile,spread", [
     (4, 1, 1, 1, 0, 0), (5, 2, 0, 1, 0, 0), (6, 3, 1, 1, 0, 0), (5, 4, 0, 1, 0, 0), (4, 4, 1, 0, 0, 0),
-    (5, 4, 1, 0, 0, 0), (4, 4, 1, 0, 1, 0), (5, 4, 1, 0, 1, 0), (4, 4, 1, 0, 0, 1), (5, 4, 1, 0, 1, 1)])
+    (5, 4, 1, 0, 0, 0), (4, 4, 1, 0, 1, 0), (5, 4, 1, 0, 1, 0), (4, 4, 1, 0, 0, 1), (5, 4, 1, 0, 1, 1),
+    (4, 4, 1, 0, 0, 4), (4, 4, 1, 0, 0, 16), (5, 4, 1, 0, 1, 64)])
 def test_tuning_variants_agree(far, near, overlap, split, j_tile, spread):
     wl = _workload(seed=33)
     ref = oracle_start(wl)
@@ -170,7 +171,7 @@ def test_tuning_validation():
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, "fp32_mixed")
     for bad in [(3, 2, 1, 1, 0), (7, 2, 1, 1, 0), (5, 0, 1, 1, 0), (5, 2, 0, 1, 0), (5, 2, 1, 2, 0), (5, 2, 1, 1, 2),
-                (5, 2, 1, 1, 0, 2)]:
+                (5, 2, 1, 1, 0, 2), (5, 2, 1, 1, 0, 0, 3), (5, 2, 1, 1, 0, 0, 128), (5, 2, 1, 1, 0, 0, -1)]:
         with pytest.raises(GrpicError):
             sim.set_tuning(*bad)
     assert sim.tuning()["far_min_blocks"] == 4
