@@ -9,7 +9,9 @@ Coordinate descent: starting from the current choice, each knob in turn is set t
 values while the others stay fixed, and the fastest is kept; two rounds.  A trial times
 `steps` whole timesteps with CUDA events on the context's stream after one untimed step (the
 first step after a change of sort interval or kernel variant pays for the change).  Trials
-advance the simulation like warm-up steps do.  Winners are cached in a JSON file keyed by the
+advance the simulation like warm-up steps do, and the step time drifts as the state evolves (the
+FP64 load grows as plasma falls in), so each value of a knob is timed twice, the values in
+forward and then in reverse order, and the means are compared: a steady drift cancels.  Winners are cached in a JSON file keyed by the
 device name and a workload signature, so later runs can reuse them without tuning.
 
 The batched engine has one knob, the persistent blocks per SM of its launches; tune_batch
@@ -97,12 +99,13 @@ def tune(sim, signature: str, steps: int = 4, rounds: int = 2, cache: str = DEFA
     for _ in range(rounds):
         changed = False
         for knob, values in choices.items():
-            results = {}
-            for v in values:
+            times = {}
+            for v in list(values) + list(values)[::-1]:
                 cand = dict(cur, **{knob: v})
                 sim.set_tuning(**cand)
-                results[v] = timer(sim, steps)
+                times.setdefault(v, []).append(timer(sim, steps))
                 trials += 1
+            results = {v: sum(t) / len(t) for v, t in times.items()}
             v_best = min(results, key=results.get)
             if v_best != cur[knob]:
                 changed = True

@@ -51,6 +51,27 @@ def test_coupled_cost_second_round(tmp_path):
     assert r["ms_per_step"] >= best
 
 
+def test_drift_of_the_step_time_cancels(tmp_path):
+    """The state evolves while tuning (each trial advances it) and the step time grows with it:
+    timing every value forward and backward cancels a linear drift that would otherwise favour
+    the values tried first."""
+    def cost(far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile, spread=0):
+        return {1: 1.0, 2: 0.96, 4: 0.92}[sort_interval] + 0.01 * far_min_blocks
+
+    class Drifting(FakeSim):
+        def __init__(self):
+            super().__init__(cost)
+
+    def drift_timer(sim, steps):
+        sim.calls += 1
+        return sim.cost(**sim.t) + 0.05 * sim.calls
+
+    sim = Drifting()
+    r = autotune.tune(sim, "d", cache=str(tmp_path / "t.json"), timer=drift_timer, device="fake",
+                      choices={"sort_interval": (1, 2, 4)}, rounds=1)
+    assert r["tuning"]["sort_interval"] == 4
+
+
 def test_cache_reused(tmp_path):
     cache = str(tmp_path / "t.json")
     sim = FakeSim(separable)
