@@ -48,7 +48,7 @@ FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 # DRAM bytes per particle-step of the push kernel (dram__bytes_read + dram__bytes_write of one
 # launch over its particles), from an ncu capture at the bench size, valid for the push sources
 # whose hash is recorded with it.
-PUSH_TRAFFIC = {"sha": "8942cfab6db11878", "bytes_per_particle": 2536.80e6 / 15.61e6}
+PUSH_TRAFFIC = {"sha": "421ab5f26fd9cdd4", "bytes_per_particle": 1381.02e6 / 15.61e6}
 
 
 def kernel_sha():
