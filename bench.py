@@ -38,8 +38,10 @@ UNIT = "particle-steps/s"
 # Arithmetic operations per particle-step of the push + deposit formulation (FMA = 2,
 # add/mul/div/sqrt = 1; index arithmetic excluded), by Gauss-Legendre order Q of Eq. 18:
 # RK4 push 2130 (4 x 492 per stage evaluation + stage algebra) + deposit 6 face weightings x
-# 4 sub-areas x Q^2 integrand evaluations (42 each) + split/weights/flux.  Derivation table
-# in DESIGN.md ("Algorithmic work per particle-step").
+# 4 sub-areas x Q^2 integrand evaluations (42 each) + split/weights/flux.  Per stage evaluation:
+# quartic root 15, f and k 23, Gamma u u 157, conversion of (b, d) 32, Lorentz term 39, gather
+# of six components 219; per integrand evaluation: node position, quartic, density and weight;
+# removal test 17.
 ALG_FLOPS = {1: 3570, 2: 6600, 3: 11640}
 
 # Nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 lanes x 2 flops x 2070 MHz.
@@ -363,7 +365,8 @@ def run_gpu(args, dist):
     if args.fp32_compare_steps > 0:
         ms32, ps32, prof32, _, _, _ = leg("fp32_mixed", args.fp32_compare_steps, args.warmup, fp64_radius=-1.0)
         fp32_all = summary(ms32, ps32, prof32, args.fp32_compare_steps,
-                           "fp64_radius < 0: no FP64 metric evaluations (error vs oracle in DESIGN.md)")
+                           "fp64_radius < 0: no FP64 metric evaluations (the FP32-only comparison; its particle error against "
+                           "the FP64 oracle after one push is ~1e-7 relative, like the policy's)")
 
     # --- end to end through the C ABI with host buffers
     e2e = None
