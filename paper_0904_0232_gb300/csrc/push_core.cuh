@@ -641,13 +641,19 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
           S[si][(2 * k + 1) >= Q ? 1 : 0] += acc[si][k].y;
         }
       // The marked nodes of FP32-mixed warps.  p and q in FP64 are sums of FP64 face, row and
-      // column terms, like their FP32 counterparts: the face and row terms are formed once.
+      // column terms, like their FP32 counterparts: face, row and column terms are formed once.
       if (slow) {
         const double cK = sel3(K, C.dxc, C.dyc, C.dzc), cI = sel3(K, C.dyc, C.dzc, C.dxc);
         const double cJ = sel3(K, C.dzc, C.dxc, C.dyc);
         const double XK64 = widen(L.PK) - cK;
         const double pK64 = fma(XK64, XK64, -C.da2);
         const double qK64 = K == 2 ? C.da2 * XK64 * XK64 : 0.0;
+        double sqJ[2 * Q];  // squared FP64 offsets of the columns
+#pragma unroll
+        for (int jb = 0; jb < 2 * Q; ++jb) {
+          const double XJ64 = widen(col_coord<Q>(L, jb)) - cJ;
+          sqJ[jb] = XJ64 * XJ64;
+        }
         int row = -1;
         double pRow64 = 0.0, qRow64 = 0.0;
         do {
@@ -671,9 +677,12 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
               pRow64 = fma(XI64, XI64, pK64);
               qRow64 = K == 1 ? C.da2 * XI64 * XI64 : qK64;
             }
-            const double XJ64 = widen(AJ) - cJ;
-            const double p64 = fma(XJ64, XJ64, pRow64);
-            const double q64 = K == 0 ? C.da2 * XJ64 * XJ64 : qRow64;
+            double sq = sqJ[0];
+#pragma unroll
+            for (int t = 1; t < 2 * Q; ++t)
+              if (jb == t) sq = sqJ[t];
+            const double p64 = pRow64 + sq;
+            const double q64 = K == 0 ? C.da2 * sq : qRow64;
             r2 = node_newton64(p64, q64, r2, D);
             ++n64;
           }
