@@ -171,13 +171,18 @@ grpic_status grpic_stage(grpic_ctx* ctx, int stage);
 /* Wait for the context's stream and report the device status. */
 grpic_status grpic_sync(grpic_ctx* ctx);
 
-/* Copy out the prognostic field and J (any pointer may be NULL). */
+/* Copy out the prognostic field and J (any pointer may be NULL).  The field tensor of Eq. 8
+ * (Sec. 3) on the staggered lattice of Sec. 3, Fig. 2: d = contravariant (F^{x4}, F^{y4}, F^{z4})
+ * on edges, b = covariant (F_{yz}, F_{zx}, F_{xy}) on faces, J = contravariant current of Sec. 4
+ * at the d points; each (3, nz, ny, nx) float64, x fastest.  mem: GRPIC_MEM_HOST or
+ * GRPIC_MEM_DEVICE for the destination.  FP32-mixed contexts widen their FP32 fields. */
 grpic_status grpic_get_fields(grpic_ctx* ctx, double* d3, double* b3, double* J3, int mem);
 
 /* Number of live particles of a species. */
 grpic_status grpic_num_particles(grpic_ctx* ctx, int species, int64_t* n);
 
-/* Copy out the live particles of a species in the library's (cell-sorted) order, with ids
+/* Particle state of Sec. 3.3 (positions x^a and four-velocities u^a advanced by Eqs. 13-16).
+ * Copy out the live particles of a species in the library's (cell-sorted) order, with ids
  * (after grpic_step; after hand-driven stages, the particles listed since the last sort stage).
  * *n_inout: capacity of the caller's arrays on entry, particles written on return.
  * x^4 is returned as the particle's own clock coordinate. */

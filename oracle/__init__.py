@@ -30,6 +30,7 @@ NO_GAMMA_TERMS = 2
 FROZEN_FIELDS = 4
 LITERAL_HALF_STEPS = 8
 RK4_AS_PRINTED = 16  # ablation only: the printed RK4 steps (Sec. 3.3) with x_n, u_n added to the finals
+ANALYTIC_WALD = 32  # test-particle pins only: the Lorentz term of Eq. 15 takes Wald's field at the particle
 
 OK, ERR_INVALID, ERR_CFL, ERR_NONFINITE = 0, 1, 4, 5
 
@@ -98,6 +99,8 @@ def lib():
                 "orc_stage_zero_j": (ctypes.c_int, [_V]),
                 "orc_stage_push_deposit": (ctypes.c_int, [_V]),
                 "orc_accel": (ctypes.c_int, [_V, ctypes.c_double, _D, _D, _D]),
+                "orc_gather": (ctypes.c_int, [_V, ctypes.c_int, _D, _D]),
+                "orc_set_wald_b0": (None, [_V, ctypes.c_double]),
                 "orc_deposit": (ctypes.c_int, [_V, _D, _D, ctypes.c_double, ctypes.c_double]),
                 "orc_face_weights": (None, [_V, ctypes.c_int, _D, _I, _D]),
                 "orc_get_stats": (None, [_V, _LL]),
@@ -341,6 +344,16 @@ class Oracle:
         out = np.zeros(4)
         self._chk(lib().orc_accel(self._h, float(q_over_m), _dp(_f64(x4)), _dp(_f64(u4)), _dp(out)), "accel")
         return out
+
+    def gather(self, comp, x3):
+        """CIC value of prognostic component comp (0..2 = d, 3..5 = b) at grid position x3."""
+        out = np.zeros(1)
+        self._chk(lib().orc_gather(self._h, int(comp), _dp(_f64(x3)), _dp(out)), "gather")
+        return float(out[0])
+
+    def set_wald_b0(self, B0):
+        """Field strength of Wald's field for a context created with ANALYTIC_WALD."""
+        lib().orc_set_wald_b0(self._h, float(B0))
 
     def deposit(self, x1, x2, q_macro, gbar=1.0):
         self._chk(lib().orc_deposit(self._h, _dp(_f64(x1)), _dp(_f64(x2)), float(q_macro), float(gbar)), "deposit")

@@ -95,6 +95,7 @@ enum {
   ORC_FROZEN_FIELDS = 4u,   // test-particle runs: the cycle does not advance the fields
   ORC_LITERAL_HALF_STEPS = 8u,  // each B half-step and the E step explicit in their own start values
   ORC_RK4_AS_PRINTED = 16u,     // ablation: the printed RK4 steps, finals with x_n, u_n added
+  ORC_ANALYTIC_WALD = 32u,      // test-particle pins: the Lorentz term takes Wald's field at the particle
 };
 
 // ---------------------------------------------------------------------------------------
@@ -452,6 +453,8 @@ typedef struct {
 
 namespace {
 
+void wald_field(const double X[3], double m, double a, double B0, double Fd[4][4], double Fu[4][4]);
+
 struct Ctx {
   orc_config cfg{};
   double Xc[3]{};
@@ -465,6 +468,7 @@ struct Ctx {
   std::vector<double> glx, glw;
   long long stat_removed_horizon = 0, stat_removed_outer = 0, stat_fallback = 0, stat_steps = 0;
   double gterm_max = 0.0, gterm_scale = 0.0;
+  double wald_B0 = 0.0;  // field strength of ORC_ANALYTIC_WALD
 
   size_t idx(int i, int j, int k) const { return ((size_t)k * n[1] + j) * n[0] + i; }
 
@@ -721,13 +725,18 @@ struct Ctx {
     double g[4][4], G[4][4][4];
     metric_at(X, cfg.m, cfg.a, g);
     christoffel_at(X, cfg.m, cfg.a, G);
-    double b[3], d[3];
-    for (int q = 0; q < 3; ++q) {
-      if (!gather(q, x, &d[q])) return false;
-      if (!gather(3 + q, x, &b[q])) return false;
-    }
     double Fu[4][4], Fd[4][4];
-    complete_tensor(g, b, d, Fu, Fd);
+    if (cfg.flags & ORC_ANALYTIC_WALD) {
+      // the field tensor evaluated in closed form at the particle instead of gathered
+      wald_field(X, cfg.m, cfg.a, wald_B0, Fd, Fu);
+    } else {
+      double b[3], d[3];
+      for (int q = 0; q < 3; ++q) {
+        if (!gather(q, x, &d[q])) return false;
+        if (!gather(3 + q, x, &b[q])) return false;
+      }
+      complete_tensor(g, b, d, Fu, Fd);
+    }
     for (int al = 0; al < 4; ++al) {
       double lor = 0.0;
       for (int be = 0; be < 4; ++be) {
@@ -1440,6 +1449,16 @@ int orc_stage_zero_j(void* p) {
   return ORC_OK;
 }
 int orc_stage_push_deposit(void* p) { return static_cast<Ctx*>(p)->push_deposit_all(); }
+
+// CIC gather of prognostic component comp (0..2 = d, 3..5 = b) at grid position x3.
+int orc_gather(void* p, int comp, const double* x3, double* out) {
+  Ctx* ctx = static_cast<Ctx*>(p);
+  if (comp < 0 || comp > 5) return ORC_ERR_INVALID;
+  return ctx->gather(comp, x3, out) ? ORC_OK : ORC_ERR_CFL;
+}
+
+// Field strength B0 of Wald's field for contexts created with ORC_ANALYTIC_WALD.
+void orc_set_wald_b0(void* p, double B0) { static_cast<Ctx*>(p)->wald_B0 = B0; }
 
 int orc_accel(void* p, double qm, const double* x4, const double* u4, double* out4) {
   Ctx* ctx = static_cast<Ctx*>(p);

@@ -90,6 +90,53 @@ def face_ambiguity_mask(ref, shape, nspecies, delta=1e-5):
     return mask
 
 
+def check_j(J, Jr, ref, nspecies, prec, factor=1.0):
+    """J parity.  FP32: nodes touched by a particle whose cell index is decided within rounding
+    of a face are compared only through the split-independent total flux per component.
+    Returns the mask used (all False for FP64)."""
+    tol = TOL[prec]["J"] * factor
+    if prec == "fp64":
+        assert rel_l2(J, Jr) <= tol, rel_l2(J, Jr)
+        return np.zeros(J.shape[1:], dtype=bool)
+    mask = face_ambiguity_mask(ref, J.shape[1:], nspecies)
+    assert mask.mean() < 0.25, mask.mean()  # at 16 particles per cell a few % of particles are near a face
+    assert rel_l2_masked(J, Jr, mask) <= tol, rel_l2_masked(J, Jr, mask)
+    for K in range(3):
+        assert abs(J[K].sum() - Jr[K].sum()) <= tol * max(np.abs(Jr[K]).sum(), 1e-300)
+    return mask
+
+
+def _near_face(x, delta):
+    fr = x - np.floor(x)
+    return (np.minimum(fr, 1.0 - fr) < delta).any(0)
+
+
+def well_conditioned(wl, nsteps, delta=1e-4, max_rounds=6, **oracle_kw):
+    """The workload without the particles whose zig-zag split the oracle decides within `delta` of a
+    cell face in any of its first `nsteps` whole steps (start or end of a move near a face).  For the
+    rest, an FP32 position error (~1e-6 cells) cannot change the cell of either endpoint, so J and
+    every field are comparable everywhere.  Dropping particles changes J and hence the orbits of
+    the others slightly, so the oracle is run again until no further particle is near a face."""
+    for _ in range(max_rounds):
+        ref = oracle_start(wl, **oracle_kw)
+        bad = [set() for _ in wl.species]
+        for _ in range(nsteps):
+            ref.step(1)
+            for s in range(len(wl.species)):
+                x0, x1, ids = ref.last_moves(s)
+                if ids.size:
+                    near = _near_face(x0, delta) | _near_face(x1, delta)
+                    bad[s].update(ids[near].tolist())
+        ref.close()
+        if not any(bad):
+            return wl
+        for s, sp in enumerate(wl.species):
+            if bad[s]:
+                keep = ~np.isin(sp.ids, np.fromiter(bad[s], dtype=np.int64))
+                sp.x4, sp.usp, sp.ids = sp.x4[:, keep], sp.usp[:, keep], sp.ids[keep]
+    raise AssertionError("no well-conditioned subset found")
+
+
 def dilate(mask, r):
     out = mask.copy()
     for ax in range(3):

@@ -6,8 +6,7 @@ four species, against the oracle over three whole cycles, in FP64 and FP32-mixed
 import numpy as np
 import pytest
 
-from parity_util import TOL, dilate, gpu_from_oracle, oracle_start, particle_errors, rel_l2_masked
-from test_gpu_parity import check_j
+from parity_util import TOL, face_ambiguity_mask, gpu_from_oracle, oracle_start, particle_errors, rel_l2, well_conditioned
 from paper_0904_0232_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -22,32 +21,44 @@ def _cuda():
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
 def test_paper_setup_full_steps(prec):
+    """All particles, J nodes and field values compared after every step; the workload drops the
+    ~0.3 % of particles whose zig-zag split the oracle decides within 1e-4 of a face (FP32 could
+    decide it the other way).  Bound after step k: (k + 1) x the per-step tolerance."""
     wl = synth.kerr_jet_disk()
     assert 0.95e6 < wl.n_particles < 1.0e6
+    n0 = wl.n_particles
+    wl = well_conditioned(wl, 3)
+    assert sum(sp.ids.size for sp in wl.species) >= 0.99 * n0
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, prec)
     tol = TOL[prec]
     ns = len(wl.species)
-    seen = np.zeros((wl.nz, wl.ny, wl.nx), dtype=bool)
+    rec = []
     for step in range(3):
         ref.step(1)
         sim.step(1)
+        grow = step + 1
+        if prec == "fp32_mixed":
+            assert not face_ambiguity_mask(ref, (wl.nz, wl.ny, wl.nx), ns).any()
         for s in range(ns):
-            ex, e4, eu = particle_errors(sim, ref, s, mask=dilate(seen, 1))
-            assert max(ex, eu) <= tol["particles"] * 4 ** step, (step, s, ex, eu)
+            ex, e4, eu = particle_errors(sim, ref, s)
+            rec.append((step, s, ex, eu))
+            assert max(ex, eu) <= tol["particles"] * grow, (step, s, ex, eu)
         d, b, J = sim.get_fields()
         dr, br, Jr = ref.get_fields()
         # FP32 J: the sub-area weights carry the rounding of the positions (up to 126 cells on the
         # z axis here, FP32 spacing 7.6e-6, twice that of the 64-cell grids the J bound was set
         # on), and the disk's small coherent moves (~0.02 cells a step) cancel little of it
         jf = 4.0 if prec == "fp32_mixed" else 1.0
-        seen = dilate(seen, 3) | check_j(J, Jr, ref, ns, prec, jf * 4 ** step)
-        assert rel_l2_masked(b, br, seen) <= tol["fields"] * 4 ** step
         # d against the norm of the whole field tensor: the E step adds to the small d the curl of
         # h, which carries the FP32 rounding of the B_z = 30 background (|b| >> |d| here)
-        keep = ~np.broadcast_to(seen, d.shape)
-        scale = max(np.linalg.norm(dr[keep]), np.linalg.norm(br[keep]))
-        assert np.linalg.norm((d - dr)[keep]) <= max(tol["fields"], jf * tol["J"]) * 4 ** step * scale
+        scale = max(np.linalg.norm(dr), np.linalg.norm(br))
+        errs = rel_l2(J, Jr), rel_l2(b, br), np.linalg.norm(d - dr) / scale
+        rec.append((step, "J,b,d", *errs))
+        assert errs[0] <= tol["J"] * jf * grow, (step, errs)
+        assert errs[1] <= tol["fields"] * grow, (step, errs)
+        assert errs[2] <= max(tol["fields"], jf * tol["J"]) * grow, (step, errs)
+    print("paper_setup", prec, rec)
     st, sr = sim.stats(), ref.stats()
     assert st["removed_horizon"] == sr["removed_horizon"] and st["removed_outer"] == sr["removed_outer"]
     if prec == "fp32_mixed":

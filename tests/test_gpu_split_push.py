@@ -12,7 +12,7 @@ per warp in one kernel (split = 0) or in separate near-hole and far-field kernel
 import numpy as np
 import pytest
 
-from parity_util import TOL, gpu_from_oracle, oracle_start, particle_errors, rel_l2, small_kerr
+from parity_util import TOL, check_j, gpu_from_oracle, oracle_start, particle_errors, rel_l2, small_kerr
 from paper_0904_0232_gb300.grpic import (GRPIC_SINGLE_PUSH_KERNEL, GRPIC_STAGE_PUSH_DEPOSIT, GRPIC_STAGE_SORT,
                                          GRPIC_STAGE_ZERO_J,
                                          GrpicError, grpic_check_conversions, grpic_check_newton64)
@@ -72,7 +72,7 @@ def test_split_push_against_oracle(mode):
         ex, e4, eu = particle_errors(sim, ref, s)
         assert max(ex, e4, eu) <= tol["particles"], (s, ex, e4, eu)
     _, _, Jr = ref.get_fields()
-    assert rel_l2(J, Jr) <= tol["J"] * 10  # split ambiguity at faces is the only source above 1e-5
+    check_j(J, Jr, ref, 2, "fp32_mixed")  # 1e-5 off the nodes of splits decided within rounding of a face
     assert sim.stats()["fp64_evals"] > 0
 
 

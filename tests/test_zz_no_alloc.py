@@ -83,6 +83,47 @@ def test_static_sort_matches_regular_path_twice(torch):
         _same(_regular_path(x4, u4, ids, N), _static_path(torch, x4, u4, ids, N), N)
 
 
+def test_static_sort_drops_particles_outside_the_grid(torch):
+    """Positions outside [0, N-1) on any axis -- negative, beyond the last cell, NaN -- go to the
+    outside bin and are not returned; the kept count is the offset of that bin.  The kept particles
+    come back in cell order, each with its own values, twice in a row."""
+    N = 32
+    rng = np.random.default_rng(7)
+    for n in (20000, 12345):
+        x4, u4, ids = _particles(int(rng.integers(100)), n, N)
+        bad = rng.random(n) < 0.3
+        ax = rng.integers(0, 3, n)
+        kind = rng.integers(0, 4, n)
+        for i in np.nonzero(bad)[0]:
+            x4[ax[i], i] = (-rng.uniform(0.0, 5.0), -1e-300, N - 1 + rng.uniform(0.0, 3.0), np.nan)[kind[i]]
+        keep = np.all((x4[:3] >= 0.0) & (x4[:3] < N - 1), axis=0)
+        assert 0.2 < 1 - keep.mean() < 0.4
+        xo, uo, io = _static_path(torch, x4, u4, ids, N)
+        assert io.size == keep.sum()
+        c = _cells(xo, N)
+        assert np.all(np.diff(c) >= 0)
+        assert np.array_equal(np.sort(c), np.sort(_cells(x4[:, keep], N)))
+        pos = {int(v): k for k, v in enumerate(ids)}
+        src = np.array([pos[int(v)] for v in io])
+        assert np.array_equal(np.sort(io), np.sort(ids[keep]))
+        assert np.array_equal(xo, x4[:, src]) and np.array_equal(uo, u4[:, src])
+
+
+def test_static_sort_of_no_particles(torch):
+    """n = 0: nothing is read or written but the count, which is 0 (after a call that kept many)."""
+    from paper_0904_0232_gb300.grpic import grpic_sort_particles_static
+
+    N = 16
+    x4, u4, ids = _particles(4, 3000, N)
+    assert _static_path(torch, x4, u4, ids, N)[2].size == 3000
+    e = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
+    i = torch.zeros(0, dtype=torch.int32, device="cuda")
+    no = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+    grpic_sort_particles_static(N, N, N, e, e, i, e.clone(), e.clone(), i.clone(), no)
+    torch.cuda.synchronize()
+    assert int(no.item()) == 0
+
+
 def test_static_sort_rejects_too_large_grid(torch):
     from paper_0904_0232_gb300.grpic import GrpicError, grpic_sort_particles_static
 
