@@ -73,11 +73,12 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=10)
     p.add_argument("--fp32-compare-steps", type=int, default=200,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
-    p.add_argument("--workload", choices=["kerr128", "batch", "disk384", "jet"], default="kerr128",
+    p.add_argument("--workload", choices=["kerr128", "batch", "disk384", "jet", "fields"], default="kerr128",
                    help="kerr128: the single-instance Kerr electron-ion workload; batch: many small "
                         "instances advanced by the batched engine; disk384: the 384^3 disk/corona plasma "
                         "(~1e9 particles, generated on the device); jet: the parameters of the paper's "
-                        "application set-up (64x64x128, c = 0.05, ~0.97 million particles)")
+                        "application set-up (64x64x128, c = 0.05, ~0.97 million particles); fields: the field "
+                        "stages alone (B half-steps, E step) on an n^3 Kerr grid without particles")
     p.add_argument("--single-kernel-steps", type=int, default=200,
                    help="steps of the comparison run with the single mixed push kernel; 0 skips it")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
@@ -630,6 +631,58 @@ def run_jet(args, dist):
             "stats": {k: st[k] for k in ("removed_horizon", "removed_outer", "gamma_fallbacks", "fp64_evals")}}
 
 
+# Algorithmic bytes per cell of the field stages in FP32 (words of 4 B; J is FP64): first B half-step
+# reads b, d and writes b^n (9 words); the second, time-centred, also reads b^{n-1/2} (12 words); the
+# E step reads b, d, J and writes d (9 words + 24 B); J = 0 writes 24 B.
+FIELD_BYTES = {"b_half": 36, "b_half2": 48, "e_step": 60, "zero_j": 24}
+
+
+def run_fields(args, dist):
+    """The field stages alone: Kerr a = 0.9 m, m = 4 cells (m = 8, a = 0.95 m at n >= 256, the
+    384^3 disk geometry), n^3 grid, uniform B_z = 0.1, no particles, FP32-mixed; device time per
+    stage from CUDA events over K whole cycles, against the stage's algorithmic bytes."""
+    import torch
+
+    from paper_0904_0232_gb300.build import build
+    from paper_0904_0232_gb300.grpic import Simulation
+
+    torch.cuda.set_device(dist.local)
+    build()
+    n = args.grid
+    m, a = (8.0, 0.95 * 8.0) if n >= 256 else (4.0, 0.9 * 4.0)
+    sim = Simulation(n, n, n, m, a, 1.0, 0.4, precision="fp32_mixed")
+    sim.set_uniform_field(B=(0.0, 0.0, 0.1))
+    sim.set_profiling(True)
+    sim.step(args.warmup)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    ms, _, prof, launches = timed_steps(sim, args.steps, dist)
+    clk = clocks.stop()
+    sim.close()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    cells = float(n) ** 3
+    stages = {}
+    for k, nbytes in FIELD_BYTES.items():
+        t = prof[k][0] / max(1, args.steps) * 1e-3
+        gbs = nbytes * cells / t / 1e9 if t > 0 else None
+        stages[k] = {"ms": round(t * 1e3, 4), "algorithmic_bytes_per_cell": nbytes,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / hbm if gbs else None}
+    return {"metric": "field stage time (B half-steps, E step)", "value": dist.max(ms) / args.steps, "unit": "ms/step",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dist.max(ms) / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (uniform field, no particles)",
+            "config": {"workload": f"fields_{n}: Kerr a={a / m:g}m, m={m:g} cells, {n}^3, B_z=0.1, dt=0.4, no particles",
+                       "hbm_peak_gbs": hbm, "l2": "field planes larger than L2" if 15 * 4 * cells > 129e6
+                       else "field planes fit in L2 (a small-grid measurement)"},
+            "gpu_launches": int(launches), "stages": stages, "clocks": clk}
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -641,6 +694,8 @@ def main():
         line = run_disk(args, dist)
     elif args.workload == "jet":
         line = run_jet(args, dist)
+    elif args.workload == "fields":
+        line = run_fields(args, dist)
     else:
         line = run_gpu(args, dist)
     if dist.rank == 0 and line is not None:

@@ -54,18 +54,77 @@ __host__ __device__ inline T grid_four_pi_c(const Grid& g) {
   if constexpr (sizeof(T) == sizeof(float)) return g.four_pi_c_f; else return g.four_pi_c;
 }
 
-// Field views.  Metric cache: for each of the 6 field locations of a cell, (f, k0, k1, k2)
-// as 4 planes -> mc[(loc*4 + q)*ncell + cell].  mask bit l of a cell: location l is advanced.
+// The field state a kernel reads: the current d and b and the current density J (FP64).
 template <typename T>
 struct Fields {
-  T* d[3];
-  T* b[3];
-  T* s[3];       // scratch: covariant e (B step) or contravariant h (E step)
-  T* bp[3];      // b at the previous half level (time-centred B update)
-  T* dp[3];      // midpoint predictor of d (time-centred E update)
+  T* d[3];  // contravariant (F^x4, F^y4, F^z4) on edges
+  T* b[3];  // covariant (F_yz, F_zx, F_xy) on faces
   double* J[3];
-  const T* mc;
-  const uint8_t* mask;
+};
+
+// Both buffers of the field ping-pong pairs and the per-cell location flags (bit l: location l
+// advanced; bit 8 + l: location l excised).  The field updates write the other buffer.
+template <typename T>
+struct FieldStore {
+  T* d[2][3];
+  T* b[2][3];
+  double* J[3];
+  const uint16_t* loc;
+};
+
+// Metric constants of the field kernels in the field type, converted once on the host (this GPU
+// converts FP64 to FP32 on its reduced-rate FP64 pipe): centre, spin, 2m, dx^4 and 4 pi / c.
+template <typename T>
+struct FieldConsts {
+  T xc, yc, zc, a, a2, two_m, dx4, four_pi_c;
+  bool massive;
+};
+template <typename T>
+__host__ __device__ inline FieldConsts<T> field_consts(const Grid& g) {
+  FieldConsts<T> K;
+  K.xc = (T)g.xc;
+  K.yc = (T)g.yc;
+  K.zc = (T)g.zc;
+  K.a = (T)g.a;
+  K.a2 = K.a * K.a;
+  K.two_m = (T)(2.0 * g.m);
+  K.dx4 = grid_dx4<T>(g);
+  K.four_pi_c = grid_four_pi_c<T>(g);
+  K.massive = g.m > 0.0;
+  return K;
+}
+
+// B half-step: b_out = b_base - coef curl e(b_src, d) at advanced face locations, b_base copied
+// elsewhere (not written when inplace: b_out == b_base).
+template <typename T>
+struct BStepArgs {
+  const T* src[3];
+  const T* base[3];
+  T* out[3];
+  const T* d[3];
+  const uint16_t* loc;
+  FieldConsts<T> K;
+  T coef;
+  bool inplace;
+};
+
+// E step: d_out = d + dx4 (4 pi/c J - div h(b, d*)) at advanced edge locations, d copied
+// elsewhere; d* = d + (dx4/2)(4 pi/c J - div h(b, d)) with pred, else d.
+template <typename T>
+struct EStepArgs {
+  const T* b[3];
+  const T* d[3];
+  T* out[3];
+  const double* J[3];
+  const uint16_t* loc;
+  FieldConsts<T> K;
+  bool pred;
+};
+
+// Patches of a grid for the field launches: ntx x nty patches of (x, y) columns, z in chunks.
+struct TileGrid {
+  int ntx, nty, ntz, zchunk;
+  __host__ __device__ long long count() const { return (long long)ntx * nty * ntz; }
 };
 
 template <typename T>
@@ -83,17 +142,14 @@ __host__ __device__ inline long long cell_index(const Grid& g, int i, int j, int
 }
 
 // ---- launchers (defined in fields.cu, push.cu, sort.cu) --------------------------------
+void launch_location_flags(const Grid& g, uint16_t* loc, cudaStream_t st);
+// B half-steps (Eq. 10) and the E step (Eq. 12); sms sizes the z chunks of the launch.
 template <typename T>
-void launch_metric_cache(const Grid& g, T* mc, uint8_t* mask, cudaStream_t st);
-// B half-steps.  which = 0: first half (b^{n-1/2} -> b^n); which = 1: second half
-// (b^n -> b^{n+1/2}).  literal = true: each half is b -= (dx4/2) curl e(b, d) in place;
-// literal = false (time-centred): the first half saves b^{n-1/2}, the second computes
-// b^{n+1/2} = b^{n-1/2} - dx4 curl e(b^n, d^n).
+void launch_b_step(const Grid& g, const BStepArgs<T>& A, int sms, cudaStream_t st);
 template <typename T>
-void launch_b_half(const Grid& g, const Fields<T>& F, int which, bool literal, cudaStream_t st);
-// E step d^n -> d^{n+1}; time-centred unless literal (midpoint predictor for d in h(b, d)).
-template <typename T>
-void launch_e_step(const Grid& g, const Fields<T>& F, bool literal, cudaStream_t st);
+void launch_e_step(const Grid& g, const EStepArgs<T>& A, int sms, cudaStream_t st);
+// Patch tables of one instance for the batched field launches.
+void batch_field_tiles(const Grid& g, bool fp32, TileGrid* btiles, TileGrid* etiles);
 template <typename T>
 void launch_uniform_field(const Grid& g, const Fields<T>& F, const double E[3], const double B[3], cudaStream_t st);
 template <typename T>
@@ -260,7 +316,11 @@ struct SpeciesDesc {
 template <typename T>
 struct InstDesc {
   Grid g;
-  Fields<T> F;
+  FieldConsts<float> K32;  // field-kernel constants in both types (the batch is FP32 or FP64)
+  FieldConsts<double> K64;
+  FieldStore<T> FS;  // b[0]: b at the start of a step (b^{n-1/2}), b[1]: b^n
+  int* dcur;         // device: which d buffer holds the current d
+  TileGrid btiles, etiles;
   DevStatus* st;
   SpeciesDesc<T> sp[4];
 };
@@ -268,10 +328,10 @@ struct InstDesc {
 template <typename T>
 struct BatchTables {
   const InstDesc<T>* desc;
-  const BlockEntry* conv;  // cells of [1, n-2]^3, 128 per block
-  int nconv;
-  const BlockEntry* upd;   // cells of [2, n-3]^3, 256 per block
-  int nupd;
+  const BlockEntry* btile;  // B-step patches of every instance
+  int nbtile;
+  const BlockEntry* etile;  // E-step patches
+  int netile;
   const BlockEntry* all;   // all cells, 256 per block
   int nall;
   const BlockEntry* part;  // particles of (instance, species), 128 per block
@@ -284,6 +344,7 @@ struct BatchTables {
   int npairs;
   int* pair_base;          // exclusive prefix at each pair's first bin (per step)
   int persist_blocks;      // grid size of the persistent launches
+  int persist_field_blocks;  // grid size of the persistent field launches (512-thread blocks)
 };
 
 template <typename T>
@@ -292,6 +353,9 @@ template <typename T>
 void launch_batch_e_step(const BatchTables<T>& bt, bool literal, cudaStream_t st);
 template <typename T>
 void launch_batch_zero_j(const BatchTables<T>& bt, cudaStream_t st);
+// flip every instance's d parity (end of a batched step)
+template <typename T>
+void launch_batch_flip_d(const BatchTables<T>& bt, int ninst, cudaStream_t st);
 template <typename T>
 void launch_batch_push(const BatchTables<T>& bt, int quad_order, cudaStream_t st);
 template <typename T>

@@ -48,10 +48,12 @@ struct grpic_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
   grpic_tuning tune{4, 4, 1, 1, 0, 0, 1};
-  void* fields = nullptr;  // 15 planes of T: d[3], b[3], scratch[3], b previous[3], d predictor[3]
+  void* fields = nullptr;  // 12 planes of T: d buffers 0 and 1 (3 planes each), b buffers 0 and 1
   double* J = nullptr;     // 3 planes
-  void* mc = nullptr;      // 24 planes of T
-  uint8_t* mask = nullptr;
+  uint16_t* loc = nullptr;  // per-cell location flags
+  // field ping-pong state: buffer of the current d and b; bprev: buffer holding b^{n-1/2} after the
+  // first B half-step (time-centred second half-step)
+  int dcur = 0, bcur = 0, bprev = 0;
   DevStatus* st = nullptr;
   DevStatus* st_host = nullptr;  // pinned
   SortScratch sort{};
@@ -109,19 +111,19 @@ grpic_status cuda_check(grpic_ctx* c, cudaError_t e, const char* where) {
 size_t particle_bytes(const grpic_ctx* c) { return 8 * c->tsize + 2 * sizeof(uint32_t); }
 
 template <typename T>
+T* field_plane(grpic_ctx* c, bool is_b, int buf, int q) {
+  return static_cast<T*>(c->fields) + (size_t)((is_b ? 6 : 0) + 3 * buf + q) * c->g.ncell;
+}
+
+// The current field state (what the push, the diagnostics and get/set_fields see).
+template <typename T>
 Fields<T> fields_view(grpic_ctx* c) {
   Fields<T> F;
-  T* base = static_cast<T*>(c->fields);
   for (int q = 0; q < 3; ++q) {
-    F.d[q] = base + (size_t)q * c->g.ncell;
-    F.b[q] = base + (size_t)(3 + q) * c->g.ncell;
-    F.s[q] = base + (size_t)(6 + q) * c->g.ncell;
-    F.bp[q] = base + (size_t)(9 + q) * c->g.ncell;
-    F.dp[q] = base + (size_t)(12 + q) * c->g.ncell;
+    F.d[q] = field_plane<T>(c, false, c->dcur, q);
+    F.b[q] = field_plane<T>(c, true, c->bcur, q);
     F.J[q] = c->J + (size_t)q * c->g.ncell;
   }
-  F.mc = static_cast<const T*>(c->mc);
-  F.mask = c->mask;
   return F;
 }
 
@@ -246,10 +248,31 @@ void enqueue_stage(grpic_ctx* c, int stage) {
   Fields<T> F = fields_view<T>(c);
   switch (stage) {
     case GRPIC_STAGE_B_HALF:
-    case GRPIC_STAGE_B_HALF2:
-      launch_b_half<T>(c->g, F, stage == GRPIC_STAGE_B_HALF ? 0 : 1, literal_fields(c), c->stream);
-      c->launches += 2;
+    case GRPIC_STAGE_B_HALF2: {
+      // first half: b_cur -> the other buffer (b_cur kept as b^{n-1/2}); second half, time-centred:
+      // b^{n+1/2} = b^{n-1/2} - dx4 curl e(b^n, d) over the saved buffer; literal: b -= dx4/2 curl e
+      // into the other buffer
+      const bool second = stage == GRPIC_STAGE_B_HALF2;
+      const bool centred = second && !literal_fields(c);
+      const int out = centred ? c->bprev : 1 - c->bcur;
+      BStepArgs<T> A;
+      for (int q = 0; q < 3; ++q) {
+        A.src[q] = field_plane<T>(c, true, c->bcur, q);
+        A.base[q] = field_plane<T>(c, true, centred ? c->bprev : c->bcur, q);
+        A.out[q] = field_plane<T>(c, true, out, q);
+        A.d[q] = F.d[q];
+      }
+      A.loc = c->loc;
+      A.K = field_consts<T>(c->g);
+      const T dx4 = grid_dx4<T>(c->g);
+      A.coef = centred ? dx4 : dx4 * T(0.5);
+      A.inplace = centred;
+      launch_b_step<T>(c->g, A, c->sms, c->stream);
+      c->launches += 1;
+      if (!second) c->bprev = c->bcur;
+      c->bcur = out;
       break;
+    }
     case GRPIC_STAGE_ZERO_J:
       cudaMemsetAsync(c->J, 0, sizeof(double) * 3 * (size_t)c->g.ncell, c->stream);
       break;
@@ -271,10 +294,22 @@ void enqueue_stage(grpic_ctx* c, int stage) {
       }
       c->pushes += 1;
       break;
-    case GRPIC_STAGE_E:
-      launch_e_step<T>(c->g, F, literal_fields(c), c->stream);
-      c->launches += literal_fields(c) ? 2 : 4;
+    case GRPIC_STAGE_E: {
+      EStepArgs<T> A;
+      for (int q = 0; q < 3; ++q) {
+        A.b[q] = F.b[q];
+        A.d[q] = F.d[q];
+        A.out[q] = field_plane<T>(c, false, 1 - c->dcur, q);
+        A.J[q] = F.J[q];
+      }
+      A.loc = c->loc;
+      A.K = field_consts<T>(c->g);
+      A.pred = !literal_fields(c);
+      launch_e_step<T>(c->g, A, c->sms, c->stream);
+      c->launches += 1;
+      c->dcur = 1 - c->dcur;
       break;
+    }
     case GRPIC_STAGE_SORT:
       for (int s = 0; s < kMaxSpecies; ++s) {
         SpeciesStore& S = c->sp[s];
@@ -464,17 +499,16 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.dx4_f = (float)g.dx4;
   g.four_pi_c_f = (float)g.four_pi_c;
 
-  c->fields = dev_alloc(c, 15 * (size_t)ncell * c->tsize);
+  c->fields = dev_alloc(c, 12 * (size_t)ncell * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));
-  c->mc = dev_alloc(c, 24 * (size_t)ncell * c->tsize);
-  c->mask = static_cast<uint8_t*>(dev_alloc(c, (size_t)ncell));
+  c->loc = static_cast<uint16_t*>(dev_alloc(c, sizeof(uint16_t) * (size_t)ncell));
   c->st = static_cast<DevStatus*>(dev_alloc(c, sizeof(DevStatus)));
   const long long nbins = ncell + 1;
   c->sort.nblocks = scan_tiles(nbins);
   c->sort.counts = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
   c->sort.offsets = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
   c->sort.blocks = static_cast<int*>(dev_alloc(c, sizeof(int) * (c->sort.nblocks + 1)));
-  bool ok = c->fields && c->J && c->mc && c->mask && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
+  bool ok = c->fields && c->J && c->loc && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
   for (int s = 0; s < kMaxSpecies && ok; ++s) {
     c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
     c->sp[s].near_n = static_cast<int*>(dev_alloc(c, 2 * sizeof(int)));
@@ -496,14 +530,11 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
     grpic_destroy(c);
     return GRPIC_ERR_OOM;
   }
-  cudaMemsetAsync(c->fields, 0, 15 * (size_t)ncell * c->tsize, c->stream);
+  cudaMemsetAsync(c->fields, 0, 12 * (size_t)ncell * c->tsize, c->stream);
   cudaMemsetAsync(c->J, 0, 3 * (size_t)ncell * sizeof(double), c->stream);
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
   for (int s = 0; s < kMaxSpecies; ++s) cudaMemsetAsync(c->sp[s].n_dev, 0, sizeof(int), c->stream);
-  if (c->mixed)
-    launch_metric_cache<float>(g, static_cast<float*>(c->mc), c->mask, c->stream);
-  else
-    launch_metric_cache<double>(g, static_cast<double*>(c->mc), c->mask, c->stream);
+  launch_location_flags(g, c->loc, c->stream);
   grpic_status s = cuda_check(c, cudaGetLastError(), "create");
   if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
   if (s != GRPIC_OK) {
@@ -519,8 +550,7 @@ grpic_status grpic_destroy(grpic_ctx* c) {
   cudaStreamSynchronize(c->stream);
   dev_free(c, c->fields);
   dev_free(c, c->J);
-  dev_free(c, c->mc);
-  dev_free(c, c->mask);
+  dev_free(c, c->loc);
   dev_free(c, c->st);
   dev_free(c, c->sort.counts);
   dev_free(c, c->sort.offsets);
@@ -578,14 +608,17 @@ grpic_status grpic_set_fields(grpic_ctx* c, const double* d3, const double* b3, 
   grpic_status s = stage_in(c, d3, sizeof(double) * n3, mem, &dd, &td);
   if (s == GRPIC_OK) s = stage_in(c, b3, sizeof(double) * n3, mem, &bd, &tb);
   if (s != GRPIC_OK) return s;
+  // the current buffers (each set of three planes is contiguous)
   if (c->mixed) {
-    float* base = static_cast<float*>(c->fields);
-    launch_convert_in<float>(base, static_cast<const double*>(dd), n3, c->stream);
-    launch_convert_in<float>(base + n3, static_cast<const double*>(bd), n3, c->stream);
+    launch_convert_in<float>(field_plane<float>(c, false, c->dcur, 0), static_cast<const double*>(dd), n3,
+                             c->stream);
+    launch_convert_in<float>(field_plane<float>(c, true, c->bcur, 0), static_cast<const double*>(bd), n3,
+                             c->stream);
   } else {
-    double* base = static_cast<double*>(c->fields);
-    cudaMemcpyAsync(base, dd, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(base + n3, bd, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(field_plane<double>(c, false, c->dcur, 0), dd, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                    c->stream);
+    cudaMemcpyAsync(field_plane<double>(c, true, c->bcur, 0), bd, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                    c->stream);
   }
   s = cuda_check(c, cudaGetLastError(), "set_fields");
   release_tmp(c, td);
@@ -716,11 +749,12 @@ grpic_status grpic_get_fields(grpic_ctx* c, double* d3, double* b3, double* J3, 
   double* outs[2] = {d3, b3};
   for (int w = 0; w < 2; ++w) {
     if (!outs[w]) continue;
+    const int buf = w ? c->bcur : c->dcur;
     if (c->mixed) {
-      launch_convert_out<float>(tmp, static_cast<float*>(c->fields) + w * n3, n3, c->stream);
+      launch_convert_out<float>(tmp, field_plane<float>(c, w == 1, buf, 0), n3, c->stream);
       cudaMemcpyAsync(outs[w], tmp, bytes, kind, c->stream);
     } else {
-      cudaMemcpyAsync(outs[w], static_cast<double*>(c->fields) + w * n3, bytes, kind, c->stream);
+      cudaMemcpyAsync(outs[w], field_plane<double>(c, w == 1, buf, 0), bytes, kind, c->stream);
     }
     cudaStreamSynchronize(c->stream);
   }
@@ -928,13 +962,15 @@ struct grpic_batch {
   int quad = 2;
   std::vector<void*> allocs;
   void* desc = nullptr;
-  BlockEntry *conv = nullptr, *upd = nullptr, *all = nullptr, *part = nullptr;
-  int nconv = 0, nupd = 0, nall = 0, npart = 0;
+  BlockEntry *btile = nullptr, *etile = nullptr, *all = nullptr, *part = nullptr;
+  int nbtile = 0, netile = 0, nall = 0, npart = 0;
+  int* dcur = nullptr;  // device d-buffer parity per instance
   int *counts = nullptr, *offsets = nullptr, *tiles = nullptr, *pairs = nullptr, *pair_base = nullptr;
   int* cur = nullptr;  // device ping-pong index per (instance, species)
   long long nbins = 0;
   int npairs = 0;
   int persist_blocks = 0;
+  int persist_field_blocks = 0;
   int sms = 1;
   std::vector<long long> pair_n;  // work upper bound of each pair when the batch was built
   cudaGraphExec_t graph = nullptr;
@@ -968,10 +1004,10 @@ template <typename T>
 BatchTables<T> batch_tables(grpic_batch* b) {
   BatchTables<T> t;
   t.desc = static_cast<const InstDesc<T>*>(b->desc);
-  t.conv = b->conv;
-  t.nconv = b->nconv;
-  t.upd = b->upd;
-  t.nupd = b->nupd;
+  t.btile = b->btile;
+  t.nbtile = b->nbtile;
+  t.etile = b->etile;
+  t.netile = b->netile;
   t.all = b->all;
   t.nall = b->nall;
   t.part = b->part;
@@ -984,6 +1020,7 @@ BatchTables<T> batch_tables(grpic_batch* b) {
   t.npairs = b->npairs;
   t.pair_base = b->pair_base;
   t.persist_blocks = b->persist_blocks;
+  t.persist_field_blocks = b->persist_field_blocks;
   return t;
 }
 
@@ -996,23 +1033,38 @@ template <typename T>
 grpic_status batch_build(grpic_batch* b) {
   const int n = (int)b->ctxs.size();
   std::vector<InstDesc<T>> desc(n);
-  std::vector<BlockEntry> conv, upd, all, part;
-  std::vector<int> pairs, cur_init;
+  std::vector<BlockEntry> btile, etile, all, part;
+  std::vector<int> pairs, cur_init, dcur_init(n, 0);
   std::vector<long long> bin_base;
   long long nbins = 0;
   // device ping-pong indices: one int per (instance, species)
   b->cur = static_cast<int*>(batch_alloc(b, sizeof(int) * 4 * n));
   if (!b->cur) return GRPIC_ERR_OOM;
+  b->dcur = static_cast<int*>(batch_alloc(b, sizeof(int) * n));
+  if (!b->dcur) return GRPIC_ERR_OOM;
   cur_init.assign(4 * n, 0);
   for (int i = 0; i < n; ++i) {
     grpic_ctx* c = b->ctxs[i];
     InstDesc<T>& D = desc[i];
     D.g = c->g;
-    D.F = fields_view<T>(c);
+    D.K32 = field_consts<float>(c->g);
+    D.K64 = field_consts<double>(c->g);
+    // b[0]: the context's current b (b^{n-1/2} at a step boundary), b[1]: the other buffer
+    for (int q = 0; q < 3; ++q) {
+      D.FS.d[0][q] = field_plane<T>(c, false, 0, q);
+      D.FS.d[1][q] = field_plane<T>(c, false, 1, q);
+      D.FS.b[0][q] = field_plane<T>(c, true, c->bcur, q);
+      D.FS.b[1][q] = field_plane<T>(c, true, 1 - c->bcur, q);
+      D.FS.J[q] = c->J + (size_t)q * c->g.ncell;
+    }
+    D.FS.loc = c->loc;
+    D.dcur = b->dcur + i;
+    dcur_init[i] = c->dcur;
     D.st = c->st;
     const Grid& g = c->g;
-    append_blocks(conv, i, (long long)(g.nx - 2) * (g.ny - 2) * (g.nz - 2), 128);
-    append_blocks(upd, i, (long long)(g.nx - 4) * (g.ny - 4) * (g.nz - 4), 256);
+    batch_field_tiles(g, sizeof(T) == sizeof(float), &D.btiles, &D.etiles);
+    for (long long q = 0; q < D.btiles.count(); ++q) btile.push_back(BlockEntry{i, (int)q});
+    for (long long q = 0; q < D.etiles.count(); ++q) etile.push_back(BlockEntry{i, (int)q});
     append_blocks(all, i, g.ncell, 256);
     for (int s = 0; s < kMaxSpecies; ++s) {
       SpeciesStore& S = c->sp[s];
@@ -1038,13 +1090,13 @@ grpic_status batch_build(grpic_batch* b) {
   }
   b->npairs = (int)pairs.size();
   b->nbins = std::max<long long>(nbins, 1);
-  b->nconv = (int)conv.size();
-  b->nupd = (int)upd.size();
+  b->nbtile = (int)btile.size();
+  b->netile = (int)etile.size();
   b->nall = (int)all.size();
   b->npart = (int)part.size();
   b->desc = batch_alloc(b, sizeof(InstDesc<T>) * n);
-  b->conv = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, conv.size())));
-  b->upd = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, upd.size())));
+  b->btile = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, btile.size())));
+  b->etile = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, etile.size())));
   b->all = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, all.size())));
   b->part = static_cast<BlockEntry*>(batch_alloc(b, sizeof(BlockEntry) * std::max<size_t>(1, part.size())));
   b->counts = static_cast<int*>(batch_alloc(b, sizeof(int) * b->nbins));
@@ -1053,15 +1105,16 @@ grpic_status batch_build(grpic_batch* b) {
   b->pairs = static_cast<int*>(batch_alloc(b, sizeof(int) * std::max(1, b->npairs)));
   // pair_base: npairs per-step bases, then pair_of_inst for every instance * 4 + species
   b->pair_base = static_cast<int*>(batch_alloc(b, sizeof(int) * (b->npairs + 4 * n)));
-  if (!b->desc || !b->conv || !b->upd || !b->all || !b->part || !b->counts || !b->offsets || !b->tiles ||
+  if (!b->desc || !b->btile || !b->etile || !b->all || !b->part || !b->counts || !b->offsets || !b->tiles ||
       !b->pairs || !b->pair_base)
     return GRPIC_ERR_OOM;
   std::vector<int> pair_of_inst(4 * n, 0);
   for (int p = 0; p < b->npairs; ++p) pair_of_inst[pairs[p]] = p;
   cudaStream_t st = b->stream;
   cudaMemcpyAsync(b->desc, desc.data(), sizeof(InstDesc<T>) * n, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b->conv, conv.data(), sizeof(BlockEntry) * conv.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b->upd, upd.data(), sizeof(BlockEntry) * upd.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->btile, btile.data(), sizeof(BlockEntry) * btile.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->etile, etile.data(), sizeof(BlockEntry) * etile.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b->dcur, dcur_init.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b->all, all.data(), sizeof(BlockEntry) * all.size(), cudaMemcpyHostToDevice, st);
   if (!part.empty())
     cudaMemcpyAsync(b->part, part.data(), sizeof(BlockEntry) * part.size(), cudaMemcpyHostToDevice, st);
@@ -1081,6 +1134,7 @@ void batch_enqueue_step(grpic_batch* b) {
   launch_batch_push<T>(t, b->quad, b->stream);
   launch_batch_b_half<T>(t, 1, b->literal, b->stream);
   launch_batch_e_step<T>(t, b->literal, b->stream);
+  launch_batch_flip_d<T>(t, (int)b->ctxs.size(), b->stream);
   launch_batch_sort<T>(t, b->stream);
 }
 
@@ -1109,6 +1163,7 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->sms = std::max(1, sms);
   b->persist_blocks = b->sms * 8;
+  b->persist_field_blocks = b->sms * 2;
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
     grpic_batch_destroy(b);
@@ -1120,9 +1175,8 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
     grpic_batch_destroy(b);
     return s;
   }
-  // kernels per step: B halves 2 x 2, zero J 1, push 1, E 2 or 4, sort 5 (+2 with particles; and 1 memset)
-  b->kernels_per_step =
-      4 + 1 + (b->npart > 0 ? 1 : 0) + (b->literal ? 2 : 4) + (b->npairs ? 5 + 2 * (b->npart > 0 ? 1 : 0) : 0);
+  // kernels per step: B halves 2, zero J 1, push 1, E 1, d parity 1, sort 5 (+2 with particles; and 1 memset)
+  b->kernels_per_step = 2 + 1 + (b->npart > 0 ? 1 : 0) + 1 + 1 + (b->npairs ? 5 + 2 * (b->npart > 0 ? 1 : 0) : 0);
   *out = b;
   return GRPIC_OK;
 }
@@ -1143,6 +1197,9 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
     cudaStreamWaitEvent(b->stream, b->ev, 0);
   }
   cudaMemcpyAsync(b->cur, cur.data(), sizeof(int) * cur.size(), cudaMemcpyHostToDevice, b->stream);
+  std::vector<int> dpar(b->ctxs.size(), 0);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) dpar[i] = b->ctxs[i]->dcur;
+  cudaMemcpyAsync(b->dcur, dpar.data(), sizeof(int) * dpar.size(), cudaMemcpyHostToDevice, b->stream);
   if (!b->graph) {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GRPIC_ERR_CUDA;
@@ -1158,12 +1215,15 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
   for (int k = 0; k < nsteps; ++k)
     if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
   cudaMemcpyAsync(cur.data(), b->cur, sizeof(int) * cur.size(), cudaMemcpyDeviceToHost, b->stream);
+  std::vector<int> dcur(b->ctxs.size(), 0);
+  cudaMemcpyAsync(dcur.data(), b->dcur, sizeof(int) * dcur.size(), cudaMemcpyDeviceToHost, b->stream);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     grpic_ctx* c = b->ctxs[i];
     c->steps += nsteps;
     c->pushes += nsteps;
     c->since_sort = 0;
+    c->dcur = dcur[i];
     c->launches += (long long)nsteps * b->kernels_per_step / (long long)b->ctxs.size();
     for (int s = 0; s < kMaxSpecies; ++s) {
       c->sp[s].cur = cur[4 * i + s];
@@ -1197,7 +1257,7 @@ grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm) {
 grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t* work_blocks) {
   if (!b) return GRPIC_ERR_INVALID;
   if (kernels_per_step) *kernels_per_step = b->kernels_per_step;
-  if (work_blocks) *work_blocks = (int64_t)b->nconv + b->nupd + b->nall + b->npart;
+  if (work_blocks) *work_blocks = (int64_t)b->nbtile + b->netile + b->nall + b->npart;
   return GRPIC_OK;
 }
 

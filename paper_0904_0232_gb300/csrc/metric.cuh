@@ -43,11 +43,12 @@ __device__ __forceinline__ double widen(float f) {
 
 // IEEE 754 binary64 -> binary32 with round-to-nearest-even, with integer operations for every
 // result in the normal binary32 range (the 29 dropped mantissa bits decide; a carry may step the
-// exponent, to infinity at the top, as the rounding rule says); other inputs (zero, subnormal
-// or out-of-range results, infinities, NaNs) take the hardware conversion.
+// exponent, to infinity at the top, as the rounding rule says) and for zeros; other inputs
+// (subnormal or out-of-range results, infinities, NaNs) take the hardware conversion.
 __device__ __forceinline__ float narrow(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
   const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e == 0u && (hi & 0xfffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);  // +-0
   if (e < 897u || e > 1150u) return __double2float_rn(d);
   unsigned r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1fffffffu;

@@ -84,11 +84,17 @@ __global__ void __launch_bounds__(128, 4) k_push_deposit_batch(const InstDesc<T>
   // launch constants were built on the host)
   const InstDesc<T>& D = desc[e.inst >> 2];
   copy_words(&sg, &D.g, sizeof(Grid));
-  copy_words(&sF, &D.F, sizeof(Fields<T>));
   copy_words(&sS, &D.sp[e.inst & 3], sizeof(SpeciesDesc<T>));
   if (threadIdx.x == 0) {
     sst = D.st;
     s_cur = *D.sp[e.inst & 3].cur;
+    // the push of a batched step runs after the first B half-step: b^n is in b buffer 1
+    const int dc = *D.dcur;
+    for (int q = 0; q < 3; ++q) {
+      sF.d[q] = D.FS.d[dc][q];
+      sF.b[q] = D.FS.b[1][q];
+      sF.J[q] = D.FS.J[q];
+    }
   }
   __syncthreads();
   const Particles<T>& sP = sS.buf[s_cur];

@@ -218,7 +218,8 @@ grpic_status grpic_request_bytes(const grpic_request* r, size_t* bytes) {
   const double cells = (double)r->cfg.nx * r->cfg.ny * r->cfg.nz;
   const double tsz = r->cfg.precision == GRPIC_FP32_MIXED ? 4.0 : 8.0;
   const double n = (double)interior_slots(*r);
-  const double fields = cells * (39.0 * tsz + 3.0 * 8.0 + 1.0 + 8.0);
+  // 12 field planes (two d and two b buffers), FP64 J, location flags, sort counts and offsets
+  const double fields = cells * (12.0 * tsz + 3.0 * 8.0 + 2.0 + 8.0);
   const double particles = n * r->nspecies * 2.0 * (8.0 * tsz + 8.0);
   const double staging = n * (4.0 * 8.0 * (1 + r->nspecies) + 4.0);
   *bytes = (size_t)(fields + particles + staging) + (size_t)(1 << 20);
