@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from parity_util import (TOL, check_j, face_ambiguity_mask, gpu_from_oracle, oracle_start, particle_errors, rel_l2,
+from parity_util import (TOL, check_j, compare_whole_state, gpu_from_oracle, oracle_start, particle_errors, rel_l2,
                          small_kerr, well_conditioned)
 from paper_0904_0232_gb300 import synth
 from paper_0904_0232_gb300.grpic import (GRPIC_LITERAL_HALF_STEPS, GRPIC_STAGE_B_HALF, GRPIC_STAGE_B_HALF2,
@@ -174,25 +174,10 @@ def _whole_steps_against_oracle(wl, prec, nsteps, record):
     independent rounding errors of k + 1 steps adding up."""
     ref = oracle_start(wl)
     sim = gpu_from_oracle(ref, wl, prec)
-    tol = TOL[prec]
-    shape = (wl.nz, wl.ny, wl.nx)
     for step in range(nsteps):
         ref.step(1)
         sim.step(1)
-        grow = step + 1
-        if prec != "fp64":
-            assert not face_ambiguity_mask(ref, shape, len(wl.species)).any()
-        for s in range(len(wl.species)):
-            ex, e4, eu = particle_errors(sim, ref, s)
-            record.append((step, s, ex, e4, eu))
-            assert max(ex, eu) <= tol["particles"] * grow, (step, s, ex, eu)
-        d, b, J = sim.get_fields()
-        dr, br, Jr = ref.get_fields()
-        errs = rel_l2(J, Jr), rel_l2(b, br), rel_l2(d, dr)
-        record.append((step, "J,b,d", *errs))
-        assert errs[0] <= tol["J"] * grow, (step, errs)
-        assert errs[1] <= tol["fields"] * grow, (step, errs)
-        assert errs[2] <= max(tol["fields"], tol["J"]) * grow, (step, errs)
+        compare_whole_state(sim, ref, len(wl.species), prec, step, record)
     return ref, sim
 
 

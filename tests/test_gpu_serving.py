@@ -3,6 +3,8 @@ the device, advanced together one batched timestep per tick.
 
 * a run's result is the same alone and in a mix of runs that arrive before and after it
   (J is accumulated with atomics, so within the parity tolerances rather than bitwise);
+* a run served in a mix, its plasma generated on the device, matches the oracle started from the
+  run's initial state;
 * admission waits for memory: with a budget for one run, the second stays queued until the
   first is released;
 * requests that could never fit, or that differ in precision, are refused.
@@ -10,7 +12,8 @@ the device, advanced together one batched timestep per tick.
 import numpy as np
 import pytest
 
-from parity_util import TOL, rel_l2
+import oracle as O
+from parity_util import TOL, compare_whole_state, rel_l2
 from paper_0904_0232_gb300.grpic import (GRPIC_RUN_DONE, GRPIC_RUN_QUEUED, GRPIC_RUN_RUNNING, GrpicError,
                                          grpic_get_fields, grpic_get_particles, grpic_poll, grpic_request_bytes,
                                          grpic_server_create, grpic_server_destroy, grpic_server_release,
@@ -68,6 +71,51 @@ def test_same_result_alone_and_in_a_mix(prec):
     (da, ba, Ja), (db, bb, Jb) = res_alone[1], res_mix[1]
     assert rel_l2(Jb, Ja) <= tol["J"] * factor and rel_l2(bb, ba) <= tol["fields"] * factor
     grpic_server_destroy(alone)
+    grpic_server_destroy(mix)
+
+
+@pytest.mark.parametrize("prec,nsteps", [("fp64", 3), ("fp32_mixed", 1)])
+def test_served_run_against_oracle(prec, nsteps):
+    """The initial state of a run is read from the same request served with no steps (its plasma is
+    generated on the device from the seed); the oracle starts from it.  The run itself is served
+    in a mix with two others.  FP64: three whole steps, all state compared.  FP32-mixed: one step,
+    every particle, and J and the fields off the nodes of zig-zag splits decided within rounding of
+    a face (the generated plasma cannot be filtered beforehand)."""
+    n = 24
+    A = dict(n=n, m=1.5, a=1.2, ppc=2, seed=31, precision=prec)
+    s0 = grpic_server_create(int(4e9), 4)
+    t0 = grpic_submit(s0, make_request(nsteps=0, **A))
+    ctx0 = _run_to_done(s0, t0)
+    start = [grpic_get_particles(ctx0, s) for s in range(2)]
+    d0, b0, _ = grpic_get_fields(ctx0, (n, n, n))
+    grpic_server_destroy(s0)
+
+    req = make_request(nsteps=nsteps, **A)
+    ref = O.Oracle(n, n, n, A["m"], A["a"], 1.0, 0.4, threads=0)
+    ref.set_fields(d0, b0)
+    for s in range(2):
+        x, u, ids = start[s]
+        ref.load_particles(s, req.q_over_m[s], req.q_macro[s], x, u, ids, umode=0)
+
+    mix = grpic_server_create(int(4e9), 8)
+    tb = grpic_submit(mix, make_request(n=20, m=1.0, a=0.3, ppc=1, nsteps=2, seed=32, precision=prec))
+    grpic_server_tick(mix)
+    ta = grpic_submit(mix, req)
+    tc = grpic_submit(mix, make_request(n=28, m=2.0, a=1.9, ppc=1, nsteps=5, seed=33, precision=prec))
+    ctx = _run_to_done(mix, ta)
+    ref.step(nsteps)
+
+    class View:  # the served context with the comparison helper's accessors
+        def get_particles(self, s):
+            return grpic_get_particles(ctx, s)
+
+        def get_fields(self):
+            return grpic_get_fields(ctx, (n, n, n))
+
+    assert all(start[s][2].size > 100 for s in range(2))
+    compare_whole_state(View(), ref, 2, prec, nsteps - 1 if prec == "fp64" else 0, masked=prec != "fp64")
+    for tk in (tb, tc):
+        _run_to_done(mix, tk)
     grpic_server_destroy(mix)
 
 
