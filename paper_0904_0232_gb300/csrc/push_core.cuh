@@ -77,7 +77,8 @@ __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(__fdividef
 
 // f and k of Eqs. 4-5 for a point whose quartic (Eq. 6) takes its p = R^2 - a^2 > 0 branch and
 // r > 0 (every stage of a far-field particle, R > |a|): with h = p / 2, r^2 = h + sqrt(h^2 + q)
-// and D = 2 sqrt(h^2 + q); the reciprocal square roots give 1/D and 1/r as well.
+// and D = 2 sqrt(h^2 + q); the reciprocal square roots give 1/D and 1/r as well, and since the
+// root satisfies Sigma = r^4 + a^2 z^2 = r^2 D, 1/Sigma and f = 2 m r / D need no division.
 __device__ __forceinline__ Kerr<float> kerr_far(float x, float y, float z, float m, float a) {
   Kerr<float> K;
   const float a2 = a * a;
@@ -92,8 +93,8 @@ __device__ __forceinline__ Kerr<float> kerr_far(float x, float y, float z, float
   K.inv_r = rsqrtf(r2);
   K.r = r2 * K.inv_r;
   K.inv_rho2 = __fdividef(1.f, r2 + a2);
-  K.inv_sig = __fdividef(1.f, fmaf(r2, r2, q));
-  K.f = 2.f * m * K.r * r2 * K.inv_sig;
+  K.inv_sig = K.inv_D * K.inv_r * K.inv_r;
+  K.f = m * K.r * rDh;
   K.k0 = (K.r * x - a * y) * K.inv_rho2;
   K.k1 = (K.r * y + a * x) * K.inv_rho2;
   K.k2 = z * K.inv_r;
@@ -593,22 +594,22 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
             const float2 p = add2(pR, pJ2[k]);
             const float2 q = add2(qR, qJ2[k]);
             const float2 D2 = fma2(p, p, q);
-            const float2 r2 = fma2(D2, rsqrt2(D2), p);
-            const float2 r = mul2(r2, rsqrt2(r2));
-            const float2 sig = fma2(r2, r2, q);
-            float2 numer, den;
+            const float2 rD2 = rsqrt2(D2);  // 2 / D
+            const float2 r2 = fma2(D2, rD2, p);
+            const float2 ir = rsqrt2(r2);
+            // at the root r^4 + a^2 z^2 = r^2 D, so f = 2 m r^3 / Sigma = 2 m r / D = m r rsqrt(D2)
+            float2 v;
             if (K == 2) {
-              numer = mul2(mul2(f2(C.two_m), r), add2(r2, f2(nzz)));
-              den = sig;
+              // f (1 - z^2 / r^2) = m rsqrt(D2) (r^2 - z^2) / r
+              v = fma2(mul2(mul2(f2(C.m), rD2), add2(r2, f2(nzz))), ir, f2(1.f));
             } else {
-              // rho^4 - num^2 over rho^4 Sigma, both negated: (num^2 - rho^4) / (-rho^4 Sigma)
+              // f (1 - k_K^2) with k_K = num / rho^2
+              const float2 r = mul2(r2, ir);
               const float2 num = fma2(r, f2(L.XK), add2(tR, tJ2[k]));
-              const float2 rho2 = add2(r2, f2(C.a2));
-              const float2 nrho4 = mul2(rho2, fma2(r2, f2(-1.f), f2(-C.a2)));
-              numer = mul2(mul2(mul2(f2(C.two_m), r), r2), fma2(num, num, nrho4));
-              den = mul2(nrho4, sig);
+              const float2 kK = mul2(num, rcp2(add2(r2, f2(C.a2))));
+              const float2 omk2 = fma2(kK, make_float2(-kK.x, -kK.y), f2(1.f));
+              v = fma2(mul2(mul2(f2(C.m), r), rD2), omk2, f2(1.f));
             }
-            float2 v = fma2(numer, rcp2(den), f2(1.f));
             float2 rv = rsqrt2(v);
             if (mixed) {
               const int bit = (si * Q + pi) * 2 * Q + 2 * k;
