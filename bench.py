@@ -68,7 +68,9 @@ def parse():
     p.add_argument("--grid", type=int, default=128)
     p.add_argument("--quad", type=int, default=2)
     p.add_argument("--sort-interval", type=int, default=1)
-    p.add_argument("--fp64-steps", type=int, default=10)
+    p.add_argument("--fp64-steps", type=int, default=20,
+                   help="steps of the FP64 comparison leg (at most --steps), after the same warm-up as the "
+                        "measured window; 0 skips it")
     p.add_argument("--fp32-compare-steps", type=int, default=200,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
     p.add_argument("--workload", choices=["kerr128", "batch", "disk384", "jet", "fields"], default="kerr128",
@@ -305,12 +307,20 @@ def run_gpu(args, dist):
         del simt
         torch.cuda.empty_cache()
 
-    def leg(precision, steps, warmup, **kw):
-        """A fresh context from the same initial state, `warmup` untimed then `steps` timed steps."""
+    invariants = {}
+
+    def leg(precision, steps, warmup, record_invariants=False, **kw):
+        """A fresh context from the same initial state, `warmup` untimed then `steps` timed steps
+        (with record_invariants, the invariant statistics over the timed steps, evaluated outside
+        the timed region)."""
         s_ = make_sim(wl, precision, args, tuning=tuned["tuning"], **kw)
         s_.set_profiling(True)
         s_.step(warmup)
+        if record_invariants:
+            invariants["start"] = s_.invariants(baseline=True)
         out = timed_steps(s_, steps, dist) + (s_.stats(), s_.tuning())
+        if record_invariants:
+            invariants["end"] = s_.invariants()
         s_.close()
         del s_
         torch.cuda.empty_cache()
@@ -326,7 +336,7 @@ def run_gpu(args, dist):
     # --- FP32-mixed, inputs resident in HBM
     clocks = Clocks(dist.local)
     clocks.start()
-    ms, psteps, prof, launches, st, tuning_used = leg("fp32_mixed", args.steps, args.warmup)
+    ms, psteps, prof, launches, st, tuning_used = leg("fp32_mixed", args.steps, args.warmup, record_invariants=True)
     clk = clocks.stop()
 
     t_max = dist.max(ms)
@@ -342,14 +352,18 @@ def run_gpu(args, dist):
     if PUSH_TRAFFIC["sha"] == sha and PUSH_TRAFFIC["bytes_per_particle"]:
         traffic = PUSH_TRAFFIC["bytes_per_particle"] * psteps / max(1, push_n)
 
-    # --- FP64 path over the first steps (it runs at a small fraction of the FP32 rate), beside the
-    #     FP32-mixed path over the same window from the same start
+    # --- the FP64 path over the measured window (its first steps when --steps is longer; it runs at a
+    #     small fraction of the FP32 rate), beside the FP32-mixed path over the same steps
     fp64 = None
-    if args.fp64_steps > 0:
-        ms64, ps64, prof64, _, _, _ = leg("fp64", args.fp64_steps, 1)
-        msw, psw, profw, _, _, _ = leg("fp32_mixed", args.fp64_steps, 1)
-        fp64 = summary(ms64, ps64, prof64, args.fp64_steps, f"steps 2-{args.fp64_steps + 1} from the start")
-        fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, args.fp64_steps)
+    n64 = min(args.fp64_steps, args.steps)
+    if n64 > 0:
+        ms64, ps64, prof64, _, _, _ = leg("fp64", n64, args.warmup)
+        if n64 == args.steps:
+            msw, psw, profw = ms, psteps, prof
+        else:
+            msw, psw, profw, _, _, _ = leg("fp32_mixed", n64, args.warmup)
+        fp64 = summary(ms64, ps64, prof64, n64, f"steps {args.warmup + 1}-{args.warmup + n64} from the start")
+        fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, n64)
 
     # --- the same steps with every particle through the FP32-mixed code (no far-field path)
     single = None
@@ -428,8 +442,21 @@ def run_gpu(args, dist):
         "cpu_baseline": cpu,
         "clocks": clk,
         "stats": {k: st[k] for k in ("removed_horizon", "removed_outer", "gamma_fallbacks", "fp64_evals")},
+        "invariants": invariant_summary(invariants["start"], invariants["end"], args.steps),
     }
     return line
+
+
+def invariant_summary(start, end, steps):
+    """Per-run invariant statistics: the normalisation residual |g(u,u) + c^2| / c^2 (Eq. 7) at the
+    start and the end of the timed steps, and the change of E = -u_4 and L = u_phi (Eq. 3) over them
+    for the tracked subsample (ids divisible by 64) -- E and L are invariants of field-free orbits
+    only; with fields they measure the work done on the particles."""
+    return {"steps": steps, "norm_max_start": start["norm_max"], "norm_max": end["norm_max"],
+            "norm_mean": end["norm_mean"], "tracked": end["tracked"],
+            "energy_change_mean": end["energy_mean"], "energy_change_max": end["energy_max"],
+            "angmom_change_mean": end["angmom_mean"], "angmom_change_max": end["angmom_max"],
+            "units": "norm relative to c^2; E and L changes divided by c (L in cells)"}
 
 
 def run_batch(args, dist):
@@ -552,16 +579,19 @@ def run_disk(args, dist):
     torch.cuda.empty_cache()
     sim.set_profiling(True)
     sim.step(args.warmup)
+    inv0 = sim.invariants(baseline=True)
     clocks = Clocks(dist.local)
     clocks.start()
     ms, psteps, prof, launches = timed_steps(sim, args.steps, dist)
     clk = clocks.stop()
+    inv1 = sim.invariants()
     st = sim.stats()
     sim.close()
     value = dist.sum(psteps) / (dist.max(ms) * 1e-3)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dist.max(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 quartic/metric/Christoffel where r < 4m; FP64 J)",
+            "invariants": invariant_summary(inv0, inv1, args.steps),
             "data": "synthetic (device-generated disk + corona)",
             "config": {"workload": f"kerr_disk_corona_{geo['n']}: Kerr a=0.95m, m={geo['m']:g} cells, {geo['n']}^3, "
                                    "Keplerian disk (|z|<0.1 r_cyl, 6m..150 cells, density ~1/r) in a 1% corona, "
@@ -606,10 +636,12 @@ def run_jet(args, dist):
     sim = make(tuning)
     sim.set_profiling(True)
     sim.step(args.warmup)
+    inv0 = sim.invariants(baseline=True)
     clocks = Clocks(dist.local)
     clocks.start()
     ms, psteps, prof, launches = timed_steps(sim, args.steps, dist)
     clk = clocks.stop()
+    inv1 = sim.invariants()
     st = sim.stats()
     used = sim.tuning()
     sim.close()
@@ -618,6 +650,7 @@ def run_jet(args, dist):
             "warmup": args.warmup, "ms_per_step": dist.max(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 quartic/metric/Christoffel where r < 4m; FP64 J)",
             "data": "synthetic (seeded; the parameters of the paper's application set-up, Sec. 6)",
+            "invariants": invariant_summary(inv0, inv1, args.steps),
             "config": {"workload": "kerr_jet_disk_64x64x128: Kerr a=0.95m, m=2 cells, c=0.05, dt=1, B_z=30, "
                                    "e-/e+ |q/m|=1e-3, Keplerian disk (R>12 cells, |cos theta|<1/8, 0.8M particles) "
                                    "at 100x the density of a free-falling corona",

@@ -127,8 +127,8 @@ typedef struct {
 typedef struct grpic_ctx grpic_ctx;
 
 /* Create a context on the current CUDA device.  Validates the configuration (Courant:
- * c dt < 1/sqrt(3), Sec. 5), computes r_+ = m + sqrt(m^2 - a^2), and caches the metric at
- * every field location.  `stream` is a cudaStream_t (NULL = default stream).
+ * c dt < 1/sqrt(3), Sec. 5), computes r_+ = m + sqrt(m^2 - a^2), and flags every field location
+ * as advanced or excised (decided in FP64).  `stream` is a cudaStream_t (NULL = default stream).
  * Returns GRPIC_ERR_INVALID / GRPIC_ERR_CFL on bad input, GRPIC_ERR_OOM if allocation fails. */
 grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out);
 
@@ -190,6 +190,25 @@ grpic_status grpic_get_particles(grpic_ctx* ctx, int species, int64_t* n_inout, 
                                  uint32_t* ids, int mem);
 
 grpic_status grpic_get_stats(grpic_ctx* ctx, grpic_stats* out);
+
+/* Invariants of the particles' motion, evaluated in FP64 from the stored state of every live
+ * particle: the normalisation g_mn u^m u^n = -c^2 of Eq. 7 (kept by the exact dynamics in any
+ * field), and for a tracked subsample (ids divisible by 64) the change of the Killing energy
+ * E = -u_4 and of the axial momentum L = u_phi = x u_y - y u_x (covariant components, position from
+ * the centre; Eq. 3), both conserved along field-free orbits, since the last call with
+ * set_baseline = 1.  Particles removed since the baseline are not compared.  The baseline buffers
+ * are allocated by the context (sized by the largest id) and freed with it. */
+typedef struct {
+  int64_t n;           /* live particles evaluated */
+  double norm_max;     /* max |g_mn u^m u^n + c^2| / c^2 */
+  double norm_mean;
+  int64_t tracked;     /* subsample particles present at the baseline and now */
+  double energy_mean;  /* mean |E - E_0| / c over the tracked particles */
+  double energy_max;
+  double angmom_mean;  /* mean |L - L_0| / c (cells) */
+  double angmom_max;
+} grpic_invariants;
+grpic_status grpic_get_invariants(grpic_ctx* ctx, int set_baseline, grpic_invariants* out);
 
 /* Message for the last error on this context ("" if none); valid until the next call. */
 const char* grpic_last_error(const grpic_ctx* ctx);
@@ -378,6 +397,8 @@ grpic_status grpic_server_tick(grpic_server* s, int* running, int* queued);
 /* State of a run (GRPIC_RUN_*); once done, *ctx (may be NULL) borrows its context (fields,
  * particles, stats) until grpic_server_release. */
 grpic_status grpic_poll(grpic_server* s, uint64_t ticket, int* state, grpic_ctx** ctx);
+/* A run's context carries the invariant baseline of its initial plasma (set at admission), so
+ * grpic_get_invariants(ctx, 0, ...) on a finished run gives the change over the whole run. */
 
 /* Free a finished run's context and forget the ticket. */
 grpic_status grpic_server_release(grpic_server* s, uint64_t ticket);

@@ -280,6 +280,15 @@ void launch_charge_density(const Particles<T>& P, double q, const Grid& g, bool 
 template <typename T>
 void launch_gauss(const Fields<T>& F, const double* rho, const Grid& g, int lo, double* res,
                   unsigned long long* maxabs, cudaStream_t stream);
+// Invariant statistics (diag.cu): mode 0 records the tracked particles' E and L, mode 1 compares;
+// acc: invariant_acc_bytes() of zeroed device memory accumulating over the species launched.
+template <typename T>
+void launch_invariants(const Grid& g, const Particles<T>& P, int mode, int stride, double* e0, double* l0,
+                       long long nslots, void* acc, cudaStream_t stream);
+template <typename T>
+void launch_max_id(const Particles<T>& P, unsigned long long* max_id, cudaStream_t stream);
+size_t invariant_acc_bytes();
+constexpr int kInvariantStride = 64;  // tracked subsample: ids divisible by this
 
 // Counting sort by cell of one species; removed particles (key == kDead) are dropped.
 // counts: nbins+1 ints, offsets: nbins+1 ints, blocks: scan scratch; n_out: device int.

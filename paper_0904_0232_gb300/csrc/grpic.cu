@@ -63,6 +63,10 @@ struct grpic_ctx {
   grpic_status step_status = GRPIC_OK;  // status of this context after the last batched step  // push stages run: particle x^4 is stored relative to c dt * pushes
   int since_sort = 0;
   grpic_stats totals{};
+  // invariant baselines: per species E and L of the tracked particles, by id / stride
+  double* inv_e0[kMaxSpecies] = {nullptr, nullptr, nullptr, nullptr};
+  double* inv_l0[kMaxSpecies] = {nullptr, nullptr, nullptr, nullptr};
+  long long inv_slots[kMaxSpecies] = {0, 0, 0, 0};
   // tracing
   long long launches = 0;
   bool profiling = false;
@@ -556,6 +560,8 @@ grpic_status grpic_destroy(grpic_ctx* c) {
   dev_free(c, c->sort.offsets);
   dev_free(c, c->sort.blocks);
   for (int s = 0; s < kMaxSpecies; ++s) {
+    dev_free(c, c->inv_e0[s]);
+    dev_free(c, c->inv_l0[s]);
     dev_free(c, c->sp[s].buf[0]);
     dev_free(c, c->sp[s].buf[1]);
     dev_free(c, c->sp[s].n_dev);
@@ -848,6 +854,82 @@ grpic_status grpic_get_stats(grpic_ctx* c, grpic_stats* out) {
     out->n_alive[q] = v;
   }
   return GRPIC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+grpic_status invariants(grpic_ctx* c, int set_baseline, grpic_invariants* out) {
+  struct Acc {
+    unsigned long long n, tracked;
+    double norm_sum, e_sum, l_sum;
+    unsigned long long norm_max, e_max, l_max;
+    unsigned long long max_id;
+  };
+  if (sizeof(Acc) != invariant_acc_bytes()) return fail(c, GRPIC_ERR_INVALID, "invariant accumulator layout");
+  // particles removed since the last sort carry the removed key and are skipped: no sort here, so
+  // the call leaves the run's sort schedule as it is
+  Acc* acc = static_cast<Acc*>(dev_alloc(c, sizeof(Acc) * (kMaxSpecies + 1)));
+  if (!acc) return fail(c, GRPIC_ERR_OOM, "invariant accumulator");
+  cudaMemsetAsync(acc, 0, sizeof(Acc) * (kMaxSpecies + 1), c->stream);
+  grpic_status st = GRPIC_OK;
+  for (int s = 0; s < kMaxSpecies && st == GRPIC_OK; ++s) {
+    SpeciesStore& S = c->sp[s];
+    if (!S.loaded || S.n == 0) continue;
+    const Particles<T> P = particles_view<T>(c, s, S.cur);
+    if (set_baseline) {
+      launch_max_id<T>(P, &acc[1 + s].max_id, c->stream);
+      Acc h{};
+      cudaMemcpyAsync(&h, &acc[1 + s], sizeof(Acc), cudaMemcpyDeviceToHost, c->stream);
+      st = cuda_check(c, cudaStreamSynchronize(c->stream), "invariants max id");
+      if (st != GRPIC_OK) break;
+      const long long slots = (long long)(h.max_id / kInvariantStride) + 1;
+      if (slots > c->inv_slots[s]) {
+        dev_free(c, c->inv_e0[s]);
+        dev_free(c, c->inv_l0[s]);
+        c->inv_e0[s] = static_cast<double*>(dev_alloc(c, sizeof(double) * slots));
+        c->inv_l0[s] = static_cast<double*>(dev_alloc(c, sizeof(double) * slots));
+        c->inv_slots[s] = (c->inv_e0[s] && c->inv_l0[s]) ? slots : 0;
+        if (!c->inv_slots[s]) st = fail(c, GRPIC_ERR_OOM, "invariant baseline");
+      }
+      if (st != GRPIC_OK) break;
+      // all-ones bytes are a NaN: slots no live particle fills stay untracked
+      cudaMemsetAsync(c->inv_e0[s], 0xff, sizeof(double) * c->inv_slots[s], c->stream);
+    }
+    launch_invariants<T>(c->g, P, set_baseline ? 0 : 1, kInvariantStride, c->inv_e0[s], c->inv_l0[s],
+                         c->inv_slots[s], acc, c->stream);
+    c->launches += 1;
+  }
+  Acc h{};
+  cudaMemcpyAsync(&h, acc, sizeof(Acc), cudaMemcpyDeviceToHost, c->stream);
+  if (st == GRPIC_OK) st = cuda_check(c, cudaStreamSynchronize(c->stream), "invariants");
+  else cudaStreamSynchronize(c->stream);
+  dev_free(c, acc);
+  if (st != GRPIC_OK || !out) return st;
+  auto bits = [](unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof(d));
+    return d;
+  };
+  out->n = (int64_t)h.n;
+  out->norm_max = bits(h.norm_max);
+  out->norm_mean = h.n ? h.norm_sum / (double)h.n : 0.0;
+  out->tracked = set_baseline ? 0 : (int64_t)h.tracked;
+  out->energy_mean = h.tracked && !set_baseline ? h.e_sum / (double)h.tracked : 0.0;
+  out->energy_max = set_baseline ? 0.0 : bits(h.e_max);
+  out->angmom_mean = h.tracked && !set_baseline ? h.l_sum / (double)h.tracked : 0.0;
+  out->angmom_max = set_baseline ? 0.0 : bits(h.l_max);
+  return GRPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grpic_status grpic_get_invariants(grpic_ctx* c, int set_baseline, grpic_invariants* out) {
+  if (!c) return GRPIC_ERR_INVALID;
+  return c->mixed ? invariants<float>(c, set_baseline, out) : invariants<double>(c, set_baseline, out);
 }
 
 grpic_status grpic_charge_density(grpic_ctx* c, int with_gamma, double* rho, int mem) {

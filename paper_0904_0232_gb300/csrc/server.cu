@@ -201,6 +201,8 @@ grpic_status start_run(grpic_server* s, Run* r) {
                                 reinterpret_cast<const uint32_t*>(ids), GRPIC_U_COV_SPATIAL | GRPIC_LOAD_DEVICE);
   }
   cudaStreamSynchronize(s->stream);
+  // invariant baseline of the run's initial plasma (reported at completion)
+  if (st == GRPIC_OK) st = grpic_get_invariants(r->ctx, 1, nullptr);
   s_free(s, x4);
   s_free(s, u4);
   s_free(s, ids);

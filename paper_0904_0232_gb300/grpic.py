@@ -57,6 +57,12 @@ class grpic_stats(ctypes.Structure):
                 ("particle_steps", ctypes.c_int64), ("n_alive", ctypes.c_int64 * 4)]
 
 
+class grpic_invariants(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("norm_max", ctypes.c_double), ("norm_mean", ctypes.c_double),
+                ("tracked", ctypes.c_int64), ("energy_mean", ctypes.c_double), ("energy_max", ctypes.c_double),
+                ("angmom_mean", ctypes.c_double), ("angmom_max", ctypes.c_double)]
+
+
 class grpic_tuning(ctypes.Structure):
     _fields_ = [("far_min_blocks", ctypes.c_int), ("near_blocks_per_sm", ctypes.c_int), ("sort_interval", ctypes.c_int),
                 ("overlap", ctypes.c_int), ("split", ctypes.c_int), ("j_tile", ctypes.c_int),
@@ -89,6 +95,7 @@ EXPORTS = {
     "grpic_get_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.c_int]),
+    "grpic_get_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(grpic_invariants)]),
     "grpic_charge_density": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
     "grpic_gauss_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double)]),
@@ -313,6 +320,14 @@ def grpic_get_profile(ctx, reset=False):
     _check(ctx, load_library().grpic_get_profile(ctx, ms, cnt, ctypes.byref(nl), int(bool(reset))),
            "grpic_get_profile")
     return {STAGE_NAMES[q]: (ms[q], cnt[q]) for q in range(6)}, nl.value
+
+
+def grpic_get_invariants(ctx, set_baseline=False):
+    """Invariant statistics of the live particles (see include/grpic.h) as a dict."""
+    out = grpic_invariants()
+    _check(ctx, load_library().grpic_get_invariants(ctx, int(bool(set_baseline)), ctypes.byref(out)),
+           "grpic_get_invariants")
+    return {k: getattr(out, k) for k, _ in grpic_invariants._fields_}
 
 
 def grpic_charge_density(ctx, shape, with_gamma=False):
@@ -565,6 +580,9 @@ class Simulation:
 
     def tuning(self):
         return grpic_get_tuning(self.handle)
+
+    def invariants(self, baseline=False):
+        return grpic_get_invariants(self.handle, baseline)
 
     def charge_density(self, with_gamma=False):
         return grpic_charge_density(self.handle, self.shape, with_gamma)

@@ -12,9 +12,9 @@ import time
 
 import numpy as np
 
-from .grpic import (GRPIC_OK, GRPIC_RUN_DONE, STATUS_NAMES, grpic_get_stats, grpic_poll, grpic_request_bytes,
-                    grpic_server_create, grpic_server_destroy, grpic_server_release, grpic_server_tick,
-                    grpic_submit, make_request)
+from .grpic import (GRPIC_OK, GRPIC_RUN_DONE, STATUS_NAMES, grpic_get_invariants, grpic_get_stats, grpic_poll,
+                    grpic_request_bytes, grpic_server_create, grpic_server_destroy, grpic_server_release,
+                    grpic_server_tick, grpic_submit, make_request)
 
 
 def sample_requests(n, seed, grids=(32, 48, 64), ppc=(1, 8), steps=(50, 200), m=(1.0, 4.0), spin_max=0.99):
@@ -44,6 +44,7 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     pending = {}   # ticket -> arrival time
     lat = []
     failed = []
+    inv = []   # per finished run: |g(u,u) + c^2| / c^2 at the end and the E, L changes over the run
     psteps = 0
     nxt = 0
     t0 = time.perf_counter()
@@ -64,6 +65,8 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
                     if state == GRPIC_RUN_DONE:
                         if ctx:
                             psteps += grpic_get_stats(ctx)["particle_steps"]
+                            iv = grpic_get_invariants(ctx)
+                            inv.append((iv["norm_max"], iv["energy_max"], iv["angmom_max"]))
                         if status == GRPIC_OK:
                             lat.append(done_now - pending.pop(tk))
                         else:
@@ -86,7 +89,14 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "p50_s_lower_bound_all": float(np.percentile(allv, 50)) if allv.size else None,
             "p99_s_lower_bound_all": float(np.percentile(allv, 99)) if allv.size else None,
-            "particle_steps_per_s": psteps / wall if wall > 0 else 0.0, "wall_s": wall}
+            "particle_steps_per_s": psteps / wall if wall > 0 else 0.0, "wall_s": wall,
+            "invariants": ({"runs": len(inv), "norm_max": max(v[0] for v in inv),
+                            "norm_max_median_run": float(np.median([v[0] for v in inv])),
+                            "energy_change_max_median_run": float(np.median([v[1] for v in inv])),
+                            "angmom_change_max_median_run": float(np.median([v[2] for v in inv])),
+                            "note": "per run, from its initial plasma to its end: |g(u,u)+c^2|/c^2 (Eq. 7) "
+                                    "and the changes of -u_4 and u_phi over the tracked subsample, /c"}
+                           if inv else None)}
 
 
 # Request mixes: grid edge, particles per cell per species, timesteps (each drawn uniformly), with
