@@ -51,7 +51,8 @@ typedef enum {
   GRPIC_ERR_NONFINITE = 5, /* NaN/Inf in particle state */
   GRPIC_ERR_TIMEOUT = 6,   /* a bounded wait gave up */
   GRPIC_ERR_AGAIN = 7,     /* serving: request not finished / not admitted yet */
-  GRPIC_ERR_CAPACITY = 8   /* more particles than the context's capacity */
+  GRPIC_ERR_CAPACITY = 8,  /* more particles than the context's capacity */
+  GRPIC_ERR_UNSTABLE = 9   /* serving: the request's box is too small for its hole (see grpic_submit) */
 } grpic_status;
 
 enum { GRPIC_FP64 = 0, GRPIC_FP32_MIXED = 1 };
@@ -385,7 +386,13 @@ grpic_status grpic_server_create(size_t hbm_budget, int max_slots, grpic_alloc_f
                                  void* alloc_user, grpic_server** out);
 
 /* Queue a run; *ticket identifies it.  GRPIC_ERR_CAPACITY if it could never fit the budget,
- * GRPIC_ERR_INVALID for a bad request or one whose precision/quadrature/flags differ. */
+ * GRPIC_ERR_INVALID for a bad request or one whose precision/quadrature/flags differ.
+ * GRPIC_ERR_UNSTABLE for a run longer than 40 light-crossing units (nsteps c dt > 40 cells) on a
+ * grid whose faces lie where the metric is far from flat, f = 2m / R_face > 0.2 with R_face =
+ * (min(nx, ny, nz) - 1) / 2: there the field update with its frozen outer layers (reading of the
+ * paper's silent boundaries) grows a mode at the box edges, whatever the timestep, which after
+ * ~100 steps accelerates the plasma past the one-cell step limit.  Short runs on such grids and
+ * every run on larger grids are admitted. */
 grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* ticket);
 
 /* Admit what fits, advance every running run one timestep, retire finished runs.  A run whose

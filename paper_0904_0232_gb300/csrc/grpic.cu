@@ -452,6 +452,7 @@ const char* grpic_status_string(grpic_status s) {
     case GRPIC_ERR_TIMEOUT: return "GRPIC_ERR_TIMEOUT";
     case GRPIC_ERR_AGAIN: return "GRPIC_ERR_AGAIN";
     case GRPIC_ERR_CAPACITY: return "GRPIC_ERR_CAPACITY";
+    case GRPIC_ERR_UNSTABLE: return "GRPIC_ERR_UNSTABLE";
   }
   return "GRPIC_ERR_UNKNOWN";
 }

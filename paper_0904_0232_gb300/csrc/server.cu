@@ -6,6 +6,7 @@
 // and Flood) keyed by (seed, stream, counter): positions uniform in each cell of [1, n-3]^3,
 // covariant spatial momenta with Maxwell-Juettner magnitudes (inverse-CDF table) and isotropic
 // directions.  u^4 is completed by the regular load path.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -102,6 +103,10 @@ std::vector<double> mj_inverse_cdf(double theta) {
   }
   return inv;
 }
+
+// Admission limits of the field update's outer boundary (see grpic_submit in include/grpic.h).
+constexpr double kMaxFaceF = 0.2;
+constexpr double kMaxUnstableTime = 40.0;
 
 long long interior_slots(const grpic_request& r) {
   return (long long)(r.cfg.nx - 3) * (r.cfg.ny - 3) * (r.cfg.nz - 3) * r.ppc;
@@ -252,6 +257,12 @@ grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* t
   const int quad = req->cfg.quad_order == 0 ? 2 : req->cfg.quad_order;
   if (s->have_kind && (req->cfg.precision != s->precision || quad != s->quad || req->cfg.flags != s->flags))
     return GRPIC_ERR_INVALID;
+  // the box's faces where f = 2m / R_face > 0.2: the field update grows an edge mode there (measured
+  // onset ~40 light-crossing units), so long runs on such grids are refused
+  const int nmin = std::min(req->cfg.nx, std::min(req->cfg.ny, req->cfg.nz));
+  const double f_face = 2.0 * req->cfg.m / (0.5 * (nmin - 1));
+  if (f_face > kMaxFaceF && (double)req->nsteps * req->cfg.c * req->cfg.dt > kMaxUnstableTime)
+    return GRPIC_ERR_UNSTABLE;
   size_t bytes = 0;
   grpic_request_bytes(req, &bytes);
   if (bytes > s->budget) return GRPIC_ERR_CAPACITY;

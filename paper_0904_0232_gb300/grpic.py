@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(HERE, "libgrpic.so")
 
 GRPIC_OK = 0
 STATUS_NAMES = {0: "GRPIC_OK", 1: "GRPIC_ERR_INVALID", 2: "GRPIC_ERR_OOM", 3: "GRPIC_ERR_CUDA", 4: "GRPIC_ERR_CFL",
-                5: "GRPIC_ERR_NONFINITE", 6: "GRPIC_ERR_TIMEOUT", 7: "GRPIC_ERR_AGAIN", 8: "GRPIC_ERR_CAPACITY"}
+                5: "GRPIC_ERR_NONFINITE", 6: "GRPIC_ERR_TIMEOUT", 7: "GRPIC_ERR_AGAIN", 8: "GRPIC_ERR_CAPACITY",
+                9: "GRPIC_ERR_UNSTABLE"}
+GRPIC_ERR_UNSTABLE = 9
 GRPIC_FP64, GRPIC_FP32_MIXED = 0, 1
 GRPIC_NO_GAMMA_IN_J = 1
 GRPIC_LITERAL_HALF_STEPS = 2

@@ -12,9 +12,9 @@ import time
 
 import numpy as np
 
-from .grpic import (GRPIC_OK, GRPIC_RUN_DONE, STATUS_NAMES, grpic_get_invariants, grpic_get_stats, grpic_poll,
-                    grpic_request_bytes, grpic_server_create, grpic_server_destroy, grpic_server_release,
-                    grpic_server_tick, grpic_submit, make_request)
+from .grpic import (GRPIC_OK, GRPIC_RUN_DONE, STATUS_NAMES, GrpicError, grpic_get_invariants, grpic_get_stats,
+                    grpic_poll, grpic_request_bytes, grpic_server_create, grpic_server_destroy,
+                    grpic_server_release, grpic_server_tick, grpic_submit, make_request)
 
 
 def sample_requests(n, seed, grids=(32, 48, 64), ppc=(1, 8), steps=(50, 200), m=(1.0, 4.0), spin_max=0.99):
@@ -44,6 +44,7 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     pending = {}   # ticket -> arrival time
     lat = []
     failed = []
+    refused = []
     inv = []   # per finished run: |g(u,u) + c^2| / c^2 at the end and the E, L changes over the run
     psteps = 0
     nxt = 0
@@ -55,7 +56,10 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
                 break
             while nxt < len(arrivals) and arrivals[nxt] <= now:
                 req = make_request(**specs[nxt])
-                pending[grpic_submit(server, req)] = arrivals[nxt]
+                try:
+                    pending[grpic_submit(server, req)] = arrivals[nxt]
+                except GrpicError as e:  # refused at admission (e.g. GRPIC_ERR_UNSTABLE), with its reason
+                    refused.append(STATUS_NAMES.get(e.code, e.code))
                 nxt += 1
             if pending:
                 grpic_server_tick(server)
@@ -85,6 +89,7 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
     allv = np.concatenate([lat, cens]) if cens.size else lat
     return {"rate": rate, "arrivals": len(arrivals), "completed": int(lat.size), "unfinished": int(cens.size),
             "failed": len(failed), "failed_status": sorted(set(failed)),
+            "refused": len(refused), "refused_status": sorted(set(refused)),
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "p50_s_lower_bound_all": float(np.percentile(allv, 50)) if allv.size else None,

@@ -170,3 +170,18 @@ def test_release_while_others_run():
             break
     assert done == {ta, tb, tc}
     grpic_server_destroy(server)
+
+
+def test_unstable_boxes_are_refused():
+    """A long run on a box whose faces see f = 2m / R_face > 0.2 is refused with GRPIC_ERR_UNSTABLE
+    (the field update grows an edge mode there, independent of the timestep); a short run on the
+    same box and a long run on a box four times larger are admitted."""
+    from paper_0904_0232_gb300.grpic import GRPIC_ERR_UNSTABLE
+
+    server = grpic_server_create(int(4e9), 8)
+    with pytest.raises(GrpicError) as ei:
+        grpic_submit(server, make_request(n=32, m=3.0, a=0.0, ppc=1, nsteps=200, seed=51))
+    assert ei.value.code == GRPIC_ERR_UNSTABLE
+    grpic_submit(server, make_request(n=32, m=3.0, a=0.0, ppc=1, nsteps=50, seed=52))
+    grpic_submit(server, make_request(n=128, m=3.0, a=0.0, ppc=1, nsteps=500, seed=53))
+    grpic_server_destroy(server)
