@@ -186,11 +186,11 @@ __device__ __forceinline__ T face_h(const FieldConsts<T>& K, const Plane3<T, BY>
 // 4 pi / c J^al in the field type: FP64 J rounded to FP32 with integer operations (this GPU runs
 // conversions on its reduced-rate FP64 pipe), then scaled in FP32.
 template <typename T>
-__device__ __forceinline__ T source(const FieldConsts<T>& K, const double* __restrict__ J, long long c) {
+__device__ __forceinline__ T source(const FieldConsts<T>& K, double J) {
   if constexpr (sizeof(T) == sizeof(float))
-    return narrow(__ldg(J + c)) * K.four_pi_c;
+    return narrow(J) * K.four_pi_c;
   else
-    return K.four_pi_c * __ldg(J + c);
+    return K.four_pi_c * J;
 }
 
 __device__ __forceinline__ bool adv(uint16_t w, int l) { return (w >> l) & 1u; }
@@ -286,10 +286,23 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
     st.stage(g, A.d, q, sm.Sd[sd(q)]);
   }
   cp_async_commit();
+  const long long splane = (long long)g.nx * g.ny;
+  uint16_t w_prev = 0;  // flags of plane P - 1, loaded one iteration ahead
   for (int P = zs; P <= ze; ++P) {
     st.stage(g, A.src, P + 2, sm.Sb[sb(P + 2)]);
     st.stage(g, A.d, P + 2, sm.Sd[sd(P + 2)]);
     cp_async_commit();
+    // loads of this iteration issued ahead of the waits: the flags of plane P and, for the in-place
+    // update of plane P - 1, its b^{n-1/2}
+    const long long cP = ((long long)P * g.ny + y) * g.nx + x;
+    const uint16_t w_cur = (in_xy && P < g.nz) ? __ldg(A.loc + cP) : (uint16_t)0;
+    const int p = P - 1;
+    const bool upd = p >= zs && out_xy;
+    T base_old[3] = {T(0), T(0), T(0)};
+    if (A.inplace && upd) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) base_old[q] = A.base[q][cP - splane];
+    }
     cp_async_wait<1>();  // planes up to P + 1 have landed
     __syncthreads();
     // e at plane P
@@ -297,8 +310,7 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
       const int buf = P & 1;
       T e0 = T(0), e1 = T(0), e2 = T(0);
       if (conv_xy && P >= 1 && P <= g.nz - 2) {
-        const long long c = ((long long)P * g.ny + y) * g.nx + x;
-        const uint16_t w = __ldg(A.loc + c);
+        const uint16_t w = w_cur;
         const T zr = (T)P - A.K.zc;
         const int b0 = sb(P - 1), b1 = sb(P), b2 = sb(P + 1);
         const int d0 = sd(P - 1), d1 = sd(P), d2 = sd(P + 1);
@@ -312,10 +324,9 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
     }
     __syncthreads();
     // b update at plane P - 1 from e of planes P - 1 and P
-    const int p = P - 1;
-    if (p >= zs && out_xy) {
-      const long long c = ((long long)p * g.ny + y) * g.nx + x;
-      const uint16_t w = __ldg(A.loc + c);
+    if (upd) {
+      const long long c = cP - splane;
+      const uint16_t w = w_prev;
       const T (&E)[3][BY][kTX] = sm.E[p & 1];
       const T (&En)[3][BY][kTX] = sm.E[P & 1];
       // curl e at the three faces: b_x = F_yz: d_y e_z - d_z e_y; b_y = F_zx: d_z e_x - d_x e_z;
@@ -327,13 +338,14 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         // b at the cell: the staged b^n when the base is the source, else the other buffer
-        const T old = A.inplace ? A.base[q][c] : sm.Sb[sb(p)].v[q][ty + 1][tx + 1];
+        const T old = A.inplace ? base_old[q] : sm.Sb[sb(p)].v[q][ty + 1][tx + 1];
         if (adv(w, 3 + q))
           A.out[q][c] = old - A.coef * cu[q];
         else if (!A.inplace)
           A.out[q][c] = old;
       }
     }
+    w_prev = w_cur;
   }
   cp_async_wait<0>();
 }
@@ -390,11 +402,25 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
   }
   cp_async_commit();
   int cur = 0;  // buffer of plane p in H1, DP, H2 (plane p + 1 in the other)
+  // flags and source of plane p, carried from the iteration that loaded them as plane p + 1
+  uint16_t w_cur = 0;
+  T src_cur[3] = {T(0), T(0), T(0)};
+  const long long splane = (long long)g.nx * g.ny;
   for (int p = zs - 3; p < ze; ++p) {
     const int nxt = cur ^ 1;
     st.stage(g, A.b, p + 3, sm.Sb[s5(p + 3)]);
     st.stage(g, A.d, p + 3, sm.Sd[s5(p + 3)]);
     cp_async_commit();
+    // flags and J of plane p + 1, issued ahead of the waits (J is converted where it is used)
+    const int pp = p + 1;
+    const bool row_in = in_xy && pp >= 0 && pp < g.nz;
+    const long long cn = ((long long)pp * g.ny + y) * g.nx + x;
+    const uint16_t w_next = row_in ? __ldg(A.loc + cn) : (uint16_t)0;
+    double j_next[3] = {0.0, 0.0, 0.0};
+    if (row_in) {
+#pragma unroll
+      for (int al = 0; al < 3; ++al) j_next[al] = __ldg(A.J[al] + cn);
+    }
     cp_async_wait<1>();  // planes up to p + 2 have landed
     __syncthreads();
     // A: h1 at plane p + 1
@@ -402,8 +428,7 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
       T v0 = T(0), v1 = T(0), v2 = T(0);
       const int pp = p + 1;
       if (conv_xy && pp >= 1 && pp <= g.nz - 2) {
-        const long long c = ((long long)pp * g.ny + y) * g.nx + x;
-        const uint16_t w = __ldg(A.loc + c);
+        const uint16_t w = w_next;
         const T zr = (T)pp - A.K.zc;
         const int a = s5(p), b = s5(p + 1), d = s5(p + 2);
         v0 = face_h<0>(A.K, sm.Sb, a, b, d, sm.Sd, a, b, d, tx, ty, xr, yr, zr, exc(w, 3));
@@ -416,19 +441,19 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
     }
     __syncthreads();
     // B: d* at plane p + 1
+    T src_next[3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) src_next[al] = source<T>(A.K, j_next[al]);
     {
-      const int pp = p + 1;
       if (dp_xy && pp >= 0 && pp < g.nz && p >= zs - 2) {
         const Plane3<T, BY>& Dn = sm.Sd[s5(pp)];
         T dv[3] = {Dn.v[0][ty + 1][tx + 1], Dn.v[1][ty + 1][tx + 1], Dn.v[2][ty + 1][tx + 1]};
         if (A.pred) {
-          const long long c = ((long long)pp * g.ny + y) * g.nx + x;
-          const uint16_t w = __ldg(A.loc + c);
           T dv_h[3];
           div_h<T, BY>(sm.H1[nxt], sm.H1[cur], tx, ty, dv_h);
 #pragma unroll
           for (int al = 0; al < 3; ++al)
-            if (adv(w, al)) dv[al] += (source<T>(A.K, A.J[al], c) - dv_h[al]) * half_dx4;
+            if (adv(w_next, al)) dv[al] += (src_next[al] - dv_h[al]) * half_dx4;
         }
         sm.DP[nxt].v[0][ty + 1][tx + 1] = dv[0];
         sm.DP[nxt].v[1][ty + 1][tx + 1] = dv[1];
@@ -440,8 +465,7 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
     if (p >= zs - 1) {
       T v0 = T(0), v1 = T(0), v2 = T(0);
       if (h2_xy && p >= 1 && p <= g.nz - 2) {
-        const long long c = ((long long)p * g.ny + y) * g.nx + x;
-        const uint16_t w = __ldg(A.loc + c);
+        const uint16_t w = w_cur;
         const T zr = (T)p - A.K.zc;
         const int a = s5(p - 1), b = s5(p), d = s5(p + 1);
         v0 = face_h<0>(A.K, sm.Sb, a, b, d, sm.DP, nxt, cur, nxt, tx, ty, xr, yr, zr, exc(w, 3));
@@ -455,18 +479,20 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
     __syncthreads();
     // D: d_out at plane p (h2 of plane p in H2[cur], of plane p - 1 in H2[nxt])
     if (p >= zs && out_xy) {
-      const long long c = ((long long)p * g.ny + y) * g.nx + x;
-      const uint16_t w = __ldg(A.loc + c);
+      const long long c = cn - splane;
       const Plane3<T, BY>& Dc = sm.Sd[s5(p)];
       T dv_h[3];
       div_h<T, BY>(sm.H2[cur], sm.H2[nxt], tx, ty, dv_h);
 #pragma unroll
       for (int al = 0; al < 3; ++al) {
         const T dold = Dc.v[al][ty + 1][tx + 1];
-        A.out[al][c] = adv(w, al) ? dold + (source<T>(A.K, A.J[al], c) - dv_h[al]) * dx4 : dold;
+        A.out[al][c] = adv(w_cur, al) ? dold + (src_cur[al] - dv_h[al]) * dx4 : dold;
       }
     }
     cur = nxt;
+    w_cur = w_next;
+#pragma unroll
+    for (int al = 0; al < 3; ++al) src_cur[al] = src_next[al];
   }
   cp_async_wait<0>();
 }

@@ -18,20 +18,38 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-// Lanes of a warp holding the same key (cell-sorted particles put several in one cell) share one
-// atomic: the lowest of them adds the group's size.  Returns the group; act = the lanes taking part.
-__device__ __forceinline__ unsigned key_peers(unsigned act, uint32_t k) { return __match_any_sync(act, k); }
+// Runs of equal keys in a warp.  Sorted or nearly sorted keys (the store is cell-sorted and particles
+// move less than a cell per step) put equal keys in adjacent lanes; each maximal run of equal keys
+// among the warp's valid lanes (a prefix of the warp) shares one atomic, taken by its first lane.
+// Equal keys in runs that are not adjacent simply take one atomic each.  The run's first lane and
+// its length come from one shuffle and two ballots (all 32 lanes call it).
+struct KeyRun {
+  bool head;  // this lane starts a run
+  int first;  // lane that starts this lane's run
+  int len;    // length of the run (meaningful on its first lane)
+};
+__device__ __forceinline__ KeyRun key_run(bool valid, uint32_t k) {
+  const int lane = threadIdx.x & 31;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, k, 1);
+  KeyRun r;
+  r.head = valid && (lane == 0 || prev != k);
+  const unsigned heads = __ballot_sync(0xffffffffu, r.head);
+  const unsigned upto = heads & (0xffffffffu >> (31 - lane));  // heads at or below this lane
+  r.first = upto ? 31 - __clz(upto) : 0;
+  const unsigned above = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));  // heads above this lane
+  const int next = above ? __ffs(above) - 1 : 32;
+  r.len = min(next, __popc(vmask)) - lane;
+  return r;
+}
 
 __global__ void k_hist(const uint32_t* __restrict__ key, long long n, const int* __restrict__ n_dev,
                        int* __restrict__ counts, long long dead_bin) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool valid = i < n && i < (long long)(*n_dev);
   const uint32_t k = valid ? key[i] : kDead;
-  const unsigned act = __ballot_sync(0xffffffffu, valid);
-  if (!valid) return;
-  const unsigned peers = key_peers(act, k);
-  if ((threadIdx.x & 31) == __ffs(peers) - 1)
-    atomicAdd(counts + (k == kDead ? dead_bin : (long long)k), __popc(peers));
+  const KeyRun r = key_run(valid, k);
+  if (r.head) atomicAdd(counts + (k == kDead ? dead_bin : (long long)k), r.len);
 }
 
 // Inclusive scan of one value per thread across the block.
@@ -118,17 +136,16 @@ template <typename T>
 __global__ void k_scatter(const Particles<T> src, const Particles<T> dst, int* __restrict__ cursor,
                           long long dead_bin) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  bool valid = i < src.n && i < (long long)(*src.n_dev);
-  const uint32_t k = valid ? src.key[i] : kDead;
-  valid = valid && k != kDead;
-  const unsigned act = __ballot_sync(0xffffffffu, valid);
-  if (!valid) return;
-  // one atomic per group of lanes in the same cell; each lane takes its rank in the group
-  const unsigned peers = key_peers(act, k);
-  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  const bool in_range = i < src.n && i < (long long)(*src.n_dev);
+  const uint32_t k = in_range ? src.key[i] : kDead;
+  // one atomic per run of lanes with the same cell, each lane at its rank in the run; removed
+  // particles form runs of their own and take no slot
+  const KeyRun r = key_run(in_range, k);
+  const int lane = threadIdx.x & 31;
   int first = 0;
-  if (lane == leader) first = atomicAdd(cursor + k, __popc(peers));
-  const int pos = __shfl_sync(peers, first, leader) + __popc(peers & ((1u << lane) - 1u));
+  if (r.head && k != kDead) first = atomicAdd(cursor + k, r.len);
+  const int pos = __shfl_sync(0xffffffffu, first, r.first) + (lane - r.first);
+  if (!in_range || k == kDead) return;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     dst.x[q][pos] = src.x[q][i];
@@ -150,9 +167,10 @@ __global__ void k_batch_hist(const InstDesc<T>* __restrict__ desc, const BlockEn
     const SpeciesDesc<T>& S = D.sp[e.inst & 3];
     const Particles<T>& P = S.buf[*S.cur];
     const long long i = (long long)e.block * blockDim.x + threadIdx.x;
-    if (i >= P.n || i >= (long long)(*P.n_dev)) continue;
-    const uint32_t k = P.key[i];
-    atomicAdd(counts + S.bin_base + (k == kDead ? D.g.ncell : (long long)k), 1);
+    const bool valid = i < P.n && i < (long long)(*P.n_dev);
+    const uint32_t k = valid ? P.key[i] : kDead;
+    const KeyRun r = key_run(valid, k);  // the block belongs to one (instance, species): warp-uniform
+    if (r.head) atomicAdd(counts + S.bin_base + (k == kDead ? D.g.ncell : (long long)k), r.len);
   }
 }
 
@@ -177,10 +195,15 @@ __global__ void k_batch_scatter(const InstDesc<T>* __restrict__ desc, const Bloc
     const Particles<T>& src = S.buf[cur];
     const Particles<T>& dst = S.buf[1 - cur];
     const long long i = (long long)e.block * blockDim.x + threadIdx.x;
-    if (i >= src.n || i >= (long long)(*src.n_dev)) continue;
-    const uint32_t k = src.key[i];
-    if (k == kDead) continue;
-    const int pos = atomicAdd(cursor + S.bin_base + k, 1) - base[pair_of_inst[e.inst]];
+    const bool in_range = i < src.n && i < (long long)(*src.n_dev);
+    const uint32_t k = in_range ? src.key[i] : kDead;
+    const KeyRun r = key_run(in_range, k);
+    const int lane = threadIdx.x & 31;
+    int first = 0;
+    if (r.head && k != kDead) first = atomicAdd(cursor + S.bin_base + k, r.len);
+    const int run0 = __shfl_sync(0xffffffffu, first, r.first);  // every lane takes part
+    if (!in_range || k == kDead) continue;
+    const int pos = run0 + (lane - r.first) - base[pair_of_inst[e.inst]];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       dst.x[q][pos] = src.x[q][i];
