@@ -1,5 +1,6 @@
 // Host side of the GRPIC C ABI (include/grpic.h): context lifecycle, memory, the
 // stream-ordered timestep pipeline of Sec. 2.2 (Fig. 1) and the device status word.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1056,7 +1057,16 @@ struct grpic_batch {
   int persist_field_blocks = 0;
   int sms = 1;
   std::vector<long long> pair_n;  // work upper bound of each pair when the batch was built
-  cudaGraphExec_t graph = nullptr;
+  // One captured step per step parity k: every step flips each particle store (the sort) and each d
+  // buffer (the E step), so replaying graph[k] when each context's (store, d) parity equals its
+  // parity at capture XOR k lets the FP32 push run as the single-context kernel per (instance,
+  // species), its buffers and constants plain launch parameters.
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::vector<int> cur0, dcur0;  // parities of the contexts when the graphs were captured
+  // the per-(instance, species) pushes run on kPushBranches parallel branches of the graph
+  static constexpr int kPushBranches = 8;
+  cudaStream_t side[kPushBranches] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kPushBranches] = {};
   cudaEvent_t ev = nullptr;
   long long kernels_per_step = 0;
 };
@@ -1207,14 +1217,60 @@ grpic_status batch_build(grpic_batch* b) {
   return cudaStreamSynchronize(st) == cudaSuccess ? GRPIC_OK : GRPIC_ERR_CUDA;
 }
 
+// The FP32-mixed push of a batched step at step parity k (see grpic_batch): per (instance,
+// species), the single-context per-warp select kernel over the store the step reads, with the d
+// buffer of the step and b^n (the other b buffer, written by the first B half-step).
+// The items are spread over the batch's parallel branches, largest first, each to the branch with
+// the fewest particles so far, so that small instances run beside large ones.
+void batch_enqueue_push_items(grpic_batch* b, int k) {
+  struct Item {
+    size_t inst;
+    int s;
+    long long n;
+  };
+  std::vector<Item> items;
+  for (size_t i = 0; i < b->ctxs.size(); ++i)
+    for (int s = 0; s < kMaxSpecies; ++s)
+      if (b->ctxs[i]->sp[s].loaded && b->ctxs[i]->sp[s].n > 0) items.push_back(Item{i, s, b->ctxs[i]->sp[s].n});
+  std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.n > y.n; });
+  cudaEventRecord(b->ev_fork, b->stream);
+  long long load[grpic_batch::kPushBranches] = {};
+  for (int br = 0; br < grpic_batch::kPushBranches; ++br) cudaStreamWaitEvent(b->side[br], b->ev_fork, 0);
+  for (const Item& it : items) {
+    int br = 0;
+    for (int q = 1; q < grpic_batch::kPushBranches; ++q)
+      if (load[q] < load[br]) br = q;
+    load[br] += it.n;
+    grpic_ctx* c = b->ctxs[it.inst];
+    Fields<float> F;
+    for (int q = 0; q < 3; ++q) {
+      F.d[q] = field_plane<float>(c, false, b->dcur0[it.inst] ^ k, q);
+      F.b[q] = field_plane<float>(c, true, 1 - c->bcur, q);
+      F.J[q] = c->J + (size_t)q * c->g.ncell;
+    }
+    SpeciesStore& S = c->sp[it.s];
+    const Particles<float> P = particles_view<float>(c, it.s, b->cur0[4 * it.inst + it.s] ^ k);
+    launch_push_select(c->g, F, P, Species{S.qm, S.qmacro}, c->st, c->tune.far_min_blocks, false, c->tune.spread,
+                       b->side[br]);
+  }
+  for (int br = 0; br < grpic_batch::kPushBranches; ++br) {
+    cudaEventRecord(b->ev_join[br], b->side[br]);
+    cudaStreamWaitEvent(b->stream, b->ev_join[br], 0);
+  }
+}
+
 // One batched timestep (Sec. 2.2 for every instance): B half, J = 0, push + deposit, B half, E,
-// removal + sort.  Each stage is one launch over all instances.
+// removal + sort.  Each field and sort stage is one launch over all instances; the FP32-mixed push
+// launches per (instance, species).
 template <typename T>
-void batch_enqueue_step(grpic_batch* b) {
+void batch_enqueue_step(grpic_batch* b, int k) {
   const BatchTables<T> t = batch_tables<T>(b);
   launch_batch_b_half<T>(t, 0, b->literal, b->stream);
   launch_batch_zero_j<T>(t, b->stream);
-  launch_batch_push<T>(t, b->quad, b->stream);
+  if constexpr (sizeof(T) == sizeof(float))
+    batch_enqueue_push_items(b, k);
+  else
+    launch_batch_push<T>(t, b->quad, b->stream);
   launch_batch_b_half<T>(t, 1, b->literal, b->stream);
   launch_batch_e_step<T>(t, b->literal, b->stream);
   launch_batch_flip_d<T>(t, (int)b->ctxs.size(), b->stream);
@@ -1247,8 +1303,13 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
   b->sms = std::max(1, sms);
   b->persist_blocks = b->sms * 8;
   b->persist_field_blocks = b->sms * 2;
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int br = 0; br < grpic_batch::kPushBranches && ok; ++br)
+    ok = cudaStreamCreateWithFlags(&b->side[br], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join[br], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     grpic_batch_destroy(b);
     return GRPIC_ERR_CUDA;
   }
@@ -1258,8 +1319,10 @@ grpic_status grpic_batch_create(grpic_ctx* const* ctxs, int n, void* stream, grp
     grpic_batch_destroy(b);
     return s;
   }
-  // kernels per step: B halves 2, zero J 1, push 1, E 1, d parity 1, sort 5 (+2 with particles; and 1 memset)
-  b->kernels_per_step = 2 + 1 + (b->npart > 0 ? 1 : 0) + 1 + 1 + (b->npairs ? 5 + 2 * (b->npart > 0 ? 1 : 0) : 0);
+  // kernels per step: B halves 2, zero J 1, push (FP32-mixed: one per pair; FP64: 1), E 1, d parity 1,
+  // sort 5 (+2 with particles; and 1 memset)
+  const int push_launches = b->npart > 0 ? (b->mixed ? b->npairs : 1) : 0;
+  b->kernels_per_step = 2 + 1 + push_launches + 1 + 1 + (b->npairs ? 5 + 2 * (b->npart > 0 ? 1 : 0) : 0);
   *out = b;
   return GRPIC_OK;
 }
@@ -1283,20 +1346,44 @@ grpic_status grpic_batch_step(grpic_batch* b, int nsteps) {
   std::vector<int> dpar(b->ctxs.size(), 0);
   for (size_t i = 0; i < b->ctxs.size(); ++i) dpar[i] = b->ctxs[i]->dcur;
   cudaMemcpyAsync(b->dcur, dpar.data(), sizeof(int) * dpar.size(), cudaMemcpyHostToDevice, b->stream);
-  if (!b->graph) {
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GRPIC_ERR_CUDA;
-    if (b->mixed)
-      batch_enqueue_step<float>(b);
-    else
-      batch_enqueue_step<double>(b);
-    if (cudaStreamEndCapture(b->stream, &graph) != cudaSuccess || !graph) return GRPIC_ERR_CUDA;
-    const cudaError_t e = cudaGraphInstantiate(&b->graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return GRPIC_ERR_CUDA;
+  // the step parity of the contexts relative to the captured graphs (recaptured when a context
+  // was stepped on its own so that its parities no longer follow the batch's)
+  int k = -1;
+  if (b->graph[0] && b->graph[1]) {
+    for (int kk = 0; kk < 2 && k < 0; ++kk) {
+      bool ok = true;
+      for (size_t i = 0; i < b->ctxs.size() && ok; ++i) {
+        ok = b->ctxs[i]->dcur == (b->dcur0[i] ^ kk);
+        for (int s = 0; s < kMaxSpecies && ok; ++s)
+          if (b->ctxs[i]->sp[s].loaded) ok = b->ctxs[i]->sp[s].cur == (b->cur0[4 * i + s] ^ kk);
+      }
+      if (ok) k = kk;
+    }
   }
-  for (int k = 0; k < nsteps; ++k)
-    if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
+  if (k < 0) {
+    for (int kk = 0; kk < 2; ++kk)
+      if (b->graph[kk]) {
+        cudaGraphExecDestroy(b->graph[kk]);
+        b->graph[kk] = nullptr;
+      }
+    b->cur0 = cur;
+    b->dcur0 = dpar;
+    for (int kk = 0; kk < 2; ++kk) {
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GRPIC_ERR_CUDA;
+      if (b->mixed)
+        batch_enqueue_step<float>(b, kk);
+      else
+        batch_enqueue_step<double>(b, kk);
+      if (cudaStreamEndCapture(b->stream, &graph) != cudaSuccess || !graph) return GRPIC_ERR_CUDA;
+      const cudaError_t e = cudaGraphInstantiate(&b->graph[kk], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return GRPIC_ERR_CUDA;
+    }
+    k = 0;
+  }
+  for (int j = 0; j < nsteps; ++j)
+    if (cudaGraphLaunch(b->graph[(k + j) & 1], b->stream) != cudaSuccess) return GRPIC_ERR_CUDA;
   cudaMemcpyAsync(cur.data(), b->cur, sizeof(int) * cur.size(), cudaMemcpyDeviceToHost, b->stream);
   std::vector<int> dcur(b->ctxs.size(), 0);
   cudaMemcpyAsync(dcur.data(), b->dcur, sizeof(int) * dcur.size(), cudaMemcpyDeviceToHost, b->stream);
@@ -1330,10 +1417,11 @@ grpic_status grpic_batch_set_blocks_per_sm(grpic_batch* b, int blocks_per_sm) {
   if (b->persist_blocks == b->sms * blocks_per_sm) return GRPIC_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
   b->persist_blocks = b->sms * blocks_per_sm;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;  // re-captured with the new grid by the next grpic_batch_step
-  }
+  for (int kk = 0; kk < 2; ++kk)
+    if (b->graph[kk]) {
+      cudaGraphExecDestroy(b->graph[kk]);
+      b->graph[kk] = nullptr;  // re-captured with the new grid by the next grpic_batch_step
+    }
   return GRPIC_OK;
 }
 
@@ -1347,9 +1435,15 @@ grpic_status grpic_batch_info(grpic_batch* b, int64_t* kernels_per_step, int64_t
 grpic_status grpic_batch_destroy(grpic_batch* b) {
   if (!b) return GRPIC_ERR_INVALID;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int kk = 0; kk < 2; ++kk)
+    if (b->graph[kk]) cudaGraphExecDestroy(b->graph[kk]);
   for (void* p : b->allocs) batch_free(b, p);
   if (b->ev) cudaEventDestroy(b->ev);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int br = 0; br < grpic_batch::kPushBranches; ++br) {
+    if (b->ev_join[br]) cudaEventDestroy(b->ev_join[br]);
+    if (b->side[br]) cudaStreamDestroy(b->side[br]);
+  }
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return GRPIC_OK;
