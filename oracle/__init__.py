@@ -50,7 +50,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("m", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
                 ("dt", ctypes.c_double), ("quad_order", ctypes.c_int),
-                ("r_excise", ctypes.c_double), ("flags", ctypes.c_uint), ("threads", ctypes.c_int)]
+                ("r_excise", ctypes.c_double), ("flags", ctypes.c_uint), ("threads", ctypes.c_int),
+                ("absorb_inner", ctypes.c_double), ("absorb_outer", ctypes.c_double), ("absorb_width", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -84,6 +85,8 @@ def lib():
                 "orc_destroy": (None, [_V]),
                 "orc_r_plus": (ctypes.c_double, [_V]),
                 "orc_set_fields": (ctypes.c_int, [_V, _D, _D]),
+                "orc_set_absorb_target": (ctypes.c_int, [_V, _D, _D]),
+                "orc_absorb_kappa": (ctypes.c_double, [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_set_j": (ctypes.c_int, [_V, _D]),
                 "orc_get_fields": (ctypes.c_int, [_V, _D, _D, _D]),
                 "orc_init_uniform_field": (ctypes.c_int, [_V, _D, _D]),
@@ -241,15 +244,18 @@ class OracleError(RuntimeError):
 class Oracle:
     """One oracle simulation context (grid, metric, fields, particles)."""
 
-    def __init__(self, nx, ny, nz, m, a, c, dt, quad_order=2, r_excise=0.0, flags=0, threads=1):
+    def __init__(self, nx, ny, nz, m, a, c, dt, quad_order=2, r_excise=0.0, flags=0, threads=1, absorb_inner=0.0,
+                 absorb_outer=0.0, absorb_width=0):
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
-        cfg = _Cfg(nx, ny, nz, m, a, c, dt, quad_order, r_excise, flags, threads)
+        cfg = _Cfg(nx, ny, nz, m, a, c, dt, quad_order, r_excise, flags, threads, absorb_inner, absorb_outer,
+                   absorb_width)
         self._h = lib().orc_create(ctypes.byref(cfg))
         if not self._h:
             raise ValueError("invalid oracle configuration")
         self.cfg = dict(nx=nx, ny=ny, nz=nz, m=m, a=a, c=c, dt=dt, quad_order=quad_order,
-                        r_excise=r_excise, flags=flags, threads=threads)
+                        r_excise=r_excise, flags=flags, threads=threads, absorb_inner=absorb_inner,
+                        absorb_outer=absorb_outer, absorb_width=absorb_width)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -278,6 +284,16 @@ class Oracle:
         d = _f64(d, (3,) + self.shape)
         b = _f64(b, (3,) + self.shape)
         self._chk(lib().orc_set_fields(self._h, _dp(d), _dp(b)), "set_fields")
+
+    def set_absorb_target(self, d, b):
+        """Replace the absorbing layers' target (reading A22; by default the field as last set)."""
+        d = _f64(d, (3,) + self.shape)
+        b = _f64(b, (3,) + self.shape)
+        self._chk(lib().orc_set_absorb_target(self._h, _dp(d), _dp(b)), "set_absorb_target")
+
+    def absorb_kappa(self, comp, i, j, k):
+        """Relaxation per step of the absorbing layers at component comp's point (i, j, k) (A22)."""
+        return lib().orc_absorb_kappa(self._h, int(comp), int(i), int(j), int(k))
 
     def set_j(self, J):
         J = _f64(J, (3,) + self.shape)

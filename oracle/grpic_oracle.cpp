@@ -57,6 +57,14 @@
  *       h on d (the shift terms), and evaluating them at each half-step's own start value
  *       (ORC_LITERAL_HALF_STEPS) is a forward-Euler step of a centred advection term, which grows
  *       without bound near the horizon.
+ *   A22 Absorbing layers (optional; off unless absorb_inner or absorb_outer > 0; the paper states
+ *       no boundary condition).  After the second B half-step and the E step every advanced
+ *       point takes F0 + (1 - kappa)(F - F0), F0 the field as last set, kappa the larger of an
+ *       inner layer's absorb_inner (r_+ - r)/(r_+ - r_excise) for r_excise <= r < r_+ (r_excise
+ *       defaulting to r_+/2 then) and an outer layer's absorb_outer ((W + 1 - s)/W)^2 over the
+ *       W cells next to the frozen faces (s = 1 at the first advanced cell).  Held fields reflect;
+ *       with a rapidly rotating hole, reflection inside the horizon feeds a mode growing next to
+ *       it, and frozen faces where the metric is far from flat feed one at the box edges.
  *
  * Parity status: every function is pinned by a CPU test against closed forms, invariants
  * or brute force.  The RK4 steps exactly as printed in Sec. 3.3 have no consistent reading
@@ -444,9 +452,11 @@ typedef struct {
   int nx, ny, nz;
   double m, a, c, dt;
   int quad_order;
-  double r_excise;  // <= 0: r_+
+  double r_excise;  // <= 0: r_+ (r_+/2 with an inner absorbing layer)
   unsigned flags;
   int threads;  // <= 0: all available
+  double absorb_inner, absorb_outer;  // A22: relaxation per step at the layers' deepest points (0: none)
+  int absorb_width;                   // outer layer width in cells (<= 0: 8)
 } orc_config;
 
 }  // extern "C"
@@ -463,6 +473,9 @@ struct Ctx {
   size_t ncell = 0;
   std::vector<double> F[6];
   std::vector<double> Fprev[3];  // b^{n-1/2} kept by the first B half-step (A21)
+  std::vector<double> F0[6];     // target of the absorbing layers (A22), kept only with layers
+  double r_abs = 0.0;            // outer radius of the inner absorbing layer (r_+)
+  int w_out = 8;                 // outer absorbing layer width
   std::vector<double> J[3];
   std::vector<Species> sp;
   std::vector<double> glx, glw;
@@ -556,6 +569,50 @@ struct Ctx {
 
   bool literal() const { return (cfg.flags & ORC_LITERAL_HALF_STEPS) != 0; }
 
+  // --- A22: absorbing layers -----------------------------------------------------------------
+  bool layers() const { return cfg.absorb_inner > 0.0 || cfg.absorb_outer > 0.0; }
+
+  // The fields just set become the layers' target.
+  void snapshot_target() {
+    if (!layers()) return;
+    for (int c = 0; c < 6; ++c) F0[c] = F[c];
+  }
+
+  // Relaxation per step at the lattice point (i,j,k) of component c: the larger of the inner
+  // layer's absorb_inner (r_abs - r) / (r_abs - r_exc) for r_exc <= r < r_abs and the outer
+  // layer's absorb_outer ((W + 1 - s) / W)^2 for s <= W, where s - 1 counts the cells between the
+  // point's cell and the outer two (frozen) index layers along the nearest axis direction.
+  double absorb_kappa(int c, int i, int j, int k) const {
+    double kap = 0.0;
+    if (cfg.absorb_outer > 0.0) {
+      const int id3[3] = {i, j, k};
+      int s = n[0];
+      for (int ax = 0; ax < 3; ++ax) s = std::min(s, 1 + std::min(id3[ax] - 2, n[ax] - 3 - id3[ax]));
+      if (s >= 1 && s <= w_out) {
+        const double u = double(w_out + 1 - s) / double(w_out);
+        kap = cfg.absorb_outer * u * u;
+      }
+    }
+    if (cfg.absorb_inner > 0.0 && r_abs > r_exc) {
+      double pos[3], X[3];
+      loc(c, i, j, k, pos);
+      rel(pos, X);
+      const KerrFK<double> kf = kerr_fk<double>(X, cfg.m, cfg.a);
+      if (!kf.flat && kf.r >= r_exc && kf.r < r_abs)
+        kap = std::max(kap, cfg.absorb_inner * (r_abs - kf.r) / (r_abs - r_exc));
+    }
+    return kap;
+  }
+
+  // v <- F0 + (1 - kappa)(v - F0) at an advanced point of component c.
+  void relax(int c, int i, int j, int k, double& v) const {
+    const double kap = absorb_kappa(c, i, j, k);
+    if (kap > 0.0) {
+      const double t = F0[c][idx(i, j, k)];
+      v = t + (1.0 - kap) * (v - t);
+    }
+  }
+
   // --- Sec. 3.1: magnetic half-steps (Eqs. 9-10, time levels A21) --------------------------
   // which = 0: first half-step (b^{n-1/2} -> b^n), 1: second half-step (-> b^{n+1/2}).
   void b_half(int which) {
@@ -602,6 +659,7 @@ struct Ctx {
               F[3 + q][id] -= (t1 + t2) * dx4 / 2.0;
             else
               F[3 + q][id] = Fprev[q][id] - (t1 + t2) * dx4;
+            if (which == 1 && layers()) relax(3 + q, i, j, k, F[3 + q][id]);
           }
     }
   }
@@ -693,6 +751,15 @@ struct Ctx {
       for (int al = 0; al < 3; ++al) F[al].swap(dn[al]);
     }
     e_update(h, dx4, newd);
+    if (layers())
+      for (int al = 0; al < 3; ++al)
+        for (int k = 2; k <= n[2] - 3; ++k)
+          for (int j = 2; j <= n[1] - 3; ++j)
+            for (int i = 2; i <= n[0] - 3; ++i) {
+              double pos[3];
+              loc(al, i, j, k, pos);
+              if (!excised(pos)) relax(al, i, j, k, newd[al][idx(i, j, k)]);
+            }
     for (int al = 0; al < 3; ++al) F[al].swap(newd[al]);
   }
 
@@ -1265,9 +1332,18 @@ void* orc_create(const orc_config* cfg) {
   ctx->n[2] = cfg->nz;
   for (int ax = 0; ax < 3; ++ax) ctx->Xc[ax] = 0.5 * (ctx->n[ax] - 1);
   ctx->r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
-  ctx->r_exc = cfg->r_excise > 0 ? cfg->r_excise : ctx->r_plus;
+  if (!(cfg->absorb_inner >= 0.0 && cfg->absorb_inner <= 1.0 && cfg->absorb_outer >= 0.0 &&
+        cfg->absorb_outer <= 1.0)) {
+    delete ctx;
+    return nullptr;
+  }
+  ctx->r_exc = cfg->r_excise > 0 ? cfg->r_excise : (cfg->absorb_inner > 0.0 ? 0.5 : 1.0) * ctx->r_plus;
+  ctx->r_abs = ctx->r_plus;
+  ctx->w_out = cfg->absorb_width > 0 ? cfg->absorb_width : 8;
   ctx->ncell = (size_t)cfg->nx * cfg->ny * cfg->nz;
   for (auto& f : ctx->F) f.assign(ctx->ncell, 0.0);
+  if (ctx->layers())
+    for (auto& f : ctx->F0) f.assign(ctx->ncell, 0.0);
   for (auto& j : ctx->J) j.assign(ctx->ncell, 0.0);
   gauss_legendre(cfg->quad_order, ctx->glx, ctx->glw);
   return ctx;
@@ -1283,7 +1359,24 @@ int orc_set_fields(void* p, const double* d3, const double* b3) {
     std::memcpy(ctx->F[q].data(), d3 + q * ctx->ncell, ctx->ncell * sizeof(double));
     std::memcpy(ctx->F[3 + q].data(), b3 + q * ctx->ncell, ctx->ncell * sizeof(double));
   }
+  ctx->snapshot_target();
   return ORC_OK;
+}
+
+// Replace the absorbing layers' target (A22) without touching the fields.
+int orc_set_absorb_target(void* p, const double* d3, const double* b3) {
+  Ctx* ctx = static_cast<Ctx*>(p);
+  if (!ctx->layers()) return ORC_ERR_INVALID;
+  for (int q = 0; q < 3; ++q) {
+    std::memcpy(ctx->F0[q].data(), d3 + q * ctx->ncell, ctx->ncell * sizeof(double));
+    std::memcpy(ctx->F0[3 + q].data(), b3 + q * ctx->ncell, ctx->ncell * sizeof(double));
+  }
+  return ORC_OK;
+}
+
+// Relaxation per step of the absorbing layers at component c's lattice point (i, j, k) (A22).
+double orc_absorb_kappa(void* p, int c, int i, int j, int k) {
+  return static_cast<Ctx*>(p)->absorb_kappa(c, i, j, k);
 }
 
 int orc_set_j(void* p, const double* J3) {
@@ -1326,6 +1419,7 @@ int orc_init_uniform_field(void* p, const double* E3, const double* B3) {
           }
           ctx->F[c][ctx->idx(i, j, k)] = v;
         }
+  ctx->snapshot_target();
   return ORC_OK;
 }
 
@@ -1341,6 +1435,7 @@ int orc_init_wald(void* p, double B0) {
           wald_field(X, ctx->cfg.m, ctx->cfg.a, B0, Fd, Fu);
           ctx->F[c][ctx->idx(i, j, k)] = (c < 3) ? Fu[c][3] : Fd[kPair[c - 3][0]][kPair[c - 3][1]];
         }
+  ctx->snapshot_target();
   return ORC_OK;
 }
 
