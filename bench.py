@@ -569,7 +569,9 @@ def run_disk(args, dist):
     build()
     wl = synth_disk.kerr_disk_corona(n=args.grid if args.grid != 128 else 384, seed=3)
     npart = wl.n_particles
-    sim = Simulation(wl.n, wl.n, wl.n, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", quad_order=args.quad)
+    layers = dict(wl.layers)
+    sim = Simulation(wl.n, wl.n, wl.n, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", quad_order=args.quad,
+                     **layers)
     sim.set_tuning(sort_interval=args.sort_interval)
     sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
     for s, sp in enumerate(wl.species):
@@ -596,6 +598,7 @@ def run_disk(args, dist):
             "config": {"workload": f"kerr_disk_corona_{geo['n']}: Kerr a=0.95m, m={geo['m']:g} cells, {geo['n']}^3, "
                                    "Keplerian disk (|z|<0.1 r_cyl, 6m..150 cells, density ~1/r) in a 1% corona, "
                                    "e-/ion (mass ratio 20), B_z=0.1, dt=0.4",
+                       "absorbing_layers": layers,
                        "particles": npart, "inner_edge_particles_per_cell": geo["n0"],
                        "sort_interval": args.sort_interval},
             "gpu_launches": int(launches),

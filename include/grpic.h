@@ -92,6 +92,16 @@ enum {
   GRPIC_STAGE_B_HALF2 = 5       /* Sec. 3.1, Eq. 10: second B half-step */
 };
 
+/* Absorbing layers (the paper states no boundary condition for the fields).  Without them the
+ * outer two index layers and the inside of r_excise are held at their values, which reflects
+ * waves; with a rapidly rotating hole that reflection inside the horizon feeds a mode that grows
+ * next to it, and where the metric at the box faces is far from flat the frozen faces feed one
+ * there.  A layer relaxes the field toward a target: after the second B half-step and the E step
+ * every advanced location with relaxation kappa > 0 takes F0 + (1 - kappa)(F - F0), kappa the
+ * larger of the two layers' values there (r in FP64 at the location; s = the cell's distance in
+ * cells to the nearest frozen layer, 1 for the first advanced cell).  The target F0 is the field
+ * of the last grpic_set_fields / grpic_set_uniform_field call (zero before the first).  The inner
+ * layer lies inside the horizon, so it acts on nothing that can reach the outside. */
 typedef void* (*grpic_alloc_fn)(size_t bytes, void* user);
 typedef void (*grpic_free_fn)(void* ptr, void* user);
 
@@ -110,6 +120,12 @@ typedef struct {
   double fp64_radius;    /* FP32_MIXED: where the FP32 estimate of r is below fp64_radius * m, the quartic,
                             the metric and the Christoffel contraction are evaluated in FP64 (0 -> 4;
                             negative -> never) */
+  double absorb_inner;   /* absorbing layer inside the horizon (see below): relaxation per step at
+                            r = r_excise, falling linearly to 0 at r = r_+; 0 -> none.  With it,
+                            r_excise <= 0 means r_+/2.  In [0, 1] */
+  double absorb_outer;   /* absorbing layer at the box faces: relaxation per step at the first advanced
+                            cell, falling as ((W + 1 - s) / W)^2 to the s = W-th; 0 -> none.  In [0, 1] */
+  int absorb_width;      /* W, in cells (<= 0 -> 8) */
   grpic_alloc_fn alloc;  /* device allocator (NULL -> cudaMalloc); e.g. a PyTorch caching allocator */
   grpic_free_fn free_fn; /* matching free */
   void* alloc_user;      /* passed to alloc / free_fn */
@@ -391,8 +407,9 @@ grpic_status grpic_server_create(size_t hbm_budget, int max_slots, grpic_alloc_f
  * grid whose faces lie where the metric is far from flat, f = 2m / R_face > 0.2 with R_face =
  * (min(nx, ny, nz) - 1) / 2: there the field update with its frozen outer layers (reading of the
  * paper's silent boundaries) grows a mode at the box edges, whatever the timestep, which after
- * ~100 steps accelerates the plasma past the one-cell step limit.  Short runs on such grids and
- * every run on larger grids are admitted. */
+ * ~100 steps accelerates the plasma past the one-cell step limit.  Short runs on such grids, runs
+ * whose configuration has an outer absorbing layer (absorb_outer > 0) and every run on larger
+ * grids are admitted. */
 grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* ticket);
 
 /* Admit what fits, advance every running run one timestep, retire finished runs.  A run whose

@@ -43,6 +43,10 @@ struct Grid {
   // field-step constants, formed once on the host in both precisions: dx^4 = c dt and 4 pi / c
   double dx4, four_pi_c;
   float dx4_f, four_pi_c_f;
+  // absorbing layers: inner relaxation k_in from r_exc (falling to 0 at r_abs = r_+), outer k_out over
+  // w_out cells; 0 -> no layer
+  double k_in, k_out, r_abs;
+  int w_out;
 };
 
 template <typename T>
@@ -62,13 +66,17 @@ struct Fields {
   double* J[3];
 };
 
-// Both buffers of the field ping-pong pairs and the per-cell location flags (bit l: location l
-// advanced; bit 8 + l: location l excised).  The field updates write the other buffer.
+// Both buffers of the field ping-pong pairs, the target of the absorbing layers (d planes 0-2, b
+// planes 3-5; null without layers) and the per-cell location flags (bit l: location l advanced;
+// bit 6: an advanced location of the cell lies in an absorbing layer; bit 8 + l: location l
+// excised).  The field updates write the other buffer.
+constexpr unsigned kLayerBit = 1u << 6;
 template <typename T>
 struct FieldStore {
   T* d[2][3];
   T* b[2][3];
   double* J[3];
+  const T* tgt[6];
   const uint16_t* loc;
 };
 
@@ -95,13 +103,15 @@ __host__ __device__ inline FieldConsts<T> field_consts(const Grid& g) {
 }
 
 // B half-step: b_out = b_base - coef curl e(b_src, d) at advanced face locations, b_base copied
-// elsewhere (not written when inplace: b_out == b_base).
+// elsewhere (not written when inplace: b_out == b_base); relaxed toward tgt in the absorbing
+// layers when tgt is set (the second half-step).
 template <typename T>
 struct BStepArgs {
   const T* src[3];
   const T* base[3];
   T* out[3];
   const T* d[3];
+  const T* tgt[3];
   const uint16_t* loc;
   FieldConsts<T> K;
   T coef;
@@ -109,12 +119,14 @@ struct BStepArgs {
 };
 
 // E step: d_out = d + dx4 (4 pi/c J - div h(b, d*)) at advanced edge locations, d copied
-// elsewhere; d* = d + (dx4/2)(4 pi/c J - div h(b, d)) with pred, else d.
+// elsewhere; d* = d + (dx4/2)(4 pi/c J - div h(b, d)) with pred, else d.  Relaxed toward tgt in
+// the absorbing layers when tgt is set.
 template <typename T>
 struct EStepArgs {
   const T* b[3];
   const T* d[3];
   T* out[3];
+  const T* tgt[3];
   const double* J[3];
   const uint16_t* loc;
   FieldConsts<T> K;

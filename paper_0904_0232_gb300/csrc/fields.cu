@@ -195,6 +195,39 @@ __device__ __forceinline__ T source(const FieldConsts<T>& K, double J) {
 
 __device__ __forceinline__ bool adv(uint16_t w, int l) { return (w >> l) & 1u; }
 __device__ __forceinline__ bool exc(uint16_t w, int l) { return (w >> (8 + l)) & 1u; }
+__device__ __forceinline__ bool in_layer(uint16_t w) { return (w & kLayerBit) != 0u; }
+
+// ---- absorbing layers -------------------------------------------------------------------------
+// Relaxation per step at location l of cell (i, j, k): the larger of the inner layer's
+// k_in (r_abs - r) / (r_abs - r_exc) where r_exc <= r < r_abs (r at the location, in FP64) and the
+// outer layer's k_out ((W + 1 - s) / W)^2 where s <= W, s being 1 + the cell's distance in cells to
+// the outer two index layers (s = 1 at the first advanced cell).
+__device__ inline double absorb_kappa(const Grid& g, int l, int i, int j, int k) {
+  double kap = 0.0;
+  if (g.k_out > 0.0) {
+    const int s = 1 + min(min(min(i - 2, g.nx - 3 - i), min(j - 2, g.ny - 3 - j)), min(k - 2, g.nz - 3 - k));
+    if (s >= 1 && s <= g.w_out) {
+      const double u = (double)(g.w_out + 1 - s) / (double)g.w_out;
+      kap = g.k_out * u * u;
+    }
+  }
+  if (g.k_in > 0.0 && g.r_abs > g.r_exc) {
+    const double X = i + 0.5 * half(l, 0) - g.xc;
+    const double Y = j + 0.5 * half(l, 1) - g.yc;
+    const double Z = k + 0.5 * half(l, 2) - g.zc;
+    const Kerr<double> K = kerr_eval<double>(X, Y, Z, g.m, g.a);
+    if (!K.flat && K.r >= g.r_exc && K.r < g.r_abs)
+      kap = fmax(kap, g.k_in * (g.r_abs - K.r) / (g.r_abs - g.r_exc));
+  }
+  return kap;
+}
+
+// v relaxed toward the target t at location l of cell (i, j, k): t + (1 - kappa)(v - t).
+template <typename T>
+__device__ __forceinline__ T relax(const Grid& g, T t, T v, int l, int i, int j, int k) {
+  const T keep = (T)(1.0 - absorb_kappa(g, l, i, j, k));
+  return t + keep * (v - t);
+}
 
 // Asynchronous 4- or 8-byte copy global -> shared (zero-filled when ok is false: no bytes are read
 // then, and src is only a valid address), and the commit / wait of the thread's copy groups.
@@ -339,10 +372,13 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
       for (int q = 0; q < 3; ++q) {
         // b at the cell: the staged b^n when the base is the source, else the other buffer
         const T old = A.inplace ? base_old[q] : sm.Sb[sb(p)].v[q][ty + 1][tx + 1];
-        if (adv(w, 3 + q))
-          A.out[q][c] = old - A.coef * cu[q];
-        else if (!A.inplace)
+        if (adv(w, 3 + q)) {
+          T v = old - A.coef * cu[q];
+          if (A.tgt[0] && in_layer(w)) v = relax<T>(g, A.tgt[q][c], v, 3 + q, x, y, p);
+          A.out[q][c] = v;
+        } else if (!A.inplace) {
           A.out[q][c] = old;
+        }
       }
     }
     w_prev = w_cur;
@@ -486,7 +522,12 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
 #pragma unroll
       for (int al = 0; al < 3; ++al) {
         const T dold = Dc.v[al][ty + 1][tx + 1];
-        A.out[al][c] = adv(w_cur, al) ? dold + (src_cur[al] - dv_h[al]) * dx4 : dold;
+        T v = dold;
+        if (adv(w_cur, al)) {
+          v = dold + (src_cur[al] - dv_h[al]) * dx4;
+          if (A.tgt[0] && in_layer(w_cur)) v = relax<T>(g, A.tgt[al][c], v, al, x, y, p);
+        }
+        A.out[al][c] = v;
       }
     }
     cur = nxt;
@@ -580,6 +621,7 @@ __device__ __forceinline__ BStepArgs<T> batch_b_args(const InstDesc<T>& D, int w
       A.out[q] = D.FS.b[0][q];
     }
   }
+  for (int q = 0; q < 3; ++q) A.tgt[q] = which == 1 ? D.FS.tgt[3 + q] : nullptr;
   A.loc = D.FS.loc;
   A.coef = (which == 1 && !literal) ? dx4 : dx4 * T(0.5);
   A.inplace = which == 1 && !literal;
@@ -596,6 +638,7 @@ __device__ __forceinline__ EStepArgs<T> batch_e_args(const InstDesc<T>& D, bool 
     A.d[q] = D.FS.d[dc][q];
     A.out[q] = D.FS.d[dc ^ 1][q];
     A.J[q] = D.FS.J[q];
+    A.tgt[q] = D.FS.tgt[q];
   }
   A.loc = D.FS.loc;
   A.pred = !literal;
@@ -654,9 +697,9 @@ __global__ void k_batch_flip_d(const InstDesc<T>* __restrict__ desc, int n) {
 }
 
 // ---- location flags --------------------------------------------------------------------------
-// bit l: location l of the cell is advanced (cell in [2, n-3]^3 and r >= r_excise); bit 8 + l:
-// location l is excised (r < r_excise, or r = 0), where conversions take the flat metric.
-// Decided once, in FP64.
+// bit l: location l of the cell is advanced (cell in [2, n-3]^3 and r >= r_excise); bit 6: an
+// advanced location of the cell has a relaxation kappa > 0; bit 8 + l: location l is excised
+// (r < r_excise, or r = 0), where conversions take the flat metric.  Decided once, in FP64.
 __global__ void k_location_flags(const Grid g, uint16_t* __restrict__ loc) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
@@ -673,7 +716,10 @@ __global__ void k_location_flags(const Grid g, uint16_t* __restrict__ loc) {
     const Kerr<double> K = kerr_eval<double>(X, Y, Z, g.m, g.a);
     const bool excised = K.flat || K.r < g.r_exc;
     if (excised) w |= 1u << (8 + l);
-    if (inner && !excised) w |= 1u << l;
+    if (inner && !excised) {
+      w |= 1u << l;
+      if (absorb_kappa(g, l, i, j, k) > 0.0) w |= kLayerBit;
+    }
   }
   loc[c] = (uint16_t)w;
 }

@@ -50,6 +50,7 @@ struct grpic_ctx {
   int sms = 0;
   grpic_tuning tune{4, 4, 1, 1, 0, 0, 1};
   void* fields = nullptr;  // 12 planes of T: d buffers 0 and 1 (3 planes each), b buffers 0 and 1
+  void* tgt = nullptr;     // absorbing layers: 6 planes of T, the target d and b (null without layers)
   double* J = nullptr;     // 3 planes
   uint16_t* loc = nullptr;  // per-cell location flags
   // field ping-pong state: buffer of the current d and b; bprev: buffer holding b^{n-1/2} after the
@@ -118,6 +119,22 @@ size_t particle_bytes(const grpic_ctx* c) { return 8 * c->tsize + 2 * sizeof(uin
 template <typename T>
 T* field_plane(grpic_ctx* c, bool is_b, int buf, int q) {
   return static_cast<T*>(c->fields) + (size_t)((is_b ? 6 : 0) + 3 * buf + q) * c->g.ncell;
+}
+
+// Plane q of the absorbing layers' target (0-2: d, 3-5: b), or null without layers.
+template <typename T>
+T* target_plane(grpic_ctx* c, int q) {
+  return c->tgt ? static_cast<T*>(c->tgt) + (size_t)q * c->g.ncell : nullptr;
+}
+
+// The current d and b become the absorbing layers' target.
+void snapshot_target(grpic_ctx* c) {
+  if (!c->tgt) return;
+  const size_t bytes = 3 * (size_t)c->g.ncell * c->tsize;
+  char* t = static_cast<char*>(c->tgt);
+  const char* f = static_cast<const char*>(c->fields);
+  cudaMemcpyAsync(t, f + (size_t)c->dcur * bytes, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(t + bytes, f + (size_t)(2 + c->bcur) * bytes, bytes, cudaMemcpyDeviceToDevice, c->stream);
 }
 
 // The current field state (what the push, the diagnostics and get/set_fields see).
@@ -266,6 +283,7 @@ void enqueue_stage(grpic_ctx* c, int stage) {
         A.base[q] = field_plane<T>(c, true, centred ? c->bprev : c->bcur, q);
         A.out[q] = field_plane<T>(c, true, out, q);
         A.d[q] = F.d[q];
+        A.tgt[q] = second ? target_plane<T>(c, 3 + q) : nullptr;
       }
       A.loc = c->loc;
       A.K = field_consts<T>(c->g);
@@ -306,6 +324,7 @@ void enqueue_stage(grpic_ctx* c, int stage) {
         A.d[q] = F.d[q];
         A.out[q] = field_plane<T>(c, false, 1 - c->dcur, q);
         A.J[q] = F.J[q];
+        A.tgt[q] = target_plane<T>(c, q);
       }
       A.loc = c->loc;
       A.K = field_consts<T>(c->g);
@@ -473,6 +492,9 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   if (ncell + 1 >= (1ll << 31)) return GRPIC_ERR_INVALID;
   // Courant condition of the Yee update (Sec. 5): c dt < dx / sqrt(3)
   if (!(cfg->c * cfg->dt < 1.0 / std::sqrt(3.0))) return GRPIC_ERR_CFL;
+  if (!(cfg->absorb_inner >= 0.0 && cfg->absorb_inner <= 1.0 && cfg->absorb_outer >= 0.0 &&
+        cfg->absorb_outer <= 1.0))
+    return GRPIC_ERR_INVALID;
 
   grpic_ctx* c = new grpic_ctx();
   c->cfg = *cfg;
@@ -495,7 +517,11 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.yc = 0.5 * (cfg->ny - 1);
   g.zc = 0.5 * (cfg->nz - 1);
   g.r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
-  g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : g.r_plus;
+  g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : (cfg->absorb_inner > 0.0 ? 0.5 : 1.0) * g.r_plus;
+  g.k_in = cfg->absorb_inner;
+  g.k_out = cfg->absorb_outer;
+  g.r_abs = g.r_plus;
+  g.w_out = cfg->absorb_width > 0 ? cfg->absorb_width : 8;
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
   g.r_fp64 = (cfg->fp64_radius == 0.0 ? 4.0 : cfg->fp64_radius) * cfg->m;
@@ -506,6 +532,8 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.four_pi_c_f = (float)g.four_pi_c;
 
   c->fields = dev_alloc(c, 12 * (size_t)ncell * c->tsize);
+  const bool layers = g.k_in > 0.0 || g.k_out > 0.0;
+  if (layers) c->tgt = dev_alloc(c, 6 * (size_t)ncell * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));
   c->loc = static_cast<uint16_t*>(dev_alloc(c, sizeof(uint16_t) * (size_t)ncell));
   c->st = static_cast<DevStatus*>(dev_alloc(c, sizeof(DevStatus)));
@@ -514,7 +542,8 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   c->sort.counts = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
   c->sort.offsets = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
   c->sort.blocks = static_cast<int*>(dev_alloc(c, sizeof(int) * (c->sort.nblocks + 1)));
-  bool ok = c->fields && c->J && c->loc && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks;
+  bool ok = c->fields && c->J && c->loc && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks &&
+            (c->tgt || !layers);
   for (int s = 0; s < kMaxSpecies && ok; ++s) {
     c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
     c->sp[s].near_n = static_cast<int*>(dev_alloc(c, 2 * sizeof(int)));
@@ -537,6 +566,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
     return GRPIC_ERR_OOM;
   }
   cudaMemsetAsync(c->fields, 0, 12 * (size_t)ncell * c->tsize, c->stream);
+  if (c->tgt) cudaMemsetAsync(c->tgt, 0, 6 * (size_t)ncell * c->tsize, c->stream);
   cudaMemsetAsync(c->J, 0, 3 * (size_t)ncell * sizeof(double), c->stream);
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
   for (int s = 0; s < kMaxSpecies; ++s) cudaMemsetAsync(c->sp[s].n_dev, 0, sizeof(int), c->stream);
@@ -555,6 +585,7 @@ grpic_status grpic_destroy(grpic_ctx* c) {
   if (!c) return GRPIC_ERR_INVALID;
   cudaStreamSynchronize(c->stream);
   dev_free(c, c->fields);
+  dev_free(c, c->tgt);
   dev_free(c, c->J);
   dev_free(c, c->loc);
   dev_free(c, c->st);
@@ -628,6 +659,7 @@ grpic_status grpic_set_fields(grpic_ctx* c, const double* d3, const double* b3, 
     cudaMemcpyAsync(field_plane<double>(c, true, c->bcur, 0), bd, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
                     c->stream);
   }
+  snapshot_target(c);
   s = cuda_check(c, cudaGetLastError(), "set_fields");
   release_tmp(c, td);
   release_tmp(c, tb);
@@ -640,6 +672,7 @@ grpic_status grpic_set_uniform_field(grpic_ctx* c, const double E[3], const doub
     launch_uniform_field<float>(c->g, fields_view<float>(c), E, B, c->stream);
   else
     launch_uniform_field<double>(c->g, fields_view<double>(c), E, B, c->stream);
+  snapshot_target(c);
   grpic_status s = cuda_check(c, cudaGetLastError(), "set_uniform_field");
   if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_uniform_field sync");
   return s;
@@ -1150,6 +1183,7 @@ grpic_status batch_build(grpic_batch* b) {
       D.FS.b[1][q] = field_plane<T>(c, true, 1 - c->bcur, q);
       D.FS.J[q] = c->J + (size_t)q * c->g.ncell;
     }
+    for (int q = 0; q < 6; ++q) D.FS.tgt[q] = target_plane<T>(c, q);
     D.FS.loc = c->loc;
     D.dcur = b->dcur + i;
     dcur_init[i] = c->dcur;

@@ -225,8 +225,10 @@ grpic_status grpic_request_bytes(const grpic_request* r, size_t* bytes) {
   const double cells = (double)r->cfg.nx * r->cfg.ny * r->cfg.nz;
   const double tsz = r->cfg.precision == GRPIC_FP32_MIXED ? 4.0 : 8.0;
   const double n = (double)interior_slots(*r);
-  // 12 field planes (two d and two b buffers), FP64 J, location flags, sort counts and offsets
-  const double fields = cells * (12.0 * tsz + 3.0 * 8.0 + 2.0 + 8.0);
+  // 12 field planes (two d and two b buffers; 6 more for the absorbing layers' target), FP64 J,
+  // location flags, sort counts and offsets
+  const bool layers = r->cfg.absorb_inner > 0.0 || r->cfg.absorb_outer > 0.0;
+  const double fields = cells * ((layers ? 18.0 : 12.0) * tsz + 3.0 * 8.0 + 2.0 + 8.0);
   const double particles = n * r->nspecies * 2.0 * (8.0 * tsz + 8.0);
   const double staging = n * (4.0 * 8.0 * (1 + r->nspecies) + 4.0);
   *bytes = (size_t)(fields + particles + staging) + (size_t)(1 << 20);
@@ -257,11 +259,13 @@ grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* t
   const int quad = req->cfg.quad_order == 0 ? 2 : req->cfg.quad_order;
   if (s->have_kind && (req->cfg.precision != s->precision || quad != s->quad || req->cfg.flags != s->flags))
     return GRPIC_ERR_INVALID;
-  // the box's faces where f = 2m / R_face > 0.2: the field update grows an edge mode there (measured
-  // onset ~40 light-crossing units), so long runs on such grids are refused
+  // the box's faces where f = 2m / R_face > 0.2: with frozen faces the field update grows an edge
+  // mode there (measured onset ~40 light-crossing units), so long runs on such grids are refused
+  // unless the request has an outer absorbing layer
   const int nmin = std::min(req->cfg.nx, std::min(req->cfg.ny, req->cfg.nz));
   const double f_face = 2.0 * req->cfg.m / (0.5 * (nmin - 1));
-  if (f_face > kMaxFaceF && (double)req->nsteps * req->cfg.c * req->cfg.dt > kMaxUnstableTime)
+  if (f_face > kMaxFaceF && (double)req->nsteps * req->cfg.c * req->cfg.dt > kMaxUnstableTime &&
+      !(req->cfg.absorb_outer > 0.0))
     return GRPIC_ERR_UNSTABLE;
   size_t bytes = 0;
   grpic_request_bytes(req, &bytes);

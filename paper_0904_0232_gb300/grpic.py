@@ -39,7 +39,8 @@ class grpic_config(ctypes.Structure):
                 ("m", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("quad_order", ctypes.c_int), ("r_excise", ctypes.c_double),
                 ("flags", ctypes.c_uint), ("sort_interval", ctypes.c_int), ("max_particles", ctypes.c_int64),
-                ("fp64_radius", ctypes.c_double),
+                ("fp64_radius", ctypes.c_double), ("absorb_inner", ctypes.c_double),
+                ("absorb_outer", ctypes.c_double), ("absorb_width", ctypes.c_int),
                 ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
@@ -475,7 +476,8 @@ def grpic_server_destroy(server):
 
 
 def make_request(n, m, a, ppc, nsteps, seed, precision="fp32_mixed", c=1.0, dt=0.4, B=(0.0, 0.0, 0.05),
-                 species=((-1.0,), (1.0,)), wp_dt=0.025, u_th=0.1, r_min=None, quad_order=2):
+                 species=((-1.0,), (1.0,)), wp_dt=0.025, u_th=0.1, r_min=None, quad_order=2, absorb_inner=0.0,
+                 absorb_outer=0.0, absorb_width=0):
     """A run request: n^3 grid, pair plasma (q/m = -1, +1) by default, macro charge for the
     stated omega_p dt at ppc particles per cell per species (0.025 by default: charge separation
     near the hole stays bounded over 500 steps there, larger values overshoot the step limit)."""
@@ -483,7 +485,8 @@ def make_request(n, m, a, ppc, nsteps, seed, precision="fp32_mixed", c=1.0, dt=0
     qms = [sp[0] for sp in species]
     q = (wp_dt / dt) ** 2 / (4.0 * np.pi * max(ppc, 1) * sum(abs(v) for v in qms))
     req = grpic_request()
-    req.cfg = grpic_config(n, n, n, m, a, c, dt, prec, quad_order, 0.0, 0, 1, 0, 0.0)
+    req.cfg = grpic_config(n, n, n, m, a, c, dt, prec, quad_order, 0.0, 0, 1, 0, 0.0, absorb_inner, absorb_outer,
+                           absorb_width)
     req.B_contra[:] = list(B)
     req.nspecies = len(qms)
     for s_, qm in enumerate(qms):
@@ -502,7 +505,8 @@ class Simulation:
     """One GRPIC context on the current CUDA device and PyTorch's current stream."""
 
     def __init__(self, nx, ny, nz, m, a, c, dt, precision="fp64", quad_order=2, r_excise=0.0, flags=0,
-                 sort_interval=1, max_particles=0, stream=None, torch_allocator=True, fp64_radius=0.0):
+                 sort_interval=1, max_particles=0, stream=None, torch_allocator=True, fp64_radius=0.0,
+                 absorb_inner=0.0, absorb_outer=0.0, absorb_width=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("GRPIC needs a CUDA device")
@@ -510,7 +514,7 @@ class Simulation:
         self.shape = (nz, ny, nx)
         prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
         cfg = grpic_config(nx, ny, nz, m, a, c, dt, prec, quad_order, r_excise, flags, sort_interval, max_particles,
-                           fp64_radius)
+                           fp64_radius, absorb_inner, absorb_outer, absorb_width)
         if torch_allocator:
             cfg.alloc = _torch_alloc
             cfg.free_fn = _torch_free

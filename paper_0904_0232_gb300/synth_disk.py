@@ -21,6 +21,10 @@ Recipe (stands in for the disk/corona set-up of Sec. 6, which has no released da
     components; corona: the normal observer's u_i = 0 plus the same thermal spread, given as
     covariant spatial components;
   * macro-particle charge chosen so that omega_p dt = wp_dt (0.025) at the inner-edge density;
+  * absorbing layers (``layers``): 0.3 per step inside the horizon (r_+/2 <= r < r_+), 0.2 per
+    step over the 8 cells next to the frozen faces.  With the inside of the horizon frozen, this
+    spin resolved by m = 8 cells grows a field mode next to the horizon (|d| x 1e4 in 500 steps,
+    the same in FP64 and at half the timestep);
   * randomness from one seeded torch generator on the device, in a fixed order of draws.
 The four species are: 0 disk electrons, 1 disk ions, 2 corona electrons, 3 corona ions.
 """
@@ -55,6 +59,8 @@ class DiskCorona:
     nsteps: int
     n0: float
     species: list
+    layers: dict = dataclasses.field(default_factory=lambda: dict(absorb_inner=0.3, absorb_outer=0.2,
+                                                                  absorb_width=8))
 
     @property
     def nx(self):

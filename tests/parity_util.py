@@ -17,10 +17,11 @@ TOL = {
 }
 
 
-def oracle_start(wl, threads=0, quad_order=2, flags=0, fields=None, r_excise=0.0):
-    """Oracle context loaded with the workload (u^4 completed by the oracle)."""
+def oracle_start(wl, threads=0, quad_order=2, flags=0, fields=None, r_excise=0.0, **absorb):
+    """Oracle context loaded with the workload (u^4 completed by the oracle); absorb: the
+    absorbing-layer settings (absorb_inner, absorb_outer, absorb_width)."""
     ref = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, quad_order=quad_order, threads=threads,
-                   flags=flags, r_excise=r_excise)
+                   flags=flags, r_excise=r_excise, **absorb)
     if fields is None:
         ref.init_uniform_field(B=(0.0, 0.0, wl.B0))
     else:
@@ -30,10 +31,11 @@ def oracle_start(wl, threads=0, quad_order=2, flags=0, fields=None, r_excise=0.0
     return ref
 
 
-def gpu_from_oracle(ref, wl, precision, quad_order=2, flags=0, sort_interval=1, r_excise=0.0):
-    """GPU context holding exactly the oracle's current state."""
+def gpu_from_oracle(ref, wl, precision, quad_order=2, flags=0, sort_interval=1, r_excise=0.0, **absorb):
+    """GPU context holding exactly the oracle's current state (whose fields also become the
+    absorbing layers' target: call it on the oracle's starting state)."""
     sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=quad_order,
-                     flags=flags, sort_interval=sort_interval, r_excise=r_excise)
+                     flags=flags, sort_interval=sort_interval, r_excise=r_excise, **absorb)
     d, b, J = ref.get_fields()
     sim.set_fields(d, b)
     sim.set_j(J)

@@ -77,3 +77,76 @@ def test_disk_corona_384_sampled():
         eu = np.abs(u1[:, keep] - us).max(0) / np.abs(us).max(0)
         assert eu.max() <= tol, (s, eu.max())
 
+
+
+def test_disk_corona_384_500_steps():
+    """The largest configuration as it is specified: 500 whole steps of the 384^3 disk + corona with
+    ~1e9 particles in FP32-mixed (with the workload's absorbing layers), with the invariant
+    statistics over the run (|g(u,u) + c^2|, and
+    the changes of -u_4 and u_phi on the tracked subsample).  From the final state, a strided
+    subsample of ~1e5 live particles is pushed and deposited once more into an empty J by the oracle
+    (FP64) and by a fresh context holding the same fields (FP32-mixed): particle states and every J
+    node are compared (J off the nodes of zig-zag splits decided within rounding of a face, as in
+    the other FP32 J checks)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 170e9:
+        pytest.skip("needs ~170 GB of free device memory")
+    from parity_util import check_j, particle_errors
+
+    wl = synth_disk.kerr_disk_corona(n=384, seed=3)
+    meta = [(sp.q_over_m, sp.q_macro) for sp in wl.species]
+    geo = (wl.n, wl.m, wl.a, wl.c, wl.dt)
+    sim = Simulation(wl.n, wl.n, wl.n, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", **wl.layers)
+    sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
+    for s, sp in enumerate(wl.species):
+        sim.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.u4, sp.ids, umode=sp.umode)
+    del wl, sp
+    torch.cuda.empty_cache()
+    inv0 = sim.invariants(baseline=True)
+    sim.step(500)
+    inv = sim.invariants()
+    st = sim.stats()
+    print("disk384 500 steps: invariants", inv0, inv, "stats", st)
+    assert st["steps"] == 500 and inv["tracked"] > 1e6
+    assert inv["norm_max"] < 0.05 and inv["norm_mean"] < 1e-4
+    d, b, _ = sim.get_fields()
+    sub = []
+    for s in range(len(meta)):
+        x, u, ids = sim.get_particles(s, device=True)
+        pick = (ids % 10000) == 0
+        sub.append((x[:, pick].cpu().numpy(), u[:, pick].cpu().numpy(), ids[pick].cpu().numpy().astype(np.uint32)))
+        del x, u, ids, pick
+        torch.cuda.empty_cache()
+    sim.close()
+    torch.cuda.empty_cache()
+    nsub = sum(v[2].size for v in sub)
+    assert 5e4 < nsub < 2e5
+
+    n, m, a, c, dt = geo
+    ref = O.Oracle(n, n, n, m, a, c, dt, threads=4, flags=O.NO_GAMMA_TERMS)
+    ref.set_fields(d, b)
+    one = Simulation(n, n, n, m, a, c, dt, precision="fp32_mixed")
+    one.set_fields(d, b)
+    for s, ((x4, u4, ids), (qm, qmac)) in enumerate(zip(sub, meta)):
+        ref.load_particles(s, qm, qmac, x4, u4, ids, umode=0)
+        one.load_particles(s, qm, qmac, x4, u4, ids)
+    ref.zero_j()
+    ref.push_deposit()
+    one.stage(GRPIC_STAGE_ZERO_J)
+    one.stage(GRPIC_STAGE_PUSH_DEPOSIT)
+    from paper_0904_0232_gb300.grpic import GRPIC_STAGE_SORT
+
+    one.stage(GRPIC_STAGE_SORT)
+    tol = TOL["fp32_mixed"]["particles"]
+    for s in range(len(sub)):
+        ex, e4, eu = particle_errors(one, ref, s, x4_scale=1.0)
+        assert max(ex, eu) <= tol, (s, ex, eu)
+    J = one.get_fields()[2]
+    Jr = ref.get_fields()[2]
+    mask = check_j(J, Jr, ref, len(sub), "fp32_mixed")
+    keep = ~np.broadcast_to(mask, J.shape)
+    print("disk384 subsample", nsub, "J rel L2 (off the face mask)",
+          np.linalg.norm((J - Jr)[keep]) / np.linalg.norm(Jr[keep]), "mask fraction", mask.mean())

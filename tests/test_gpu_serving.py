@@ -185,3 +185,24 @@ def test_unstable_boxes_are_refused():
     grpic_submit(server, make_request(n=32, m=3.0, a=0.0, ppc=1, nsteps=50, seed=52))
     grpic_submit(server, make_request(n=128, m=3.0, a=0.0, ppc=1, nsteps=500, seed=53))
     grpic_server_destroy(server)
+
+
+def test_absorbing_layers_admit_and_complete():
+    """The long run refused above, requested with absorbing layers (outer: 4 cells, 0.2 per step at
+    the faces; inner: 0.3 per step inside the horizon), is admitted and runs all its steps within
+    the step limit, its field staying of the order of the initial one."""
+    from paper_0904_0232_gb300.grpic import grpic_get_stats
+
+    server = grpic_server_create(int(4e9), 8)
+    req = dict(n=32, m=3.0, a=0.0, ppc=1, nsteps=200, seed=51)
+    t = grpic_submit(server, make_request(**req, absorb_inner=0.3, absorb_outer=0.2, absorb_width=4))
+    t2 = grpic_submit(server, make_request(**dict(req, a=2.7, seed=54), absorb_inner=0.3, absorb_outer=0.2,
+                                           absorb_width=4))
+    for tk in (t, t2):
+        ctx = _run_to_done(server, tk)
+        assert grpic_get_stats(ctx)["steps"] == 200
+        d, b, _ = grpic_get_fields(ctx, (32, 32, 32))
+        assert np.isfinite(d).all() and np.abs(d).max() < 2.0 and np.abs(b).max() < 2.0, (
+            np.abs(d).max(), np.abs(b).max())
+        grpic_server_release(server, tk)
+    grpic_server_destroy(server)
