@@ -47,6 +47,8 @@ struct Grid {
   // w_out cells; 0 -> no layer
   double k_in, k_out, r_abs;
   int w_out;
+  double inv_w;           // 1 / w_out
+  float k_out_f, inv_w_f;  // the outer layer's constants in FP32
 };
 
 template <typename T>
@@ -68,9 +70,10 @@ struct Fields {
 
 // Both buffers of the field ping-pong pairs, the target of the absorbing layers (d planes 0-2, b
 // planes 3-5; null without layers) and the per-cell location flags (bit l: location l advanced;
-// bit 6: an advanced location of the cell lies in an absorbing layer; bit 8 + l: location l
-// excised).  The field updates write the other buffer.
+// bit 6: an advanced location of the cell lies in an absorbing layer; bit 7: in the inner one;
+// bit 8 + l: location l excised).  The field updates write the other buffer.
 constexpr unsigned kLayerBit = 1u << 6;
+constexpr unsigned kInnerBit = 1u << 7;
 template <typename T>
 struct FieldStore {
   T* d[2][3];

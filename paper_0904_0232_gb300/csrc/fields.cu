@@ -198,35 +198,47 @@ __device__ __forceinline__ bool exc(uint16_t w, int l) { return (w >> (8 + l)) &
 __device__ __forceinline__ bool in_layer(uint16_t w) { return (w & kLayerBit) != 0u; }
 
 // ---- absorbing layers -------------------------------------------------------------------------
-// Relaxation per step at location l of cell (i, j, k): the larger of the inner layer's
-// k_in (r_abs - r) / (r_abs - r_exc) where r_exc <= r < r_abs (r at the location, in FP64) and the
-// outer layer's k_out ((W + 1 - s) / W)^2 where s <= W, s being 1 + the cell's distance in cells to
-// the outer two index layers (s = 1 at the first advanced cell).
-__device__ inline double absorb_kappa(const Grid& g, int l, int i, int j, int k) {
-  double kap = 0.0;
-  if (g.k_out > 0.0) {
-    const int s = 1 + min(min(min(i - 2, g.nx - 3 - i), min(j - 2, g.ny - 3 - j)), min(k - 2, g.nz - 3 - k));
-    if (s >= 1 && s <= g.w_out) {
-      const double u = (double)(g.w_out + 1 - s) / (double)g.w_out;
-      kap = g.k_out * u * u;
-    }
+// Relaxation per step at location l of cell (i, j, k): the larger of the outer layer's
+// k_out ((W + 1 - s) / W)^2 where s <= W, s being 1 + the cell's distance in cells to the outer two
+// index layers (s = 1 at the first advanced cell), and the inner layer's
+// k_in (r_abs - r) / (r_abs - r_exc) where r_exc <= r < r_abs (r at the location, in FP64).  The
+// outer profile is evaluated in the field type from integers and constants converted on the host;
+// the inner one only in cells flagged for it (kInnerBit), which lie inside the horizon.
+template <typename T>
+__device__ __forceinline__ T outer_kappa(const Grid& g, int i, int j, int k) {
+  const int s = 1 + min(min(min(i - 2, g.nx - 3 - i), min(j - 2, g.ny - 3 - j)), min(k - 2, g.nz - 3 - k));
+  if (s < 1 || s > g.w_out) return T(0);  // (k_out = 0 gives 0 below)
+  T k_out, inv_w;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    k_out = g.k_out_f;
+    inv_w = g.inv_w_f;
+  } else {
+    k_out = g.k_out;
+    inv_w = g.inv_w;
   }
-  if (g.k_in > 0.0 && g.r_abs > g.r_exc) {
-    const double X = i + 0.5 * half(l, 0) - g.xc;
-    const double Y = j + 0.5 * half(l, 1) - g.yc;
-    const double Z = k + 0.5 * half(l, 2) - g.zc;
-    const Kerr<double> K = kerr_eval<double>(X, Y, Z, g.m, g.a);
-    if (!K.flat && K.r >= g.r_exc && K.r < g.r_abs)
-      kap = fmax(kap, g.k_in * (g.r_abs - K.r) / (g.r_abs - g.r_exc));
-  }
-  return kap;
+  const T u = (T)(g.w_out + 1 - s) * inv_w;
+  return k_out * u * u;
+}
+// Out of line: the FP64 quartic would otherwise take registers from the stencil code around the
+// (rare) call.
+__device__ __noinline__ double inner_kappa_at(double X, double Y, double Z, double m, double a, double r_exc,
+                                              double r_abs, double k_in) {
+  const Kerr<double> K = kerr_eval<double>(X, Y, Z, m, a);
+  if (K.flat || K.r < r_exc || K.r >= r_abs) return 0.0;
+  return k_in * (r_abs - K.r) / (r_abs - r_exc);
+}
+__device__ __forceinline__ double inner_kappa(const Grid& g, int l, int i, int j, int k) {
+  if (!(g.k_in > 0.0) || !(g.r_abs > g.r_exc)) return 0.0;
+  return inner_kappa_at(i + 0.5 * half(l, 0) - g.xc, j + 0.5 * half(l, 1) - g.yc, k + 0.5 * half(l, 2) - g.zc, g.m,
+                        g.a, g.r_exc, g.r_abs, g.k_in);
 }
 
-// v relaxed toward the target t at location l of cell (i, j, k): t + (1 - kappa)(v - t).
+// v relaxed toward the target t at location l of cell (i, j, k) with flags w: t + (1 - kappa)(v - t).
 template <typename T>
-__device__ __forceinline__ T relax(const Grid& g, T t, T v, int l, int i, int j, int k) {
-  const T keep = (T)(1.0 - absorb_kappa(g, l, i, j, k));
-  return t + keep * (v - t);
+__device__ __forceinline__ T relax(const Grid& g, uint16_t w, T t, T v, int l, int i, int j, int k) {
+  T kap = outer_kappa<T>(g, i, j, k);
+  if (w & kInnerBit) kap = fmax(kap, (T)inner_kappa(g, l, i, j, k));
+  return t + (T(1) - kap) * (v - t);
 }
 
 // Asynchronous 4- or 8-byte copy global -> shared (zero-filled when ok is false: no bytes are read
@@ -374,7 +386,7 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
         const T old = A.inplace ? base_old[q] : sm.Sb[sb(p)].v[q][ty + 1][tx + 1];
         if (adv(w, 3 + q)) {
           T v = old - A.coef * cu[q];
-          if (A.tgt[0] && in_layer(w)) v = relax<T>(g, A.tgt[q][c], v, 3 + q, x, y, p);
+          if (A.tgt[0] && in_layer(w)) v = relax<T>(g, w, A.tgt[q][c], v, 3 + q, x, y, p);
           A.out[q][c] = v;
         } else if (!A.inplace) {
           A.out[q][c] = old;
@@ -520,15 +532,18 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
       T dv_h[3];
       div_h<T, BY>(sm.H2[cur], sm.H2[nxt], tx, ty, dv_h);
 #pragma unroll
+      T v[3];
+#pragma unroll
       for (int al = 0; al < 3; ++al) {
         const T dold = Dc.v[al][ty + 1][tx + 1];
-        T v = dold;
-        if (adv(w_cur, al)) {
-          v = dold + (src_cur[al] - dv_h[al]) * dx4;
-          if (A.tgt[0] && in_layer(w_cur)) v = relax<T>(g, A.tgt[al][c], v, al, x, y, p);
-        }
-        A.out[al][c] = v;
+        v[al] = adv(w_cur, al) ? dold + (src_cur[al] - dv_h[al]) * dx4 : dold;
       }
+      if (A.tgt[0] && in_layer(w_cur)) {
+        for (int al = 0; al < 3; ++al)
+          if (adv(w_cur, al)) v[al] = relax<T>(g, w_cur, A.tgt[al][c], v[al], al, x, y, p);
+      }
+#pragma unroll
+      for (int al = 0; al < 3; ++al) A.out[al][c] = v[al];
     }
     cur = nxt;
     w_cur = w_next;
@@ -698,7 +713,8 @@ __global__ void k_batch_flip_d(const InstDesc<T>* __restrict__ desc, int n) {
 
 // ---- location flags --------------------------------------------------------------------------
 // bit l: location l of the cell is advanced (cell in [2, n-3]^3 and r >= r_excise); bit 6: an
-// advanced location of the cell has a relaxation kappa > 0; bit 8 + l: location l is excised
+// advanced location of the cell has a relaxation kappa > 0; bit 7: one from the inner layer;
+// bit 8 + l: location l is excised
 // (r < r_excise, or r = 0), where conversions take the flat metric.  Decided once, in FP64.
 __global__ void k_location_flags(const Grid g, uint16_t* __restrict__ loc) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -718,7 +734,8 @@ __global__ void k_location_flags(const Grid g, uint16_t* __restrict__ loc) {
     if (excised) w |= 1u << (8 + l);
     if (inner && !excised) {
       w |= 1u << l;
-      if (absorb_kappa(g, l, i, j, k) > 0.0) w |= kLayerBit;
+      if (outer_kappa<double>(g, i, j, k) > 0.0) w |= kLayerBit;
+      if (inner_kappa(g, l, i, j, k) > 0.0) w |= kLayerBit | kInnerBit;
     }
   }
   loc[c] = (uint16_t)w;

@@ -522,6 +522,9 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.k_out = cfg->absorb_outer;
   g.r_abs = g.r_plus;
   g.w_out = cfg->absorb_width > 0 ? cfg->absorb_width : 8;
+  g.inv_w = 1.0 / g.w_out;
+  g.k_out_f = (float)g.k_out;
+  g.inv_w_f = (float)g.inv_w;
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
   g.r_fp64 = (cfg->fp64_radius == 0.0 ? 4.0 : cfg->fp64_radius) * cfg->m;

@@ -30,9 +30,17 @@ def sample_requests(n, seed, grids=(32, 48, 64), ppc=(1, 8), steps=(50, 200), m=
     return out
 
 
-def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **spec_ranges):
+def layers_for(n):
+    """Absorbing layers a client requests for an n^3 box: 0.3 per step inside the horizon, 0.2 per
+    step at the faces over n/8 cells (4 to 8).  Without them, long runs on boxes whose faces see
+    f = 2m / R_face > 0.2 are refused (a mode grows at the frozen faces there)."""
+    return dict(absorb_inner=0.3, absorb_outer=0.2, absorb_width=int(min(8, max(4, n // 8))))
+
+
+def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, layers=True, **spec_ranges):
     """Run a Poisson arrival stream (rate per second over `duration` seconds of arrivals) to
-    completion.  Returns latencies (s), aggregate particle-steps/s and counts."""
+    completion, every request with absorbing layers unless `layers` is false.  Returns latencies
+    (s), aggregate particle-steps/s and counts."""
     rng = np.random.default_rng(seed)
     arrivals = []
     t = rng.exponential(1.0 / rate)
@@ -55,7 +63,8 @@ def serve_poisson(rate, duration, budget_bytes, slots, seed=0, max_wall=None, **
             if max_wall is not None and now > max_wall:
                 break
             while nxt < len(arrivals) and arrivals[nxt] <= now:
-                req = make_request(**specs[nxt])
+                spec = specs[nxt]
+                req = make_request(**spec, **(layers_for(spec["n"]) if layers else {}))
                 try:
                     pending[grpic_submit(server, req)] = arrivals[nxt]
                 except GrpicError as e:  # refused at admission (e.g. GRPIC_ERR_UNSTABLE), with its reason
@@ -122,12 +131,13 @@ def main():
     p.add_argument("--slots", type=int, default=64)
     p.add_argument("--max-wall", type=float, default=None, help="stop waiting for completions after this")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-layers", action="store_true", help="requests without absorbing layers")
     args = p.parse_args()
     for r in args.rate:
         res = serve_poisson(r, args.duration, int(args.budget_gb * 1e9), args.slots, seed=args.seed,
-                            max_wall=args.max_wall, **MIXES[args.mix])
+                            max_wall=args.max_wall, layers=not args.no_layers, **MIXES[args.mix])
         res.update(mix=args.mix, mix_ranges=MIXES[args.mix], budget_gb=args.budget_gb, slots=args.slots,
-                   arrival_window_s=args.duration)
+                   arrival_window_s=args.duration, absorbing_layers=not args.no_layers)
         print(json.dumps(res), flush=True)
 
 
