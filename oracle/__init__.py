@@ -286,13 +286,13 @@ class Oracle:
         self._chk(lib().orc_set_fields(self._h, _dp(d), _dp(b)), "set_fields")
 
     def set_absorb_target(self, d, b):
-        """Replace the absorbing layers' target (reading A22; by default the field as last set)."""
+        """Replace the absorbing layers' target (reading A23; by default the field as last set)."""
         d = _f64(d, (3,) + self.shape)
         b = _f64(b, (3,) + self.shape)
         self._chk(lib().orc_set_absorb_target(self._h, _dp(d), _dp(b)), "set_absorb_target")
 
     def absorb_kappa(self, comp, i, j, k):
-        """Relaxation per step of the absorbing layers at component comp's point (i, j, k) (A22)."""
+        """Relaxation per step of the absorbing layers at component comp's point (i, j, k) (A23)."""
         return lib().orc_absorb_kappa(self._h, int(comp), int(i), int(j), int(k))
 
     def set_j(self, J):

@@ -57,7 +57,7 @@
  *       h on d (the shift terms), and evaluating them at each half-step's own start value
  *       (ORC_LITERAL_HALF_STEPS) is a forward-Euler step of a centred advection term, which grows
  *       without bound near the horizon.
- *   A22 Absorbing layers (optional; off unless absorb_inner or absorb_outer > 0; the paper states
+ *   A23 Absorbing layers (optional; off unless absorb_inner or absorb_outer > 0; the paper states
  *       no boundary condition).  After the second B half-step and the E step every advanced
  *       point takes F0 + (1 - kappa)(F - F0), F0 the field as last set, kappa the larger of an
  *       inner layer's absorb_inner (r_+ - r)/(r_+ - r_excise) for r_excise <= r < r_+ (r_excise
@@ -455,7 +455,7 @@ typedef struct {
   double r_excise;  // <= 0: r_+ (r_+/2 with an inner absorbing layer)
   unsigned flags;
   int threads;  // <= 0: all available
-  double absorb_inner, absorb_outer;  // A22: relaxation per step at the layers' deepest points (0: none)
+  double absorb_inner, absorb_outer;  // A23: relaxation per step at the layers' deepest points (0: none)
   int absorb_width;                   // outer layer width in cells (<= 0: 8)
 } orc_config;
 
@@ -473,7 +473,7 @@ struct Ctx {
   size_t ncell = 0;
   std::vector<double> F[6];
   std::vector<double> Fprev[3];  // b^{n-1/2} kept by the first B half-step (A21)
-  std::vector<double> F0[6];     // target of the absorbing layers (A22), kept only with layers
+  std::vector<double> F0[6];     // target of the absorbing layers (A23), kept only with layers
   double r_abs = 0.0;            // outer radius of the inner absorbing layer (r_+)
   int w_out = 8;                 // outer absorbing layer width
   std::vector<double> J[3];
@@ -569,7 +569,7 @@ struct Ctx {
 
   bool literal() const { return (cfg.flags & ORC_LITERAL_HALF_STEPS) != 0; }
 
-  // --- A22: absorbing layers -----------------------------------------------------------------
+  // --- A23: absorbing layers -----------------------------------------------------------------
   bool layers() const { return cfg.absorb_inner > 0.0 || cfg.absorb_outer > 0.0; }
 
   // The fields just set become the layers' target.
@@ -1363,7 +1363,7 @@ int orc_set_fields(void* p, const double* d3, const double* b3) {
   return ORC_OK;
 }
 
-// Replace the absorbing layers' target (A22) without touching the fields.
+// Replace the absorbing layers' target (A23) without touching the fields.
 int orc_set_absorb_target(void* p, const double* d3, const double* b3) {
   Ctx* ctx = static_cast<Ctx*>(p);
   if (!ctx->layers()) return ORC_ERR_INVALID;
@@ -1374,7 +1374,7 @@ int orc_set_absorb_target(void* p, const double* d3, const double* b3) {
   return ORC_OK;
 }
 
-// Relaxation per step of the absorbing layers at component c's lattice point (i, j, k) (A22).
+// Relaxation per step of the absorbing layers at component c's lattice point (i, j, k) (A23).
 double orc_absorb_kappa(void* p, int c, int i, int j, int k) {
   return static_cast<Ctx*>(p)->absorb_kappa(c, i, j, k);
 }

@@ -1,4 +1,4 @@
-"""Pins of the oracle's absorbing layers (reading A22: after the second B half-step and the E step,
+"""Pins of the oracle's absorbing layers (reading A23: after the second B half-step and the E step,
 every advanced point takes F0 + (1 - kappa)(F - F0); kappa from an inner layer inside the horizon
 and an outer layer next to the frozen faces).
 
