@@ -49,6 +49,9 @@ struct Grid {
   int w_out;
   double inv_w;           // 1 / w_out
   float k_out_f, inv_w_f;  // the outer layer's constants in FP32
+  // box of cells (origin, extent per axis) holding every location of the inner layer; its table
+  // of relaxations is 6 x kboxn[0] x kboxn[1] x kboxn[2] values (location-major)
+  int kbox0[3], kboxn[3];
 };
 
 template <typename T>
@@ -80,6 +83,7 @@ struct FieldStore {
   T* b[2][3];
   double* J[3];
   const T* tgt[6];
+  const T* kin;  // the inner layer's relaxation table (null without it)
   const uint16_t* loc;
 };
 
@@ -115,6 +119,7 @@ struct BStepArgs {
   T* out[3];
   const T* d[3];
   const T* tgt[3];
+  const T* kin;
   const uint16_t* loc;
   FieldConsts<T> K;
   T coef;
@@ -130,6 +135,7 @@ struct EStepArgs {
   const T* d[3];
   T* out[3];
   const T* tgt[3];
+  const T* kin;
   const double* J[3];
   const uint16_t* loc;
   FieldConsts<T> K;
@@ -158,6 +164,9 @@ __host__ __device__ inline long long cell_index(const Grid& g, int i, int j, int
 
 // ---- launchers (defined in fields.cu, push.cu, sort.cu) --------------------------------
 void launch_location_flags(const Grid& g, uint16_t* loc, cudaStream_t st);
+// The inner absorbing layer's relaxation over the box g.kbox0 / g.kboxn (6 values per cell).
+template <typename T>
+void launch_inner_kappa_table(const Grid& g, T* kin, cudaStream_t st);
 // B half-steps (Eq. 10) and the E step (Eq. 12); sms sizes the z chunks of the launch.
 template <typename T>
 void launch_b_step(const Grid& g, const BStepArgs<T>& A, int sms, cudaStream_t st);

@@ -203,41 +203,53 @@ __device__ __forceinline__ bool in_layer(uint16_t w) { return (w & kLayerBit) !=
 // index layers (s = 1 at the first advanced cell), and the inner layer's
 // k_in (r_abs - r) / (r_abs - r_exc) where r_exc <= r < r_abs (r at the location, in FP64).  The
 // outer profile is evaluated in the field type from integers and constants converted on the host;
-// the inner one only in cells flagged for it (kInnerBit), which lie inside the horizon.
+// the inner one is tabulated once, in FP64, over the box of cells around the hole that holds every
+// location with r < r_abs, and looked up in cells flagged for it (kInnerBit).  The field kernels
+// then run no FP64 operation for the layers (this GPU's FP64 pipe, which also does its
+// conversions, is narrow).
+
+// A small non-negative int as a float without a conversion instruction: the float with the bits
+// of 2^23 + v, minus 2^23; exact for 0 <= v < 2^23.
+__device__ __forceinline__ float small_int_to_float(int v) { return __int_as_float(0x4B000000 | v) - 8388608.f; }
+
 template <typename T>
 __device__ __forceinline__ T outer_kappa(const Grid& g, int i, int j, int k) {
   const int s = 1 + min(min(min(i - 2, g.nx - 3 - i), min(j - 2, g.ny - 3 - j)), min(k - 2, g.nz - 3 - k));
   if (s < 1 || s > g.w_out) return T(0);  // (k_out = 0 gives 0 below)
-  T k_out, inv_w;
+  T k_out, inv_w, n;
   if constexpr (sizeof(T) == sizeof(float)) {
     k_out = g.k_out_f;
     inv_w = g.inv_w_f;
+    n = small_int_to_float(g.w_out + 1 - s);
   } else {
     k_out = g.k_out;
     inv_w = g.inv_w;
+    n = (double)(g.w_out + 1 - s);
   }
-  const T u = (T)(g.w_out + 1 - s) * inv_w;
+  const T u = n * inv_w;
   return k_out * u * u;
 }
-// Out of line: the FP64 quartic would otherwise take registers from the stencil code around the
-// (rare) call.
-__device__ __noinline__ double inner_kappa_at(double X, double Y, double Z, double m, double a, double r_exc,
-                                              double r_abs, double k_in) {
-  const Kerr<double> K = kerr_eval<double>(X, Y, Z, m, a);
-  if (K.flat || K.r < r_exc || K.r >= r_abs) return 0.0;
-  return k_in * (r_abs - K.r) / (r_abs - r_exc);
-}
-__device__ __forceinline__ double inner_kappa(const Grid& g, int l, int i, int j, int k) {
+
+// The inner layer's relaxation at location l of cell (i, j, k), in FP64.
+__device__ inline double inner_kappa(const Grid& g, int l, int i, int j, int k) {
   if (!(g.k_in > 0.0) || !(g.r_abs > g.r_exc)) return 0.0;
-  return inner_kappa_at(i + 0.5 * half(l, 0) - g.xc, j + 0.5 * half(l, 1) - g.yc, k + 0.5 * half(l, 2) - g.zc, g.m,
-                        g.a, g.r_exc, g.r_abs, g.k_in);
+  const Kerr<double> K = kerr_eval<double>(i + 0.5 * half(l, 0) - g.xc, j + 0.5 * half(l, 1) - g.yc,
+                                           k + 0.5 * half(l, 2) - g.zc, g.m, g.a);
+  if (K.flat || K.r < g.r_exc || K.r >= g.r_abs) return 0.0;
+  return g.k_in * (g.r_abs - K.r) / (g.r_abs - g.r_exc);
+}
+
+// Index of location l of cell (i, j, k) in the inner layer's table (the cell must lie in the box).
+__host__ __device__ __forceinline__ long long kin_index(const Grid& g, int l, int i, int j, int k) {
+  return (((long long)l * g.kboxn[2] + (k - g.kbox0[2])) * g.kboxn[1] + (j - g.kbox0[1])) * g.kboxn[0] +
+         (i - g.kbox0[0]);
 }
 
 // v relaxed toward the target t at location l of cell (i, j, k) with flags w: t + (1 - kappa)(v - t).
 template <typename T>
-__device__ __forceinline__ T relax(const Grid& g, uint16_t w, T t, T v, int l, int i, int j, int k) {
+__device__ __forceinline__ T relax(const Grid& g, const T* kin, uint16_t w, T t, T v, int l, int i, int j, int k) {
   T kap = outer_kappa<T>(g, i, j, k);
-  if (w & kInnerBit) kap = fmax(kap, (T)inner_kappa(g, l, i, j, k));
+  if (w & kInnerBit) kap = fmax(kap, __ldg(kin + kin_index(g, l, i, j, k)));
   return t + (T(1) - kap) * (v - t);
 }
 
@@ -386,7 +398,7 @@ __device__ __forceinline__ void b_step_tile(const Grid& g, const BStepArgs<T>& A
         const T old = A.inplace ? base_old[q] : sm.Sb[sb(p)].v[q][ty + 1][tx + 1];
         if (adv(w, 3 + q)) {
           T v = old - A.coef * cu[q];
-          if (A.tgt[0] && in_layer(w)) v = relax<T>(g, w, A.tgt[q][c], v, 3 + q, x, y, p);
+          if (A.tgt[0] && in_layer(w)) v = relax<T>(g, A.kin, w, A.tgt[q][c], v, 3 + q, x, y, p);
           A.out[q][c] = v;
         } else if (!A.inplace) {
           A.out[q][c] = old;
@@ -540,7 +552,7 @@ __device__ __forceinline__ void e_step_tile(const Grid& g, const EStepArgs<T>& A
       }
       if (A.tgt[0] && in_layer(w_cur)) {
         for (int al = 0; al < 3; ++al)
-          if (adv(w_cur, al)) v[al] = relax<T>(g, w_cur, A.tgt[al][c], v[al], al, x, y, p);
+          if (adv(w_cur, al)) v[al] = relax<T>(g, A.kin, w_cur, A.tgt[al][c], v[al], al, x, y, p);
       }
 #pragma unroll
       for (int al = 0; al < 3; ++al) A.out[al][c] = v[al];
@@ -637,6 +649,7 @@ __device__ __forceinline__ BStepArgs<T> batch_b_args(const InstDesc<T>& D, int w
     }
   }
   for (int q = 0; q < 3; ++q) A.tgt[q] = which == 1 ? D.FS.tgt[3 + q] : nullptr;
+  A.kin = D.FS.kin;
   A.loc = D.FS.loc;
   A.coef = (which == 1 && !literal) ? dx4 : dx4 * T(0.5);
   A.inplace = which == 1 && !literal;
@@ -655,6 +668,7 @@ __device__ __forceinline__ EStepArgs<T> batch_e_args(const InstDesc<T>& D, bool 
     A.J[q] = D.FS.J[q];
     A.tgt[q] = D.FS.tgt[q];
   }
+  A.kin = D.FS.kin;
   A.loc = D.FS.loc;
   A.pred = !literal;
   return A;
@@ -735,7 +749,10 @@ __global__ void k_location_flags(const Grid g, uint16_t* __restrict__ loc) {
     if (inner && !excised) {
       w |= 1u << l;
       if (outer_kappa<double>(g, i, j, k) > 0.0) w |= kLayerBit;
-      if (inner_kappa(g, l, i, j, k) > 0.0) w |= kLayerBit | kInnerBit;
+      // (the box holds every such cell by construction; checked so that no lookup can leave it)
+      const bool in_box = i >= g.kbox0[0] && i < g.kbox0[0] + g.kboxn[0] && j >= g.kbox0[1] &&
+                          j < g.kbox0[1] + g.kboxn[1] && k >= g.kbox0[2] && k < g.kbox0[2] + g.kboxn[2];
+      if (in_box && inner_kappa(g, l, i, j, k) > 0.0) w |= kLayerBit | kInnerBit;
     }
   }
   loc[c] = (uint16_t)w;
@@ -787,6 +804,27 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 void launch_location_flags(const Grid& g, uint16_t* loc, cudaStream_t st) {
   k_location_flags<<<blocks_for(g.ncell, 256), 256, 0, st>>>(g, loc);
 }
+
+template <typename T>
+__global__ void k_inner_kappa_table(const Grid g, T* __restrict__ kin, long long n) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int i = g.kbox0[0] + (int)(e % g.kboxn[0]);
+  long long r = e / g.kboxn[0];
+  const int j = g.kbox0[1] + (int)(r % g.kboxn[1]);
+  r /= g.kboxn[1];
+  const int k = g.kbox0[2] + (int)(r % g.kboxn[2]);
+  const int l = (int)(r / g.kboxn[2]);
+  kin[e] = (T)inner_kappa(g, l, i, j, k);
+}
+
+template <typename T>
+void launch_inner_kappa_table(const Grid& g, T* kin, cudaStream_t st) {
+  const long long n = 6ll * g.kboxn[0] * g.kboxn[1] * g.kboxn[2];
+  if (n > 0) k_inner_kappa_table<T><<<blocks_for(n, 256), 256, 0, st>>>(g, kin, n);
+}
+template void launch_inner_kappa_table<float>(const Grid&, float*, cudaStream_t);
+template void launch_inner_kappa_table<double>(const Grid&, double*, cudaStream_t);
 
 // Dynamic shared memory of the field kernels (above the 48 KB default): set once per kernel.
 template <typename K>

@@ -51,6 +51,7 @@ struct grpic_ctx {
   grpic_tuning tune{4, 4, 1, 1, 0, 0, 1};
   void* fields = nullptr;  // 12 planes of T: d buffers 0 and 1 (3 planes each), b buffers 0 and 1
   void* tgt = nullptr;     // absorbing layers: 6 planes of T, the target d and b (null without layers)
+  void* kin = nullptr;     // inner absorbing layer: relaxation table over g.kbox0 / g.kboxn (T)
   double* J = nullptr;     // 3 planes
   uint16_t* loc = nullptr;  // per-cell location flags
   // field ping-pong state: buffer of the current d and b; bprev: buffer holding b^{n-1/2} after the
@@ -285,6 +286,7 @@ void enqueue_stage(grpic_ctx* c, int stage) {
         A.d[q] = F.d[q];
         A.tgt[q] = second ? target_plane<T>(c, 3 + q) : nullptr;
       }
+      A.kin = static_cast<const T*>(c->kin);
       A.loc = c->loc;
       A.K = field_consts<T>(c->g);
       const T dx4 = grid_dx4<T>(c->g);
@@ -326,6 +328,7 @@ void enqueue_stage(grpic_ctx* c, int stage) {
         A.J[q] = F.J[q];
         A.tgt[q] = target_plane<T>(c, q);
       }
+      A.kin = static_cast<const T*>(c->kin);
       A.loc = c->loc;
       A.K = field_consts<T>(c->g);
       A.pred = !literal_fields(c);
@@ -525,6 +528,23 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.inv_w = 1.0 / g.w_out;
   g.k_out_f = (float)g.k_out;
   g.inv_w_f = (float)g.inv_w;
+  // box of cells around the hole holding every location with r < r_+: there r^2 >= R^2 - a^2, so
+  // R < sqrt(r_+^2 + a^2), and a location lies within half a cell of its cell's corner
+  long long kin_cells = 0;
+  for (int ax = 0; ax < 3; ++ax) g.kbox0[ax] = g.kboxn[ax] = 0;
+  if (g.k_in > 0.0 && g.m > 0.0) {
+    const double hw = std::sqrt(g.r_abs * g.r_abs + g.a * g.a) + 1.0;
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    const double cen[3] = {g.xc, g.yc, g.zc};
+    kin_cells = 1;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int lo = std::max(2, (int)std::floor(cen[ax] - hw));
+      const int hi = std::min(n3[ax] - 3, (int)std::ceil(cen[ax] + hw));
+      g.kbox0[ax] = lo;
+      g.kboxn[ax] = std::max(0, hi - lo + 1);
+      kin_cells *= g.kboxn[ax];
+    }
+  }
   g.quad_order = c->cfg.quad_order;
   g.flags = cfg->flags;
   g.r_fp64 = (cfg->fp64_radius == 0.0 ? 4.0 : cfg->fp64_radius) * cfg->m;
@@ -537,6 +557,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   c->fields = dev_alloc(c, 12 * (size_t)ncell * c->tsize);
   const bool layers = g.k_in > 0.0 || g.k_out > 0.0;
   if (layers) c->tgt = dev_alloc(c, 6 * (size_t)ncell * c->tsize);
+  if (kin_cells > 0) c->kin = dev_alloc(c, 6 * (size_t)kin_cells * c->tsize);
   c->J = static_cast<double*>(dev_alloc(c, 3 * (size_t)ncell * sizeof(double)));
   c->loc = static_cast<uint16_t*>(dev_alloc(c, sizeof(uint16_t) * (size_t)ncell));
   c->st = static_cast<DevStatus*>(dev_alloc(c, sizeof(DevStatus)));
@@ -546,7 +567,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   c->sort.offsets = static_cast<int*>(dev_alloc(c, sizeof(int) * nbins));
   c->sort.blocks = static_cast<int*>(dev_alloc(c, sizeof(int) * (c->sort.nblocks + 1)));
   bool ok = c->fields && c->J && c->loc && c->st && c->sort.counts && c->sort.offsets && c->sort.blocks &&
-            (c->tgt || !layers);
+            (c->tgt || !layers) && (c->kin || kin_cells == 0);
   for (int s = 0; s < kMaxSpecies && ok; ++s) {
     c->sp[s].n_dev = static_cast<int*>(dev_alloc(c, sizeof(int)));
     c->sp[s].near_n = static_cast<int*>(dev_alloc(c, 2 * sizeof(int)));
@@ -574,6 +595,12 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
   for (int s = 0; s < kMaxSpecies; ++s) cudaMemsetAsync(c->sp[s].n_dev, 0, sizeof(int), c->stream);
   launch_location_flags(g, c->loc, c->stream);
+  if (c->kin) {
+    if (c->mixed)
+      launch_inner_kappa_table<float>(g, static_cast<float*>(c->kin), c->stream);
+    else
+      launch_inner_kappa_table<double>(g, static_cast<double*>(c->kin), c->stream);
+  }
   grpic_status s = cuda_check(c, cudaGetLastError(), "create");
   if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "create sync");
   if (s != GRPIC_OK) {
@@ -589,6 +616,7 @@ grpic_status grpic_destroy(grpic_ctx* c) {
   cudaStreamSynchronize(c->stream);
   dev_free(c, c->fields);
   dev_free(c, c->tgt);
+  dev_free(c, c->kin);
   dev_free(c, c->J);
   dev_free(c, c->loc);
   dev_free(c, c->st);
@@ -1187,6 +1215,7 @@ grpic_status batch_build(grpic_batch* b) {
       D.FS.J[q] = c->J + (size_t)q * c->g.ncell;
     }
     for (int q = 0; q < 6; ++q) D.FS.tgt[q] = target_plane<T>(c, q);
+    D.FS.kin = static_cast<const T*>(c->kin);
     D.FS.loc = c->loc;
     D.dcur = b->dcur + i;
     dcur_init[i] = c->dcur;
