@@ -92,8 +92,13 @@ __device__ __forceinline__ void warp_sum_max(double v, double* sum, unsigned lon
 template <typename T>
 __global__ void k_max_id(const Particles<T> P, unsigned long long* max_id) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= P.n || i >= (long long)(*P.n_dev) || P.key[i] == kDead) return;
-  atomicMax(max_id, (unsigned long long)P.id[i]);
+  const bool live = i < P.n && i < (long long)(*P.n_dev) && P.key[i] != kDead;
+  // ids are 32-bit: one warp maximum, then one atomic per warp (a live id may be 0, so the warp
+  // publishes only when it has a live particle)
+  const unsigned v = live ? P.id[i] : 0u;
+  const unsigned m = __reduce_max_sync(0xffffffffu, v);
+  const unsigned any = __ballot_sync(0xffffffffu, live);
+  if (any && (threadIdx.x & 31) == 0) atomicMax(max_id, (unsigned long long)m);
 }
 
 // mode 0: record E and L of the tracked particles (id % stride == 0) at slot id / stride; mode 1:
