@@ -51,7 +51,8 @@ class _Cfg(ctypes.Structure):
                 ("m", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double),
                 ("dt", ctypes.c_double), ("quad_order", ctypes.c_int),
                 ("r_excise", ctypes.c_double), ("flags", ctypes.c_uint), ("threads", ctypes.c_int),
-                ("absorb_inner", ctypes.c_double), ("absorb_outer", ctypes.c_double), ("absorb_width", ctypes.c_int)]
+                ("absorb_inner", ctypes.c_double), ("absorb_outer", ctypes.c_double), ("absorb_width", ctypes.c_int),
+                ("z_origin", ctypes.c_int), ("nz_total", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -245,17 +246,18 @@ class Oracle:
     """One oracle simulation context (grid, metric, fields, particles)."""
 
     def __init__(self, nx, ny, nz, m, a, c, dt, quad_order=2, r_excise=0.0, flags=0, threads=1, absorb_inner=0.0,
-                 absorb_outer=0.0, absorb_width=0):
+                 absorb_outer=0.0, absorb_width=0, z_origin=0, nz_total=0):
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
         cfg = _Cfg(nx, ny, nz, m, a, c, dt, quad_order, r_excise, flags, threads, absorb_inner, absorb_outer,
-                   absorb_width)
+                   absorb_width, z_origin, nz_total)
         self._h = lib().orc_create(ctypes.byref(cfg))
         if not self._h:
             raise ValueError("invalid oracle configuration")
         self.cfg = dict(nx=nx, ny=ny, nz=nz, m=m, a=a, c=c, dt=dt, quad_order=quad_order,
                         r_excise=r_excise, flags=flags, threads=threads, absorb_inner=absorb_inner,
-                        absorb_outer=absorb_outer, absorb_width=absorb_width)
+                        absorb_outer=absorb_outer, absorb_width=absorb_width, z_origin=z_origin,
+                        nz_total=nz_total)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -278,7 +280,8 @@ class Oracle:
 
     @property
     def centre(self):
-        return np.array([(self.cfg["nx"] - 1) / 2, (self.cfg["ny"] - 1) / 2, (self.cfg["nz"] - 1) / 2])
+        nzt = self.cfg["nz_total"] or self.cfg["nz"]
+        return np.array([(self.cfg["nx"] - 1) / 2, (self.cfg["ny"] - 1) / 2, (nzt - 1) / 2 - self.cfg["z_origin"]])
 
     def set_fields(self, d, b):
         d = _f64(d, (3,) + self.shape)

@@ -66,6 +66,10 @@
  *       with a rapidly rotating hole, reflection inside the horizon feeds a mode growing next to
  *       it, and frozen faces where the metric is far from flat feed one at the box edges.
  *
+ *   A24 (not in the paper) A grid may be one slab of a larger run: planes z_origin ..
+ *       z_origin + nz - 1 of nz_total, the hole at the whole run's centre.  Everything else is as
+ *       for a whole grid; a driver that splits a run refreshes the slabs' overlapping planes.
+ *
  * Parity status: every function is pinned by a CPU test against closed forms, invariants
  * or brute force.  The RK4 steps exactly as printed in Sec. 3.3 have no consistent reading
  * (parity unpinned for that literal form).  For an ablation ORC_RK4_AS_PRINTED takes the
@@ -457,6 +461,9 @@ typedef struct {
   int threads;  // <= 0: all available
   double absorb_inner, absorb_outer;  // A23: relaxation per step at the layers' deepest points (0: none)
   int absorb_width;                   // outer layer width in cells (<= 0: 8)
+  // A24: this grid as planes z_origin .. z_origin + nz - 1 of a run whose grid has nz_total planes
+  // (0: nz); the hole sits at the centre of the whole run's grid
+  int z_origin, nz_total;
 } orc_config;
 
 }  // extern "C"
@@ -1331,6 +1338,14 @@ void* orc_create(const orc_config* cfg) {
   ctx->n[1] = cfg->ny;
   ctx->n[2] = cfg->nz;
   for (int ax = 0; ax < 3; ++ax) ctx->Xc[ax] = 0.5 * (ctx->n[ax] - 1);
+  // A24: a slab of a larger run keeps the run's centre
+  const int nz_total = cfg->nz_total > 0 ? cfg->nz_total : cfg->nz;
+  const bool slab = cfg->z_origin != 0 || nz_total != cfg->nz;
+  if (cfg->z_origin < 0 || cfg->z_origin + cfg->nz > nz_total || (slab && cfg->absorb_outer > 0.0)) {
+    delete ctx;
+    return nullptr;
+  }
+  ctx->Xc[2] = 0.5 * (nz_total - 1) - cfg->z_origin;
   ctx->r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
   if (!(cfg->absorb_inner >= 0.0 && cfg->absorb_inner <= 1.0 && cfg->absorb_outer >= 0.0 &&
         cfg->absorb_outer <= 1.0)) {
