@@ -126,6 +126,13 @@ typedef struct {
   double absorb_outer;   /* absorbing layer at the box faces: relaxation per step at the first advanced
                             cell, falling as ((W + 1 - s) / W)^2 to the s = W-th; 0 -> none.  In [0, 1] */
   int absorb_width;      /* W, in cells (<= 0 -> 8) */
+  int z_origin;          /* this context's grid as planes z_origin .. z_origin + nz - 1 of a run whose grid has
+                            nz_total planes (one z-slab of a run split across contexts, see
+                            paper_0904_0232_gb300/slab.py): the hole sits at the run's centre, z_c =
+                            (nz_total - 1)/2 - z_origin; the slab's edge planes are held like faces, so
+                            a driver refreshes them from the neighbouring slabs.  0 with nz_total 0:
+                            a whole grid.  An outer absorbing layer needs a whole grid */
+  int nz_total;          /* planes of the whole run (0 -> nz) */
   grpic_alloc_fn alloc;  /* device allocator (NULL -> cudaMalloc); e.g. a PyTorch caching allocator */
   grpic_free_fn free_fn; /* matching free */
   void* alloc_user;      /* passed to alloc / free_fn */

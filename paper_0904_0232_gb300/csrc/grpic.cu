@@ -498,6 +498,11 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   if (!(cfg->absorb_inner >= 0.0 && cfg->absorb_inner <= 1.0 && cfg->absorb_outer >= 0.0 &&
         cfg->absorb_outer <= 1.0))
     return GRPIC_ERR_INVALID;
+  // one z-slab of a larger run: inside the run's planes; the outer layer's faces would not be its own
+  const int nz_total = cfg->nz_total > 0 ? cfg->nz_total : cfg->nz;
+  const bool slab = cfg->z_origin != 0 || nz_total != cfg->nz;
+  if (cfg->z_origin < 0 || cfg->z_origin + cfg->nz > nz_total || (slab && cfg->absorb_outer > 0.0))
+    return GRPIC_ERR_INVALID;
 
   grpic_ctx* c = new grpic_ctx();
   c->cfg = *cfg;
@@ -518,7 +523,7 @@ grpic_status grpic_create(const grpic_config* cfg, void* stream, grpic_ctx** out
   g.dt = cfg->dt;
   g.xc = 0.5 * (cfg->nx - 1);
   g.yc = 0.5 * (cfg->ny - 1);
-  g.zc = 0.5 * (cfg->nz - 1);
+  g.zc = 0.5 * (nz_total - 1) - cfg->z_origin;
   g.r_plus = cfg->m + std::sqrt(std::max(0.0, cfg->m * cfg->m - cfg->a * cfg->a));
   g.r_exc = cfg->r_excise > 0.0 ? cfg->r_excise : (cfg->absorb_inner > 0.0 ? 0.5 : 1.0) * g.r_plus;
   g.k_in = cfg->absorb_inner;

@@ -254,8 +254,9 @@ grpic_status grpic_server_create(size_t hbm_budget, int max_slots, grpic_alloc_f
 
 grpic_status grpic_submit(grpic_server* s, const grpic_request* req, uint64_t* ticket) {
   if (!s || !req || !ticket || req->nspecies < 1 || req->nspecies > 4 || req->ppc < 0 || req->nsteps < 0 ||
-      req->cfg.nx < 8 || req->cfg.ny < 8 || req->cfg.nz < 8)
-    return GRPIC_ERR_INVALID;
+      req->cfg.nx < 8 || req->cfg.ny < 8 || req->cfg.nz < 8 || req->cfg.z_origin != 0 ||
+      (req->cfg.nz_total != 0 && req->cfg.nz_total != req->cfg.nz))
+    return GRPIC_ERR_INVALID;  // (a served run is a whole grid)
   const int quad = req->cfg.quad_order == 0 ? 2 : req->cfg.quad_order;
   if (s->have_kind && (req->cfg.precision != s->precision || quad != s->quad || req->cfg.flags != s->flags))
     return GRPIC_ERR_INVALID;

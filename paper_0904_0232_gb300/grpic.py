@@ -41,6 +41,7 @@ class grpic_config(ctypes.Structure):
                 ("flags", ctypes.c_uint), ("sort_interval", ctypes.c_int), ("max_particles", ctypes.c_int64),
                 ("fp64_radius", ctypes.c_double), ("absorb_inner", ctypes.c_double),
                 ("absorb_outer", ctypes.c_double), ("absorb_width", ctypes.c_int),
+                ("z_origin", ctypes.c_int), ("nz_total", ctypes.c_int),
                 ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_user", ctypes.c_void_p)]
 
 
@@ -506,7 +507,7 @@ class Simulation:
 
     def __init__(self, nx, ny, nz, m, a, c, dt, precision="fp64", quad_order=2, r_excise=0.0, flags=0,
                  sort_interval=1, max_particles=0, stream=None, torch_allocator=True, fp64_radius=0.0,
-                 absorb_inner=0.0, absorb_outer=0.0, absorb_width=0):
+                 absorb_inner=0.0, absorb_outer=0.0, absorb_width=0, z_origin=0, nz_total=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("GRPIC needs a CUDA device")
@@ -514,7 +515,7 @@ class Simulation:
         self.shape = (nz, ny, nx)
         prec = {"fp64": GRPIC_FP64, "fp32_mixed": GRPIC_FP32_MIXED}[precision]
         cfg = grpic_config(nx, ny, nz, m, a, c, dt, prec, quad_order, r_excise, flags, sort_interval, max_particles,
-                           fp64_radius, absorb_inner, absorb_outer, absorb_width)
+                           fp64_radius, absorb_inner, absorb_outer, absorb_width, z_origin, nz_total)
         if torch_allocator:
             cfg.alloc = _torch_alloc
             cfg.free_fn = _torch_free
