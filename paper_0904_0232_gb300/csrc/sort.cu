@@ -132,27 +132,54 @@ __global__ void k_live_count(const int* __restrict__ offsets, long long dead_bin
   *n_out = offsets[dead_bin];
 }
 
+// Each thread moves kScatterItems records, from kScatterItems consecutive blocks' worth of the store
+// (chunk j of block b covers [(b * items + j) * blockDim, ...)), so a warp's lanes stay contiguous.
+// Every record and key is read before any slot is known, so that the record loads and the atomics
+// are in flight together (k_scatter at 96^3: 145 -> 122 us).  Two items per thread measured the
+// same as one.
+constexpr int kScatterItems = 1;
+
 template <typename T>
 __global__ void k_scatter(const Particles<T> src, const Particles<T> dst, int* __restrict__ cursor,
                           long long dead_bin) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool in_range = i < src.n && i < (long long)(*src.n_dev);
-  const uint32_t k = in_range ? src.key[i] : kDead;
-  // one atomic per run of lanes with the same cell, each lane at its rank in the run; removed
-  // particles form runs of their own and take no slot
-  const KeyRun r = key_run(in_range, k);
-  const int lane = threadIdx.x & 31;
-  int first = 0;
-  if (r.head && k != kDead) first = atomicAdd(cursor + k, r.len);
-  const int pos = __shfl_sync(0xffffffffu, first, r.first) + (lane - r.first);
-  if (!in_range || k == kDead) return;
+  const long long live_n = min(src.n, (long long)(*src.n_dev));
+  uint32_t k[kScatterItems], idv[kScatterItems];
+  T xv[kScatterItems][4], uv[kScatterItems][4];
+  bool in_range[kScatterItems];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    dst.x[q][pos] = src.x[q][i];
-    dst.u[q][pos] = src.u[q][i];
+  for (int j = 0; j < kScatterItems; ++j) {
+    const long long i = ((long long)blockIdx.x * kScatterItems + j) * blockDim.x + threadIdx.x;
+    in_range[j] = i < live_n;
+    k[j] = in_range[j] ? src.key[i] : kDead;
+    idv[j] = 0;
+    if (in_range[j] && k[j] != kDead) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xv[j][q] = src.x[q][i];
+        uv[j][q] = src.u[q][i];
+      }
+      idv[j] = src.id[i];
+    }
   }
-  dst.id[pos] = src.id[i];
-  dst.key[pos] = k;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kScatterItems; ++j) {
+    // one atomic per run of lanes with the same cell, each lane at its rank in the run; removed
+    // particles form runs of their own and take no slot
+    const KeyRun r = key_run(in_range[j], k[j]);
+    int first = 0;
+    if (r.head && k[j] != kDead) first = atomicAdd(cursor + k[j], r.len);
+    const int pos = __shfl_sync(0xffffffffu, first, r.first) + (lane - r.first);
+    if (in_range[j] && k[j] != kDead) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        dst.x[q][pos] = xv[j][q];
+        dst.u[q][pos] = uv[j][q];
+      }
+      dst.id[pos] = idv[j];
+      dst.key[pos] = k[j];
+    }
+  }
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -197,19 +224,30 @@ __global__ void k_batch_scatter(const InstDesc<T>* __restrict__ desc, const Bloc
     const long long i = (long long)e.block * blockDim.x + threadIdx.x;
     const bool in_range = i < src.n && i < (long long)(*src.n_dev);
     const uint32_t k = in_range ? src.key[i] : kDead;
+    const bool live = in_range && k != kDead;
+    T xv[4], uv[4];
+    uint32_t idv = 0;
+    if (live) {  // read ahead of the atomic, as in k_scatter
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xv[q] = src.x[q][i];
+        uv[q] = src.u[q][i];
+      }
+      idv = src.id[i];
+    }
     const KeyRun r = key_run(in_range, k);
     const int lane = threadIdx.x & 31;
     int first = 0;
     if (r.head && k != kDead) first = atomicAdd(cursor + S.bin_base + k, r.len);
     const int run0 = __shfl_sync(0xffffffffu, first, r.first);  // every lane takes part
-    if (!in_range || k == kDead) continue;
+    if (!live) continue;
     const int pos = run0 + (lane - r.first) - base[pair_of_inst[e.inst]];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      dst.x[q][pos] = src.x[q][i];
-      dst.u[q][pos] = src.u[q][i];
+      dst.x[q][pos] = xv[q];
+      dst.u[q][pos] = uv[q];
     }
-    dst.id[pos] = src.id[i];
+    dst.id[pos] = idv;
     dst.key[pos] = k;
   }
 }
@@ -244,7 +282,8 @@ void launch_sort(const Grid& g, const Particles<T>& src, const Particles<T>& dst
   k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(s.counts, nbins, s.blocks, s.offsets);
   // scatter first: it reads the old count through src.n_dev, which may alias n_out.  Removed
   // particles never take a slot, so the cursor of the removed bin still holds the live count.
-  if (src.n > 0) k_scatter<T><<<blocks_for(src.n, 256), 256, 0, stream>>>(src, dst, s.offsets, dead_bin);
+  if (src.n > 0)
+    k_scatter<T><<<blocks_for(src.n, 256 * kScatterItems), 256, 0, stream>>>(src, dst, s.offsets, dead_bin);
   k_live_count<<<1, 1, 0, stream>>>(s.offsets, dead_bin, n_out);
 }
 
