@@ -524,11 +524,15 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
 #pragma unroll 1
   for (int seg = 0; seg < 2; ++seg) {
     const int cx = seg ? c2[0] : c1[0], cy = seg ? c2[1] : c1[1], cz = seg ? c2[2] : c1[2];
-    float P[3], dseg[3];
+    // fr: the segment midpoint's position within the segment's cell, from x0 - c (exact: the two are
+    // within two cells of each other) plus the small offset, so that the sub-rectangle widths keep
+    // FP32's relative precision instead of the absolute rounding of a grid coordinate (~4e-6 cells at
+    // coordinates near 100); the midpoint itself is c + fr
+    float dseg[3], fr[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       dseg[ax] = seg ? s2[ax] : s1[ax];
-      P[ax] = seg ? x0[ax] + (s1[ax] + 0.5f * s2[ax]) : x0[ax] + 0.5f * s1[ax];
+      fr[ax] = seg ? (x0[ax] - (float)c2[ax]) + (s1[ax] + 0.5f * s2[ax]) : (x0[ax] - (float)c1[ax]) + 0.5f * s1[ax];
     }
     const long long base = ((long long)cz * g.ny + cy) * g.nx + cx;
 #pragma unroll 1
@@ -538,18 +542,19 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float flux = qg * dK * inv_dt;
       FaceLattice L;
       L.K = K;
-      L.PK = sel3(K, P[0], P[1], P[2]);
-      L.XK = L.PK - sel3(K, cen[0], cen[1], cen[2]);
-      L.PI = sel3(K, P[1], P[2], P[0]);
-      L.PJ = sel3(K, P[2], P[0], P[1]);
+      const float frI = sel3(K, fr[1], fr[2], fr[0]), frJ = sel3(K, fr[2], fr[0], fr[1]);
       L.i0 = (float)sel3(K, cy, cz, cx);
       L.j0 = (float)sel3(K, cz, cx, cy);
+      L.PK = (float)sel3(K, cx, cy, cz) + sel3(K, fr[0], fr[1], fr[2]);
+      L.XK = L.PK - sel3(K, cen[0], cen[1], cen[2]);
+      L.PI = L.i0 + frI;
+      L.PJ = L.j0 + frJ;
       L.cI = sel3(K, cen[1], cen[2], cen[0]);
       L.cJ = sel3(K, cen[2], cen[0], cen[1]);
       // sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J)
-      L.wI0 = L.PI - L.i0;
-      L.wI1 = L.i0 + 1.f - L.PI;
-      const float wJ[2] = {L.PJ - L.j0, L.j0 + 1.f - L.PJ};
+      L.wI0 = frI;
+      L.wI1 = 1.f - frI;
+      const float wJ[2] = {frJ, 1.f - frJ};
       // Per node the quartic needs p = R^2 - a^2 and q = a^2 z^2, k_K's numerator the spin term
       // -a x^I (K = 0) or +a x^J (K = 1); z is x^K, x^I or x^J (K = 2, 1, 0).  Each of these is a
       // sum of a face constant, a row term and a column term.

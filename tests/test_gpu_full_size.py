@@ -102,3 +102,49 @@ def test_full_size_step(workload, oracle_fields, prec):
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.all(np.abs(jsum - flux_total) <= tol * flux_abs), (jsum, flux_total, flux_abs)
     sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32_mixed", "fp64"])
+@pytest.mark.parametrize("shapes", ["default", "tuned"])
+def test_full_size_j_element_by_element(workload, oracle_fields, prec, shapes):
+    """J node by node at the full 128^3 grid size: a strided 1/500 sample of both species (plus the
+    300 particles of each closest to the hole) pushed and deposited into an empty J by a context of
+    the bench's grid with the bench's launch shapes ("tuned": the per-warp select push with chunks
+    spread in groups of 16, as the autotuner picks for this workload; "default": single chunks), and
+    by the oracle, from the fields after the first B half-step.  Every J node is compared (FP32: off
+    the nodes of zig-zag splits decided within rounding of a face, and the total flux everywhere).
+    Both sides start from positions representable in FP32: a grid coordinate near 100 rounds to FP32
+    with an absolute error up to 4e-6 cells, which alone moves a sub-rectangle width of Eq. 18 by
+    ~1e-5 of itself."""
+    from parity_util import check_j
+
+    wl = workload
+    ref0 = oracle_fields
+    dr, br, _ = ref0.get_fields()
+    cen = np.array([(wl.nx - 1) / 2] * 3).reshape(3, 1)
+    ref = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=0, flags=O.NO_GAMMA_TERMS)
+    ref.set_fields(dr, br)
+    sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=prec)
+    if prec == "fp32_mixed" and shapes == "tuned":
+        sim.set_tuning(far_min_blocks=4, near_blocks_per_sm=1, sort_interval=4, overlap=0, split=0, j_tile=0,
+                       spread=16)
+    sim.set_fields(dr, br)
+    n = 0
+    for s, sp in enumerate(wl.species):
+        R = np.sqrt(((sp.x4[:3] - cen) ** 2).sum(0))
+        pick = np.unique(np.concatenate([np.arange(0, sp.ids.size, 500), np.argsort(R)[:300]]))
+        x32 = sp.x4[:, pick].astype(np.float32).astype(np.float64)
+        ref.load_particles(s, sp.q_over_m, sp.q_macro, x32, sp.usp[:, pick], sp.ids[pick], umode=1)
+        x, u, i = ref.get_particles(s)  # u^a completed by the oracle, loaded as is by the library
+        sim.load_particles(s, sp.q_over_m, sp.q_macro, x, u, i)
+        n += i.size
+    assert n > 60000
+    ref.zero_j()
+    ref.push_deposit()
+    sim.stage(GRPIC_STAGE_ZERO_J)
+    sim.stage(GRPIC_STAGE_PUSH_DEPOSIT)
+    J = sim.get_fields()[2]
+    Jr = ref.get_fields()[2]
+    mask = check_j(J, Jr, ref, len(wl.species), prec)
+    print("full-size J", prec, shapes, "rel L2", rel_l2(J, Jr), "masked node fraction", mask.mean())
+    sim.close()
