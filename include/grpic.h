@@ -202,6 +202,19 @@ grpic_status grpic_sync(grpic_ctx* ctx);
  * GRPIC_MEM_DEVICE for the destination.  FP32-mixed contexts widen their FP32 fields. */
 grpic_status grpic_get_fields(grpic_ctx* ctx, double* d3, double* b3, double* J3, int mem);
 
+/* A range of z-planes of one field, for a driver that splits one run into z-slabs across contexts
+ * and exchanges the planes next to a neighbour's (not in the paper).  which: GRPIC_FIELD_D (the
+ * contravariant F^{i4} of Eq. 12's update), GRPIC_FIELD_B (the covariant F_{yz}, F_{zx}, F_{xy} of
+ * Eq. 10's), GRPIC_FIELD_J (the current density of Sec. 4); planes z0 .. z0 + nplanes - 1 of each of
+ * the three components, FP64, component-major: buf[(q * nplanes + z - z0) * ny * nx + y * nx + x].
+ * The current buffers, as grpic_get_fields / grpic_set_fields see them.  grpic_set_planes writes the
+ * planes (FP32_MIXED rounds d and b) or, with add = 1, adds into them (J only).  buf is host or device
+ * memory by mem; the caller owns it.  GRPIC_ERR_INVALID for a range outside the grid, an unknown
+ * field or add on d or b. */
+enum { GRPIC_FIELD_D = 0, GRPIC_FIELD_B = 1, GRPIC_FIELD_J = 2 };
+grpic_status grpic_get_planes(grpic_ctx* ctx, int which, int z0, int nplanes, double* buf, int mem);
+grpic_status grpic_set_planes(grpic_ctx* ctx, int which, int z0, int nplanes, const double* buf, int mem, int add);
+
 /* Number of live particles of a species. */
 grpic_status grpic_num_particles(grpic_ctx* ctx, int species, int64_t* n);
 

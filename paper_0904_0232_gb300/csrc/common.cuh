@@ -180,6 +180,8 @@ template <typename T>
 void launch_convert_in(T* dst, const double* src, long long n, cudaStream_t st);
 template <typename T>
 void launch_convert_out(double* dst, const T* src, long long n, cudaStream_t st);
+// dst[i] += src[i], FP64
+void launch_add_f64(double* dst, const double* src, long long n, cudaStream_t st);
 
 struct Species {
   double qm, qmacro;

@@ -901,6 +901,15 @@ void launch_uniform_field(const Grid& g, const Fields<T>& F, const double E[3], 
   k_uniform_field<T><<<blocks_for(g.ncell, 256), 256, 0, st>>>(g, F, E[0], E[1], E[2], B[0], B[1], B[2]);
 }
 
+__global__ void k_add_f64(double* __restrict__ dst, const double* __restrict__ src, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
+void launch_add_f64(double* dst, const double* src, long long n, cudaStream_t st) {
+  if (n > 0) k_add_f64<<<blocks_for(n, 256), 256, 0, st>>>(dst, src, n);
+}
+
 template <typename T>
 void launch_convert_in(T* dst, const double* src, long long n, cudaStream_t st) {
   k_convert_in<T><<<blocks_for(n, 256), 256, 0, st>>>(dst, src, n);

@@ -841,6 +841,77 @@ grpic_status grpic_get_fields(grpic_ctx* c, double* d3, double* b3, double* J3, 
   return s;
 }
 
+// Planes z0 .. z0 + n - 1 of component q of field `which` (the current buffer), as a pointer of T
+// (d, b) or double (J); count = n planes of nx * ny.
+static bool plane_range_ok(const grpic_ctx* c, int which, int z0, int n) {
+  return c && which >= GRPIC_FIELD_D && which <= GRPIC_FIELD_J && z0 >= 0 && n >= 0 && z0 + n <= c->g.nz;
+}
+
+grpic_status grpic_get_planes(grpic_ctx* c, int which, int z0, int nplanes, double* buf, int mem) {
+  if (!plane_range_ok(c, which, z0, nplanes) || (!buf && nplanes > 0)) return GRPIC_ERR_INVALID;
+  const long long plane = (long long)c->g.nx * c->g.ny, count = plane * nplanes;
+  if (count == 0) return GRPIC_OK;
+  const cudaMemcpyKind kind = mem == GRPIC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* tmp = nullptr;
+  if (which != GRPIC_FIELD_J && c->mixed) {
+    tmp = static_cast<double*>(dev_alloc(c, sizeof(double) * 3 * count));
+    if (!tmp) return fail(c, GRPIC_ERR_OOM, "staging allocation failed");
+  }
+  for (int q = 0; q < 3; ++q) {
+    double* dst = buf + q * count;
+    if (which == GRPIC_FIELD_J) {
+      cudaMemcpyAsync(dst, c->J + (size_t)q * c->g.ncell + z0 * plane, sizeof(double) * count, kind, c->stream);
+    } else {
+      const bool is_b = which == GRPIC_FIELD_B;
+      const int cur = is_b ? c->bcur : c->dcur;
+      if (c->mixed) {
+        launch_convert_out<float>(tmp + q * count, field_plane<float>(c, is_b, cur, q) + z0 * plane, count,
+                                  c->stream);
+        cudaMemcpyAsync(dst, tmp + q * count, sizeof(double) * count, kind, c->stream);
+      } else {
+        cudaMemcpyAsync(dst, field_plane<double>(c, is_b, cur, q) + z0 * plane, sizeof(double) * count, kind,
+                        c->stream);
+      }
+    }
+  }
+  grpic_status s = cuda_check(c, cudaStreamSynchronize(c->stream), "get_planes");
+  if (tmp) dev_free(c, tmp);
+  return s;
+}
+
+grpic_status grpic_set_planes(grpic_ctx* c, int which, int z0, int nplanes, const double* buf, int mem, int add) {
+  if (!plane_range_ok(c, which, z0, nplanes) || (!buf && nplanes > 0) || (add && which != GRPIC_FIELD_J))
+    return GRPIC_ERR_INVALID;
+  const long long plane = (long long)c->g.nx * c->g.ny, count = plane * nplanes;
+  if (count == 0) return GRPIC_OK;
+  const void* src;
+  void* tmp;
+  grpic_status s = stage_in(c, buf, sizeof(double) * 3 * count, mem, &src, &tmp);
+  if (s != GRPIC_OK) return s;
+  const double* in = static_cast<const double*>(src);
+  for (int q = 0; q < 3; ++q) {
+    if (which == GRPIC_FIELD_J) {
+      double* J = c->J + (size_t)q * c->g.ncell + z0 * plane;
+      if (add)
+        launch_add_f64(J, in + q * count, count, c->stream);
+      else
+        cudaMemcpyAsync(J, in + q * count, sizeof(double) * count, cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+      const bool is_b = which == GRPIC_FIELD_B;
+      const int cur = is_b ? c->bcur : c->dcur;
+      if (c->mixed)
+        launch_convert_in<float>(field_plane<float>(c, is_b, cur, q) + z0 * plane, in + q * count, count, c->stream);
+      else
+        cudaMemcpyAsync(field_plane<double>(c, is_b, cur, q) + z0 * plane, in + q * count, sizeof(double) * count,
+                        cudaMemcpyDeviceToDevice, c->stream);
+    }
+  }
+  s = cuda_check(c, cudaGetLastError(), "set_planes");
+  release_tmp(c, tmp);
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_planes sync");
+  return s;
+}
+
 grpic_status grpic_num_particles(grpic_ctx* c, int species, int64_t* n) {
   if (!c || !n || species < 0 || species >= kMaxSpecies) return GRPIC_ERR_INVALID;
   SpeciesStore& S = c->sp[species];

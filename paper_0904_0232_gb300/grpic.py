@@ -80,6 +80,10 @@ EXPORTS = {
     "grpic_set_uniform_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double)]),
     "grpic_set_j": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_get_planes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int]),
+    "grpic_set_planes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int]),
     "grpic_load_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int]),
@@ -300,6 +304,28 @@ def grpic_get_fields(ctx, shape):
                                                 J.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST),
            "grpic_get_fields")
     return d, b, J
+
+
+GRPIC_FIELD_D, GRPIC_FIELD_B, GRPIC_FIELD_J = 0, 1, 2
+
+
+def grpic_get_planes(ctx, which, z0, nplanes, shape):
+    """Planes z0 .. z0 + nplanes - 1 of field `which` (GRPIC_FIELD_D / _B / _J): a (3, nplanes, ny, nx)
+    float64 array.  shape: the context's (nz, ny, nx)."""
+    out = np.zeros((3, int(nplanes)) + tuple(shape[1:]))
+    _check(ctx, load_library().grpic_get_planes(ctx, int(which), int(z0), int(nplanes),
+                                                out.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST),
+           "grpic_get_planes")
+    return out
+
+
+def grpic_set_planes(ctx, which, z0, planes, add=False):
+    """Write (or, for J with add, add into) planes z0 .. z0 + n - 1 of field `which` from a
+    (3, n, ny, nx) array."""
+    pa, mem, keep = _as_arg(planes, np.float64)
+    n = int(planes.shape[1])
+    _check(ctx, load_library().grpic_set_planes(ctx, int(which), int(z0), n, pa, mem, int(bool(add))),
+           "grpic_set_planes")
 
 
 def grpic_get_stats(ctx):
@@ -567,6 +593,12 @@ class Simulation:
 
     def get_particles(self, species, device=False):
         return grpic_get_particles(self.handle, species, device=device)
+
+    def get_planes(self, which, z0, nplanes):
+        return grpic_get_planes(self.handle, which, z0, nplanes, self.shape)
+
+    def set_planes(self, which, z0, planes, add=False):
+        grpic_set_planes(self.handle, which, z0, planes, add)
 
     def num_particles(self, species):
         return grpic_num_particles(self.handle, species)

@@ -23,17 +23,15 @@ particle moves less than a cell per step (the step limit), so its push and depos
 two planes past the plane it starts in.  With the ghost planes refreshed after every field stage,
 every owned plane then sees exactly what it would see in the whole run.
 
-The engine of a rank is any object with ``stage(name)`` for the stage names below, ``get_fields()``
--> (d, b, J) host arrays (3, nz_local, ny, nx), ``set_fields(d, b)``, ``set_j(J)``,
+The engine of a rank is any object with ``stage(name)`` for the stage names below,
+``get_planes(which, z0, n)`` -> a (3, n, ny, nx) float64 array of planes z0 .. z0 + n - 1 (local) of
+field which in "d", "b", "J", ``set_planes(which, z0, planes, add=False)`` (add: J only),
 ``get_particles(s)`` -> (x4, u4, ids) with x4[2] in local planes and x^4 the particle's own clock, and
 ``load_particles(s, q_over_m, q_macro, x4, u4, ids)`` taking u^a as given.  ``LibraryEngine`` wraps a
-library context (one GPU each).  Messages are float64 vectors; ``DistTransport`` sends them with
-torch.distributed point-to-point calls (gloo or NCCL), ``LocalTransport`` hands them over within one
-process (all slabs in one process, e.g. one GPU holding several contexts).
-
-The exchange goes through host copies of the local grid (get/set of whole fields), so it is a
-correctness layer, not a fast path: a multi-GPU run would move only the GHOST planes, device to
-device.
+library context (one GPU each; the planes move through grpic_get_planes / grpic_set_planes).  Messages
+are float64 vectors; ``DistTransport`` sends them with torch.distributed point-to-point calls (gloo or
+NCCL), ``LocalTransport`` hands them over within one process (all slabs in one process, e.g. one GPU
+holding several contexts).  Only the GHOST planes next to a neighbour cross, through host memory.
 """
 from __future__ import annotations
 
@@ -75,10 +73,11 @@ class SlabRun:
 
     PHASES = ("b_half", "j_sum", "j_halo", "b_half2", "e", "migrate")
 
-    def __init__(self, plan: SlabPlan, rank: int, engine, species):
-        """species: list of (q_over_m, q_macro) per species index."""
+    def __init__(self, plan: SlabPlan, rank: int, engine, species, plane_shape=None):
+        """species: list of (q_over_m, q_macro) per species index; plane_shape: (ny, nx) of the run."""
         self.plan, self.rank, self.engine = plan, rank, engine
         self.species = list(species)
+        self.plane_shape = tuple(plane_shape) if plane_shape is not None else getattr(engine, "plane_shape", None)
         self.lo, self.hi = plan.local(rank)
         self.z0, self.z1 = plan.owned(rank)
 
@@ -112,24 +111,21 @@ class SlabRun:
         """{peer: float64 vector} to send after `phase`'s compute."""
         out = {}
         peers = self.plan.neighbours(self.rank)
+        e = self.engine
         if phase in ("b_half", "b_half2", "e"):
-            d, b, _ = self.engine.get_fields()
-            F = d if phase == "e" else b
+            which = "d" if phase == "e" else "b"
             for q in peers:
-                out[q] = np.ascontiguousarray(F[:, self._sl(*self._edge_for(q))]).ravel()
-        elif phase == "j_sum":
-            J = self.engine.get_fields()[2]
+                g0, g1 = self._edge_for(q)
+                out[q] = e.get_planes(which, g0 - self.lo, g1 - g0).ravel()
+        elif phase in ("j_sum", "j_halo"):
             for q in peers:
-                out[q] = np.ascontiguousarray(J[:, self._sl(*self._ghost_of(q))]).ravel()
-        elif phase == "j_halo":
-            J = self.engine.get_fields()[2]
-            for q in peers:
-                out[q] = np.ascontiguousarray(J[:, self._sl(*self._edge_for(q))]).ravel()
+                g0, g1 = self._ghost_of(q) if phase == "j_sum" else self._edge_for(q)
+                out[q] = e.get_planes("J", g0 - self.lo, g1 - g0).ravel()
         elif phase == "migrate":
             self._moving = {}
             keep = []
             for s in range(len(self.species)):
-                x4, u4, ids = self.engine.get_particles(s)
+                x4, u4, ids = e.get_particles(s)
                 zg = x4[2] + self.lo
                 below, above = zg < self.z0, zg >= self.z1
                 stay = ~(below | above)
@@ -151,25 +147,14 @@ class SlabRun:
 
     def incoming(self, phase, msgs):
         """Apply the neighbours' messages of `phase`."""
-        if phase in ("b_half", "b_half2", "e"):
-            d, b, _ = self.engine.get_fields()
-            F = d if phase == "e" else b
+        e = self.engine
+        if phase in ("b_half", "b_half2", "e", "j_sum", "j_halo"):
+            which = {"b_half": "b", "b_half2": "b", "e": "d"}.get(phase, "J")
             for q, v in msgs.items():
-                sl = self._sl(*self._ghost_of(q))
-                F[:, sl] = v.reshape(F[:, sl].shape)
-            self.engine.set_fields(d, b)
-        elif phase == "j_sum":
-            J = self.engine.get_fields()[2]
-            for q, v in msgs.items():
-                sl = self._sl(*self._edge_for(q))
-                J[:, sl] += v.reshape(J[:, sl].shape)
-            self.engine.set_j(J)
-        elif phase == "j_halo":
-            J = self.engine.get_fields()[2]
-            for q, v in msgs.items():
-                sl = self._sl(*self._ghost_of(q))
-                J[:, sl] = v.reshape(J[:, sl].shape)
-            self.engine.set_j(J)
+                # ghost sums land on the own planes next to the sender; the rest on the ghost planes
+                g0, g1 = self._edge_for(q) if phase == "j_sum" else self._ghost_of(q)
+                planes = v.reshape((3, g1 - g0) + self._plane_shape(v, g1 - g0))
+                e.set_planes(which, g0 - self.lo, planes, add=phase == "j_sum")
         elif phase == "migrate":
             got = [v.reshape((10, -1), order="F") for v in msgs.values()]
             for s, (qm, qmac) in enumerate(self.species):
@@ -182,9 +167,15 @@ class SlabRun:
                     parts_x.append(x)
                     parts_u.append(rec[5:9, sel])
                     parts_i.append(rec[9, sel].astype(np.uint32))
-                self.engine.load_particles(s, qm, qmac, np.hstack(parts_x), np.hstack(parts_u),
-                                           np.concatenate(parts_i))
+                e.load_particles(s, qm, qmac, np.hstack(parts_x), np.hstack(parts_u), np.concatenate(parts_i))
             self._keep = None
+
+    def _plane_shape(self, v, nplanes):
+        """(ny, nx) of a message of 3 x nplanes planes (the run's transverse shape)."""
+        if self.plane_shape is None:
+            raise RuntimeError("SlabRun needs plane_shape=(ny, nx)")
+        assert v.size == 3 * nplanes * self.plane_shape[0] * self.plane_shape[1]
+        return tuple(self.plane_shape)
 
 
 class LocalTransport:
@@ -250,6 +241,8 @@ class LibraryEngine:
         from . import grpic as G
 
         self.sim, self.G = sim, G
+        self.plane_shape = tuple(sim.shape[1:])
+        self._which = {"d": G.GRPIC_FIELD_D, "b": G.GRPIC_FIELD_B, "J": G.GRPIC_FIELD_J}
         self._stages = {"b_half": G.GRPIC_STAGE_B_HALF, "zero_j": G.GRPIC_STAGE_ZERO_J,
                         "push_deposit": G.GRPIC_STAGE_PUSH_DEPOSIT, "b_half2": G.GRPIC_STAGE_B_HALF2,
                         "e": G.GRPIC_STAGE_E, "sort": G.GRPIC_STAGE_SORT}
@@ -257,14 +250,14 @@ class LibraryEngine:
     def stage(self, name):
         self.sim.stage(self._stages[name])
 
+    def get_planes(self, which, z0, n):
+        return self.sim.get_planes(self._which[which], z0, n)
+
+    def set_planes(self, which, z0, planes, add=False):
+        self.sim.set_planes(self._which[which], z0, planes, add)
+
     def get_fields(self):
         return self.sim.get_fields()
-
-    def set_fields(self, d, b):
-        self.sim.set_fields(d, b)
-
-    def set_j(self, J):
-        self.sim.set_j(J)
 
     def get_particles(self, s):
         x4, u4, ids = self.sim.get_particles(s)

@@ -14,7 +14,8 @@ import pytest
 import oracle as O
 from parity_util import TOL, rel_l2, well_conditioned
 from paper_0904_0232_gb300 import synth
-from paper_0904_0232_gb300.grpic import GRPIC_U_FULL, Simulation
+from paper_0904_0232_gb300.grpic import (GRPIC_FIELD_B, GRPIC_FIELD_D, GRPIC_FIELD_J, GRPIC_U_FULL, GrpicError,
+                                         Simulation)
 from paper_0904_0232_gb300.slab import LibraryEngine, LocalTransport, SlabPlan, SlabRun, library_slab
 
 pytestmark = pytest.mark.gpu
@@ -126,3 +127,30 @@ def test_fp32_mixed_slabs_against_one_context():
         assert np.array_equal(i, i1[o])
         assert np.abs(x[:3] - x1[:3, o]).max() <= tol["particles"] * N
         assert np.abs(u - u1[:, o]).max() <= tol["particles"] * max(1.0, np.abs(u1).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_planes(prec):
+    """grpic_get_planes / grpic_set_planes: the planes of grpic_get_fields, written back exactly (FP32
+    values round-trip), J added into; ranges outside the grid and adding into d or b are refused."""
+    sim = Simulation(12, 10, 16, 2.0, 1.0, 1.0, 0.4, precision=prec)
+    rng = np.random.default_rng(3)
+    d0, b0, J0 = (rng.standard_normal((3, 16, 10, 12)) for _ in range(3))
+    sim.set_fields(d0, b0)
+    sim.set_j(J0)
+    d, b, J = sim.get_fields()
+    for which, F in ((GRPIC_FIELD_D, d), (GRPIC_FIELD_B, b), (GRPIC_FIELD_J, J)):
+        assert np.array_equal(sim.get_planes(which, 5, 4), F[:, 5:9])
+    new = rng.standard_normal((3, 3, 10, 12))
+    sim.set_planes(GRPIC_FIELD_B, 0, new)
+    sim.set_planes(GRPIC_FIELD_J, 13, new, add=True)
+    d1, b1, J1 = sim.get_fields()
+    assert np.array_equal(d1, d)
+    tol = 0.0 if prec == "fp64" else 1e-7
+    assert np.abs(b1[:, :3] - new).max() <= tol * np.abs(new).max() and np.array_equal(b1[:, 3:], b[:, 3:])
+    assert np.allclose(J1[:, 13:], J[:, 13:] + new, rtol=1e-15, atol=0) and np.array_equal(J1[:, :13], J[:, :13])
+    with pytest.raises(GrpicError):
+        sim.get_planes(GRPIC_FIELD_D, 14, 3)
+    with pytest.raises(GrpicError):
+        sim.set_planes(GRPIC_FIELD_D, 0, new, add=True)
+    sim.close()

@@ -29,6 +29,25 @@ class OracleEngine:
 
     def __init__(self, ref):
         self.ref = ref
+        self.plane_shape = ref.shape[1:]
+
+    def get_planes(self, which, z0, n):
+        d, b, J = self.ref.get_fields()
+        return {"d": d, "b": b, "J": J}[which][:, z0:z0 + n].copy()
+
+    def set_planes(self, which, z0, planes, add=False):
+        d, b, J = self.ref.get_fields()
+        n = planes.shape[1]
+        if which == "J":
+            if add:
+                J[:, z0:z0 + n] += planes
+            else:
+                J[:, z0:z0 + n] = planes
+            self.ref.set_j(J)
+        else:
+            assert not add
+            (d if which == "d" else b)[:, z0:z0 + n] = planes
+            self.ref.set_fields(d, b)
 
     def stage(self, name):
         {"b_half": self.ref.b_half, "zero_j": self.ref.zero_j, "push_deposit": self.ref.push_deposit,
