@@ -87,6 +87,7 @@ def lib():
                 "orc_r_plus": (ctypes.c_double, [_V]),
                 "orc_set_fields": (ctypes.c_int, [_V, _D, _D]),
                 "orc_set_absorb_target": (ctypes.c_int, [_V, _D, _D]),
+                "orc_get_contra_h": (ctypes.c_int, [_V, _D]),
                 "orc_absorb_kappa": (ctypes.c_double, [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_set_j": (ctypes.c_int, [_V, _D]),
                 "orc_get_fields": (ctypes.c_int, [_V, _D, _D, _D]),
@@ -308,6 +309,13 @@ class Oracle:
         J = np.zeros((3,) + self.shape)
         self._chk(lib().orc_get_fields(self._h, _dp(d), _dp(b), _dp(J)), "get_fields")
         return d, b, J
+
+    def get_contra_h(self):
+        """Contravariant (F^yz, F^zx, F^xy) at the b faces from the current (b, d), as the E step
+        converts them; zero on the outer index layer."""
+        h = np.zeros((3,) + self.shape)
+        self._chk(lib().orc_get_contra_h(self._h, _dp(h)), "get_contra_h")
+        return h
 
     def init_uniform_field(self, E=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0)):
         self._chk(lib().orc_init_uniform_field(self._h, _dp(_f64(E)), _dp(_f64(B))), "init_uniform_field")

@@ -1400,6 +1400,16 @@ int orc_set_j(void* p, const double* J3) {
   return ORC_OK;
 }
 
+// Contravariant F^{jk} (h: F^{yz}, F^{zx}, F^{xy}) at the b face lattice points, from the current (b, d)
+// as the E step converts them (A7); zero on the outer index layer.
+int orc_get_contra_h(void* p, double* h3) {
+  Ctx* ctx = static_cast<Ctx*>(p);
+  std::vector<double> h[3];
+  ctx->contra_h(h);
+  for (int q = 0; q < 3; ++q) std::memcpy(h3 + q * ctx->ncell, h[q].data(), ctx->ncell * sizeof(double));
+  return ORC_OK;
+}
+
 int orc_get_fields(void* p, double* d3, double* b3, double* J3) {
   Ctx* ctx = static_cast<Ctx*>(p);
   for (int q = 0; q < 3; ++q) {
