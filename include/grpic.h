@@ -202,6 +202,14 @@ grpic_status grpic_sync(grpic_ctx* ctx);
  * GRPIC_MEM_DEVICE for the destination.  FP32-mixed contexts widen their FP32 fields. */
 grpic_status grpic_get_fields(grpic_ctx* ctx, double* d3, double* b3, double* J3, int mem);
 
+/* The field in contravariant components (Eq. 8: F^{4j} = E^j, F^{jk} = eps^{jkl} B^l): d3 receives the
+ * prognostic contravariant F^{i4} at the edges (as grpic_get_fields), h3 the contravariant (F^{yz},
+ * F^{zx}, F^{xy}) at the b faces, converted from (b, d) as the E step converts them (the other
+ * components brought to the face as the mean of their nearest points, the metric at the face; Sec. 3,
+ * Eqs. 8 and 11); h3 is zero on the outer index layer.  Either pointer may be NULL; FP64, 3 planes each,
+ * caller-owned, host or device memory by mem. */
+grpic_status grpic_get_fields_contra(grpic_ctx* ctx, double* d3, double* h3, int mem);
+
 /* A range of z-planes of one field, for a driver that splits one run into z-slabs across contexts
  * and exchanges the planes next to a neighbour's (not in the paper).  which: GRPIC_FIELD_D (the
  * contravariant F^{i4} of Eq. 12's update), GRPIC_FIELD_B (the covariant F_{yz}, F_{zx}, F_{xy} of

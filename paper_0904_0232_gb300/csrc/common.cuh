@@ -180,6 +180,10 @@ template <typename T>
 void launch_convert_in(T* dst, const double* src, long long n, cudaStream_t st);
 template <typename T>
 void launch_convert_out(double* dst, const T* src, long long n, cudaStream_t st);
+// The contravariant face components (F^yz, F^zx, F^xy) of every cell as the E step converts them,
+// into h3 (3 planes of FP64, device)
+template <typename T>
+void launch_contra_h(const Grid& g, const Fields<T>& F, const uint16_t* loc, double* h3, cudaStream_t st);
 // dst[i] += src[i], FP64
 void launch_add_f64(double* dst, const double* src, long long n, cudaStream_t st);
 

@@ -786,6 +786,63 @@ __global__ void k_uniform_field(const Grid g, const Fields<T> F, double E0, doub
   }
 }
 
+// ---- read-out of the contravariant face components --------------------------------------------
+// Mean of the points of source lattice SL nearest to the point of target lattice TL in cell
+// (i, j, k), from global memory, in the order of avg_s.
+template <int TL, int SL, typename T>
+__device__ __forceinline__ T avg_g(const T* __restrict__ F, const Grid& g, int i, int j, int k) {
+  constexpr int lx = nb_lo(TL, SL, 0), hx = nb_hi(TL, SL, 0);
+  constexpr int ly = nb_lo(TL, SL, 1), hy = nb_hi(TL, SL, 1);
+  constexpr int lz = nb_lo(TL, SL, 2), hz = nb_hi(TL, SL, 2);
+  constexpr int cnt = (hx - lx + 1) * (hy - ly + 1) * (hz - lz + 1);
+  T s = T(0);
+#pragma unroll
+  for (int dz = lz; dz <= hz; ++dz)
+#pragma unroll
+    for (int dy = ly; dy <= hy; ++dy)
+#pragma unroll
+      for (int dx = lx; dx <= hx; ++dx) s += F[((long long)(k + dz) * g.ny + (j + dy)) * g.nx + (i + dx)];
+  if (cnt == 1) return s;
+  return s * (T(1) / T(cnt));
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ double face_h_g(const Grid& g, const FieldConsts<T>& K, const Fields<T>& F, int i, int j,
+                                           int k, bool excised) {
+  constexpr int L = 3 + Q;
+  T bb[3];
+  bb[0] = avg_g<L, 3>(F.b[0], g, i, j, k);
+  bb[1] = avg_g<L, 4>(F.b[1], g, i, j, k);
+  bb[2] = avg_g<L, 5>(F.b[2], g, i, j, k);
+  constexpr int A = (Q + 1) % 3, B = (Q + 2) % 3;  // (d x k)_Q = d_A k_B - d_B k_A
+  const T dA = avg_g<L, A>(F.d[A], g, i, j, k);
+  const T dB = avg_g<L, B>(F.d[B], g, i, j, k);
+  const Pt<T> P = metric_pt<T>(K, L, (T)i - K.xc, (T)j - K.yc, (T)k - K.zc, excised);
+  const T kA = A == 0 ? P.k0 : (A == 1 ? P.k1 : P.k2);
+  const T kB = B == 0 ? P.k0 : (B == 1 ? P.k1 : P.k2);
+  return (double)h_comp(Q, P, bb, dA * kB - dB * kA, rcp_t(T(1) + P.f));
+}
+
+// h (F^yz, F^zx, F^xy) at every b face of the cells 1 .. n-2 per axis, as the E step converts the
+// field; zero on the outer index layer.
+template <typename T>
+__global__ void k_contra_h(const Grid g, const FieldConsts<T> K, const Fields<T> F, const uint16_t* __restrict__ loc,
+                           double* __restrict__ h0, double* __restrict__ h1, double* __restrict__ h2) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int i = (int)(c % g.nx);
+  const int j = (int)((c / g.nx) % g.ny);
+  const int k = (int)(c / ((long long)g.nx * g.ny));
+  if (i < 1 || j < 1 || k < 1 || i > g.nx - 2 || j > g.ny - 2 || k > g.nz - 2) {
+    h0[c] = h1[c] = h2[c] = 0.0;
+    return;
+  }
+  const uint16_t w = loc[c];
+  h0[c] = face_h_g<0, T>(g, K, F, i, j, k, exc(w, 3));
+  h1[c] = face_h_g<1, T>(g, K, F, i, j, k, exc(w, 4));
+  h2[c] = face_h_g<2, T>(g, K, F, i, j, k, exc(w, 5));
+}
+
 template <typename T>
 __global__ void k_convert_in(T* __restrict__ dst, const double* __restrict__ src, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -800,6 +857,14 @@ __global__ void k_convert_out(double* __restrict__ dst, const T* __restrict__ sr
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+template <typename T>
+void launch_contra_h(const Grid& g, const Fields<T>& F, const uint16_t* loc, double* h3, cudaStream_t st) {
+  k_contra_h<T><<<blocks_for(g.ncell, 256), 256, 0, st>>>(g, field_consts<T>(g), F, loc, h3, h3 + g.ncell,
+                                                   h3 + 2 * g.ncell);
+}
+template void launch_contra_h<float>(const Grid&, const Fields<float>&, const uint16_t*, double*, cudaStream_t);
+template void launch_contra_h<double>(const Grid&, const Fields<double>&, const uint16_t*, double*, cudaStream_t);
 
 void launch_location_flags(const Grid& g, uint16_t* loc, cudaStream_t st) {
   k_location_flags<<<blocks_for(g.ncell, 256), 256, 0, st>>>(g, loc);

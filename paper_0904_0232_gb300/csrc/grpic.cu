@@ -841,6 +841,29 @@ grpic_status grpic_get_fields(grpic_ctx* c, double* d3, double* b3, double* J3, 
   return s;
 }
 
+grpic_status grpic_get_fields_contra(grpic_ctx* c, double* d3, double* h3, int mem) {
+  if (!c) return GRPIC_ERR_INVALID;
+  grpic_status s = GRPIC_OK;
+  if (d3) s = grpic_get_fields(c, d3, nullptr, nullptr, mem);
+  if (s != GRPIC_OK || !h3) return s;
+  const size_t bytes = sizeof(double) * 3 * c->g.ncell;
+  double* out = h3;
+  if (mem != GRPIC_MEM_DEVICE) {
+    out = static_cast<double*>(dev_alloc(c, bytes));
+    if (!out) return fail(c, GRPIC_ERR_OOM, "staging allocation failed");
+  }
+  if (c->mixed)
+    launch_contra_h<float>(c->g, fields_view<float>(c), c->loc, out, c->stream);
+  else
+    launch_contra_h<double>(c->g, fields_view<double>(c), c->loc, out, c->stream);
+  s = cuda_check(c, cudaGetLastError(), "contra_h");
+  if (s == GRPIC_OK && out != h3)
+    s = cuda_check(c, cudaMemcpyAsync(h3, out, bytes, cudaMemcpyDeviceToHost, c->stream), "contra_h copy");
+  if (s == GRPIC_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "contra_h sync");
+  if (out != h3) dev_free(c, out);
+  return s;
+}
+
 // Planes z0 .. z0 + n - 1 of component q of field `which` (the current buffer), as a pointer of T
 // (d, b) or double (J); count = n planes of nx * ny.
 static bool plane_range_ok(const grpic_ctx* c, int which, int z0, int n) {

@@ -80,6 +80,7 @@ EXPORTS = {
     "grpic_set_uniform_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double)]),
     "grpic_set_j": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grpic_get_fields_contra": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "grpic_get_planes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_int]),
     "grpic_set_planes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -307,6 +308,16 @@ def grpic_get_fields(ctx, shape):
 
 
 GRPIC_FIELD_D, GRPIC_FIELD_B, GRPIC_FIELD_J = 0, 1, 2
+
+
+def grpic_get_fields_contra(ctx, shape):
+    """(d, h): contravariant F^{i4} at the edges and (F^yz, F^zx, F^xy) at the faces, (3,) + shape each."""
+    d = np.zeros((3,) + tuple(shape))
+    h = np.zeros((3,) + tuple(shape))
+    _check(ctx, load_library().grpic_get_fields_contra(ctx, d.ctypes.data_as(ctypes.c_void_p),
+                                                       h.ctypes.data_as(ctypes.c_void_p), GRPIC_MEM_HOST),
+           "grpic_get_fields_contra")
+    return d, h
 
 
 def grpic_get_planes(ctx, which, z0, nplanes, shape):
@@ -593,6 +604,9 @@ class Simulation:
 
     def get_particles(self, species, device=False):
         return grpic_get_particles(self.handle, species, device=device)
+
+    def get_fields_contra(self):
+        return grpic_get_fields_contra(self.handle, self.shape)
 
     def get_planes(self, which, z0, nplanes):
         return grpic_get_planes(self.handle, which, z0, nplanes, self.shape)

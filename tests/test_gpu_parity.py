@@ -318,3 +318,24 @@ def test_schwarzschild_pairs_full_run():
         d, b, J = sim.get_fields()
         dr, br, Jr = ref.get_fields()
         assert rel_l2(J, Jr) <= tol and rel_l2(b, br) <= tol and rel_l2(d, dr) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_fields_contra_readout(prec):
+    """grpic_get_fields_contra against the oracle's read-out on random fields around a = 0.9m (every
+    face of cells 1 .. n-2; zero on the outer layer), and d as grpic_get_fields returns it."""
+    N, m = 24, 2.0
+    rng = np.random.default_rng(11)
+    d = 0.05 * rng.standard_normal((3, N, N, N))
+    b = 0.1 + 0.05 * rng.standard_normal((3, N, N, N))
+    ref = O.Oracle(N, N, N, m, 0.9 * m, 1.0, 0.4, threads=0)
+    ref.set_fields(d, b)
+    sim = Simulation(N, N, N, m, 0.9 * m, 1.0, 0.4, precision=prec)
+    sim.set_fields(d, b)
+    dd, h = sim.get_fields_contra()
+    hr = ref.get_contra_h()
+    assert np.array_equal(dd, sim.get_fields()[0])
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert np.abs(h - hr).max() <= tol * np.abs(hr).max(), np.abs(h - hr).max()
+    assert np.abs(h[:, 0]).max() == 0.0 and np.abs(h[:, :, -1]).max() == 0.0
+    sim.close()
