@@ -48,7 +48,7 @@ FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 # DRAM bytes per particle-step of the push kernel (dram__bytes_read + dram__bytes_write of one
 # launch over its particles), from an ncu capture at the bench size, valid for the push sources
 # whose hash is recorded with it.
-PUSH_TRAFFIC = {"sha": "c023865740c10db6", "bytes_per_particle": 1380.25e6 / 15.61e6}
+PUSH_TRAFFIC = {"sha": "89f6fa0125cae024", "bytes_per_particle": 1379.84e6 / 15.61e6}
 
 
 def kernel_sha():
