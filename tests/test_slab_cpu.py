@@ -2,8 +2,8 @@
 slab's engine: the split run against the same run on one grid.
 
 * the plan: owned ranges, local planes and the minimum slab size;
-* three slabs in one process (LocalTransport) and two gloo ranks (DistTransport, point-to-point
-  messages only), each over five whole steps of a pair plasma around a = 0.9m whose hole lies next
+* three slabs in one process (LocalTransport) and two or three gloo ranks (DistTransport,
+  point-to-point messages only), each over five whole steps of a pair plasma around a = 0.9m whose hole lies next
   to the slab boundaries: every particle (matched by id) and every field value of the owned planes
   agree with the single grid to FP64 rounding.  The one difference in arithmetic is the order in
   which J at a node next to a boundary adds up (the neighbour's share is added as one sum), so the
@@ -185,16 +185,19 @@ def _rank_main(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks():
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks(world):
+    """One slab per process, point-to-point messages over gloo (three ranks: the middle one exchanges
+    with both neighbours)."""
     torch = pytest.importorskip("torch")
     mp = torch.multiprocessing.get_context("spawn")
     q = mp.Queue()
     port = _free_port()
-    procs = [mp.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    procs = [mp.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = dict(q.get(timeout=300) for _ in range(2))
+    res = dict(q.get(timeout=300) for _ in range(world))
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    _compare(_workload(), [res[0], res[1]], SlabPlan(N, 2))
+    _compare(_workload(), [res[r] for r in range(world)], SlabPlan(N, world))
