@@ -304,6 +304,15 @@ grpic_status grpic_gauss_residual(grpic_ctx* ctx, double* res, int mem, double* 
  *                       groups of G consecutive chunks, spreading the near-hole (FP64-heavy) chunks over
  *                       the launch while each group keeps neighbouring cells together (larger G: more
  *                       L2 locality, less even FP64 load); 0 keeps them in order
+ *   area_table:         split = 0, Q = 2, j_tile = 0, FP32_MIXED only: 1 takes the face AREAs of Eq. 18
+ *                       for far-field warps from per-cell polynomial fits of the integrand instead of
+ *                       the Q x Q Gauss nodes, and raises the far-field radius to
+ *                       max(r_fp64 + |a| + 4, 4 + (m / 4.5e-7)^(1/6)) cells, where the fits' weights
+ *                       agree with the Q = 2 quadrature to a few 1e-9.  The fits (total degree 4 in the
+ *                       cell fractions, 36 FP32 coefficients per cell and face orientation: 432 bytes
+ *                       per cell) are allocated and computed on the context's stream by the first
+ *                       grpic_set_tuning that sets it (GRPIC_ERR_OOM if they do not fit) and kept
+ *                       until grpic_destroy
  * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */
 typedef struct {
   int far_min_blocks;
@@ -313,6 +322,7 @@ typedef struct {
   int split;
   int j_tile;
   int spread;
+  int area_table;
 } grpic_tuning;
 grpic_status grpic_set_tuning(grpic_ctx* ctx, const grpic_tuning* t);
 grpic_status grpic_get_tuning(const grpic_ctx* ctx, grpic_tuning* t);

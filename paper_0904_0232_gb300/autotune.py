@@ -2,8 +2,8 @@
 whether the FP32-mixed push runs as one kernel with a per-warp choice of code or split into
 near-hole and far-field kernels, the register budget of the far-field code (resident blocks
 per SM), the persistent blocks per SM of the near-hole kernel, whether that kernel overlaps the
-far one on a second stream, whether the per-warp kernel accumulates J in shared-memory tiles, and
-the sort interval.
+far one on a second stream, whether the per-warp kernel accumulates J in shared-memory tiles,
+whether its far-field warps take the face areas from per-cell fits, and the sort interval.
 
 Coordinate descent: starting from the current choice, each knob in turn is set to each of its
 values while the others stay fixed, and the fastest is kept; two rounds.  A trial times
@@ -11,7 +11,9 @@ values while the others stay fixed, and the fastest is kept; two rounds.  A tria
 first step after a change of sort interval or kernel variant pays for the change).  Trials
 advance the simulation like warm-up steps do, and the step time drifts as the state evolves (the
 FP64 load grows as plasma falls in), so each value of a knob is timed twice, the values in
-forward and then in reverse order, and the means are compared: a steady drift cancels.  Winners are cached in a JSON file keyed by the
+forward and then in reverse order, and the means are compared: a steady drift cancels.  A
+combination the context refuses (GrpicError: the area fits with a J tile, say) is timed with one
+other knob back at its first choice instead, or skipped.  Winners are cached in a JSON file keyed by the
 device name and a workload signature, so later runs can reuse them without tuning.
 
 The batched engine has one knob, the persistent blocks per SM of its launches; tune_batch
@@ -22,10 +24,13 @@ from __future__ import annotations
 import json
 import os
 
+from .grpic import GrpicError
+
 CHOICES = {
     "split": (0, 1),
     "spread": (0, 1, 16),
     "j_tile": (0, 1),
+    "area_table": (0, 1),
     "far_min_blocks": (4, 5, 6),
     "near_blocks_per_sm": (1, 2, 4),
     "overlap": (0, 1),
@@ -82,6 +87,26 @@ def _time_steps(sim, steps):
     return e0.elapsed_time(e1) / steps
 
 
+def _apply(sim, cand, knob, choices):
+    """Apply cand; if the context refuses it, the same with one other knob back at its first
+    choice (the first such combination it accepts).  Returns the applied tuning or None."""
+    try:
+        sim.set_tuning(**cand)
+        return cand
+    except GrpicError:
+        pass
+    for other, vals in choices.items():
+        if other == knob or cand[other] == vals[0]:
+            continue
+        alt = dict(cand, **{other: vals[0]})
+        try:
+            sim.set_tuning(**alt)
+            return alt
+        except GrpicError:
+            continue
+    return None
+
+
 def tune(sim, signature: str, steps: int = 4, rounds: int = 2, cache: str = DEFAULT_CACHE, choices=CHOICES,
          use_cache: bool = True, timer=_time_steps, device: str | None = None):
     """Tune `sim` (a grpic.Simulation) in place; returns {"tuning": {...}, "ms_per_step": t,
@@ -99,17 +124,19 @@ def tune(sim, signature: str, steps: int = 4, rounds: int = 2, cache: str = DEFA
     for _ in range(rounds):
         changed = False
         for knob, values in choices.items():
-            times = {}
+            times, combos = {}, {}
             for v in list(values) + list(values)[::-1]:
-                cand = dict(cur, **{knob: v})
-                sim.set_tuning(**cand)
+                cand = _apply(sim, dict(cur, **{knob: v}), knob, choices)
+                if cand is None:
+                    continue
+                combos[v] = cand
                 times.setdefault(v, []).append(timer(sim, steps))
                 trials += 1
             results = {v: sum(t) / len(t) for v, t in times.items()}
             v_best = min(results, key=results.get)
-            if v_best != cur[knob]:
+            if combos[v_best] != cur:
                 changed = True
-            cur = dict(cur, **{knob: v_best})
+            cur = combos[v_best]
             best_ms = results[v_best]
         if not changed:
             break

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrpic.so")
 SOURCES = ["grpic.cu", "fields.cu", "push.cu", "push_far.cu", "sort.cu", "peak.cu", "static_sort.cu", "server.cu",
-           "diag.cu"]
+           "diag.cu", "area_table.cu"]
 HEADERS = ["common.cuh", "metric.cuh", "push_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The FP32 paths of the push and the field updates tolerate the hardware's approximate

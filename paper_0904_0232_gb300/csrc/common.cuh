@@ -252,6 +252,15 @@ __host__ __device__ inline double near_radius(const Grid& g) {
   return (g.r_fp64 > 0.0 ? g.r_fp64 : 0.0) + (g.a < 0.0 ? -g.a : g.a) + 4.0;
 }
 
+// Far-field deposit from per-cell polynomial fits of the Eq. 18 integrand (area_table.cu):
+// kAreaTableStride float4 per cell (36 coefficients for each face orientation K), indexed by the
+// cell's linear index.  table_radius: a warp takes the table only if every particle has
+// R(x_n) >= table_radius (>= near_radius; where the fit's truncation error, ~m / r^6, leaves the
+// weights within a few 1e-9 of Q = 2 Gauss quadrature).
+constexpr int kAreaTableStride = 27;
+double table_radius(const Grid& g);
+void launch_area_table(const Grid& g, float4* tab, cudaStream_t st);
+
 // Split FP32-mixed push.  near_radius: particles with R(x_n) below it are classified near
 // (marked kNear, listed; count[0] = list length, count[1] = work cursor) and pushed by
 // launch_push_near (nblocks persistent blocks; new sort keys to keys[slot]); the rest by launch_push_far (FP32 only; minb selects
@@ -291,9 +300,10 @@ inline int spread_log2(int group) {
   return lg;
 }
 // Unsplit alternative: one launch, far-field or FP32-mixed code chosen per warp by the same
-// near_radius criterion.
+// near_radius criterion.  atab (non-null, Q = 2, no tile): far-field warps deposit with the
+// per-cell area fits, and the criterion becomes table_radius.
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, int spread, cudaStream_t stream);
+                        DevStatus* st, int minb, bool tile, int spread, const float4* atab, cudaStream_t stream);
 
 template <typename T>
 void launch_load_particles(const Grid& g, const Particles<T>& P, long long n, const double* x4, const double* u4,

@@ -48,11 +48,12 @@ struct grpic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int sms = 0;
-  grpic_tuning tune{4, 4, 1, 1, 0, 0, 1};
+  grpic_tuning tune{4, 4, 1, 1, 0, 0, 1, 0};
   void* fields = nullptr;  // 12 planes of T: d buffers 0 and 1 (3 planes each), b buffers 0 and 1
   void* tgt = nullptr;     // absorbing layers: 6 planes of T, the target d and b (null without layers)
   void* kin = nullptr;     // inner absorbing layer: relaxation table over g.kbox0 / g.kboxn (T)
   double* J = nullptr;     // 3 planes
+  float4* atab = nullptr;  // per-cell area fits of the far-field deposit (built when tune.area_table is set)
   uint16_t* loc = nullptr;  // per-cell location flags
   // field ping-pong state: buffer of the current d and b; bprev: buffer holding b^{n-1/2} after the
   // first B half-step (time-centred second half-step)
@@ -192,6 +193,9 @@ void enqueue_rho(grpic_ctx* c, bool with_gamma, double* rho) {
   }
 }
 
+// The area fits the per-warp select push uses, or null.
+const float4* area_table_of(const grpic_ctx* c) { return c->tune.area_table ? c->atab : nullptr; }
+
 // Unsplit FP32-mixed push: one launch per species, far-field or mixed code chosen per warp.
 void enqueue_select_push(grpic_ctx* c) {
   Fields<float> F = fields_view<float>(c);
@@ -200,7 +204,7 @@ void enqueue_select_push(grpic_ctx* c) {
     if (!S.loaded || S.n == 0) continue;
     refresh_count(S);
     launch_push_select(c->g, F, particles_view<float>(c, s, S.cur), Species{S.qm, S.qmacro}, c->st,
-                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->tune.spread, c->stream);
+                       c->tune.far_min_blocks, c->tune.j_tile != 0, c->tune.spread, area_table_of(c), c->stream);
     c->launches += 1;
   }
 }
@@ -622,6 +626,7 @@ grpic_status grpic_destroy(grpic_ctx* c) {
   dev_free(c, c->fields);
   dev_free(c, c->tgt);
   dev_free(c, c->kin);
+  dev_free(c, c->atab);
   dev_free(c, c->J);
   dev_free(c, c->loc);
   dev_free(c, c->st);
@@ -1154,8 +1159,19 @@ grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
   if (t->far_min_blocks < 4 || t->far_min_blocks > 6 || t->near_blocks_per_sm < 1 ||
       t->near_blocks_per_sm > 32 || t->sort_interval < 1 || (t->overlap != 0 && t->overlap != 1) ||
       (t->split != 0 && t->split != 1) || (t->j_tile != 0 && t->j_tile != 1) ||
-      t->spread < 0 || t->spread > 64 || (t->spread & (t->spread - 1)) != 0)
+      t->spread < 0 || t->spread > 64 || (t->spread & (t->spread - 1)) != 0 ||
+      (t->area_table != 0 && t->area_table != 1))
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
+  if (t->area_table && (!c->mixed || t->j_tile))
+    return fail(c, GRPIC_ERR_INVALID, "area_table needs an FP32_MIXED context and j_tile = 0");
+  if (t->area_table && !c->atab) {
+    c->atab = static_cast<float4*>(dev_alloc(c, sizeof(float4) * kAreaTableStride * (size_t)c->g.ncell));
+    if (!c->atab) return fail(c, GRPIC_ERR_OOM, "area table allocation");
+    launch_area_table(c->g, c->atab, c->stream);
+    c->launches += 1;
+    const grpic_status s = cuda_check(c, cudaGetLastError(), "area table");
+    if (s != GRPIC_OK) return s;
+  }
   c->tune = *t;
   c->cfg.sort_interval = t->sort_interval;
   return GRPIC_OK;
@@ -1416,7 +1432,7 @@ void batch_enqueue_push_items(grpic_batch* b, int k) {
     SpeciesStore& S = c->sp[it.s];
     const Particles<float> P = particles_view<float>(c, it.s, b->cur0[4 * it.inst + it.s] ^ k);
     launch_push_select(c->g, F, P, Species{S.qm, S.qmacro}, c->st, c->tune.far_min_blocks, false, c->tune.spread,
-                       b->side[br]);
+                       area_table_of(c), b->side[br]);
   }
   for (int br = 0; br < grpic_batch::kPushBranches; ++br) {
     cudaEventRecord(b->ev_join[br], b->side[br]);

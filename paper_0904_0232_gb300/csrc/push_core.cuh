@@ -484,6 +484,69 @@ __device__ __forceinline__ float node_value(const Consts<float>& C, const FaceLa
   return v * rsqrtf(v);
 }
 
+// Means of t^i (i = 0..4) over [0, x] (lane x: x^i / (i+1)) and over [x, 1] (lane y:
+// (1 + x + ... + x^i) / (i+1)): the integral of a monomial over a sub-interval is its width times
+// this mean, so the areas below keep the relative precision of the widths x and 1 - x.
+__device__ __forceinline__ void interval_means(float x, float2 M[5]) {
+  float p = x, cum = 1.f + x;
+  M[0] = f2(1.f);
+  M[1] = mul2(make_float2(p, cum), f2(0.5f));
+#pragma unroll
+  for (int i = 2; i < 5; ++i) {
+    p *= x;
+    cum += p;
+    M[i] = mul2(make_float2(p, cum), f2(1.f / (float)(i + 1)));
+  }
+}
+
+// The four sub-rectangle AREAs of Eq. 18 in the face plane at fraction w along K of a cell, split
+// at fractions (u, v) along (I, J), from the cell's polynomial fit t (36 coefficients, area_table.cu:
+// for j = 0..4, i = 0..4-j, the coefficients of w^0..w^(4-i-j) of u^i v^j).  With c_ij the fit's
+// u^i v^j coefficient at w, the area over U x V is |U| |V| sum_ij c_ij mean_U(u^i) mean_V(v^j).
+// A00 = [u,1] x [v,1], A10 = [0,u] x [v,1], A01 = [u,1] x [0,v], A11 = [0,u] x [0,v].
+__device__ __forceinline__ void table_areas(const float4* __restrict__ t, float u, float v, float w, float& A00,
+                                            float& A10, float& A01, float& A11) {
+  float c[36];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const float4 e = __ldg(t + q);
+    c[4 * q] = e.x;
+    c[4 * q + 1] = e.y;
+    c[4 * q + 2] = e.z;
+    c[4 * q + 3] = e.w;
+  }
+  float2 Mu[5], Mv[5];
+  interval_means(u, Mu);
+  interval_means(v, Mv);
+  // R_j = sum_i c_ij(w) mean(u^i) over [0,u] (lane x) and [u,1] (lane y); c_ij(w) by Horner in w
+  float2 R[5];
+  int n = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+#pragma unroll
+    for (int i = 0; i + j < 5; ++i) {
+      const int kmax = 4 - i - j;
+      float cij = c[n + kmax];
+#pragma unroll
+      for (int k = kmax - 1; k >= 0; --k) cij = fmaf(cij, w, c[n + k]);
+      n += kmax + 1;
+      R[j] = i == 0 ? f2(cij) : fma2(f2(cij), Mu[i], R[j]);
+    }
+  }
+  // sums over j against mean(v^j) over [0,v] (S0) and [v,1] (S1)
+  float2 S0 = R[0], S1 = R[0];
+#pragma unroll
+  for (int j = 1; j < 5; ++j) {
+    S0 = fma2(R[j], f2(Mv[j].x), S0);
+    S1 = fma2(R[j], f2(Mv[j].y), S1);
+  }
+  const float wu = 1.f - u, wv = 1.f - v;
+  A11 = S0.x * (u * v);
+  A01 = S0.y * (wu * v);
+  A10 = S1.x * (u * wv);
+  A00 = S1.y * (wu * wv);
+}
+
 // FP32 deposit (the zig-zag split, fluxes and Eq. 18 weights of deposit() below) evaluated on a
 // per-face node lattice: the Q x Q Gauss nodes of the four sub-rectangles of a face make a
 // 2Q x 2Q lattice in (x^I, x^J), so node coordinates, their squares and the spin terms are
@@ -500,10 +563,11 @@ __device__ __forceinline__ float node_value(const Consts<float>& C, const FaceLa
 // left out of the sums and marked; after the lattice each marked node is evaluated again -- the
 // cancellation-free form of the root, then the FP64 policy (node_newton64 on FP64 p and q) where
 // it applies; r = 0 gives the flat limit -- and added.  The main loop has no call in it.
-template <int Q>
+template <int Q, bool TAB = false>
 __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<float>& F, const Consts<float>& C,
                                                 const float x0[3], const float dx[3], float qg, float inv_dt,
-                                                unsigned& flags, unsigned& n64, bool mixed, const JTile& jt) {
+                                                unsigned& flags, unsigned& n64, bool mixed, const JTile& jt,
+                                                const float4* __restrict__ atab = nullptr) {
   static_assert(4 * Q * Q <= 64, "node mask");
   const int nn[3] = {g.nx, g.ny, g.nz};
   int c1[3], c2[3];
@@ -540,178 +604,183 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float dK = sel3(K, dseg[0], dseg[1], dseg[2]);
       if (dK == 0.f) continue;
       const float flux = qg * dK * inv_dt;
-      FaceLattice L;
-      L.K = K;
       const float frI = sel3(K, fr[1], fr[2], fr[0]), frJ = sel3(K, fr[2], fr[0], fr[1]);
-      L.i0 = (float)sel3(K, cy, cz, cx);
-      L.j0 = (float)sel3(K, cz, cx, cy);
-      L.PK = (float)sel3(K, cx, cy, cz) + sel3(K, fr[0], fr[1], fr[2]);
-      L.XK = L.PK - sel3(K, cen[0], cen[1], cen[2]);
-      L.PI = L.i0 + frI;
-      L.PJ = L.j0 + frJ;
-      L.cI = sel3(K, cen[1], cen[2], cen[0]);
-      L.cJ = sel3(K, cen[2], cen[0], cen[1]);
-      // sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J)
-      L.wI0 = frI;
-      L.wI1 = 1.f - frI;
-      const float wJ[2] = {frJ, 1.f - frJ};
-      // Per node the quartic needs p = R^2 - a^2 and q = a^2 z^2, k_K's numerator the spin term
-      // -a x^I (K = 0) or +a x^J (K = 1); z is x^K, x^I or x^J (K = 2, 1, 0).  Each of these is a
-      // sum of a face constant, a row term and a column term.
-      L.pK = L.XK * L.XK - C.a2;
-      L.qK = K == 2 ? C.a2 * L.XK * L.XK : 0.f;
-      L.qI = K == 1 ? C.a2 : 0.f;
-      L.tI = K == 0 ? -C.a : 0.f;
-      L.qJ = K == 0 ? C.a2 : 0.f;
-      L.tJ = K == 1 ? C.a : 0.f;
-      float2 pJ2[Q], qJ2[Q], tJ2[Q];
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        const float2 XJ = add2(make_float2(col_coord<Q>(L, 2 * k), col_coord<Q>(L, 2 * k + 1)), f2(-L.cJ));
-        const float2 sq = mul2(XJ, XJ);
-        pJ2[k] = mul2(f2(0.5f), sq);
-        qJ2[k] = mul2(f2(L.qJ), sq);
-        tJ2[k] = mul2(f2(L.tJ), XJ);
-      }
-      const float nzz = -(L.XK * L.XK);
-      // acc[si][k]: lane-wise sums over the rows of sub-interval si, node pair k of a row
-      float2 acc[2][Q];
-#pragma unroll
-      for (int si = 0; si < 2; ++si)
-#pragma unroll
-        for (int k = 0; k < Q; ++k) acc[si][k] = f2(0.f);
-      unsigned long long slow = 0ull;  // marked nodes, bit (si * Q + pi) * 2Q + jb
-#pragma unroll 1
-      for (int pi = 0; pi < Q; ++pi) {
-        float gw = (float)Gauss<Q>::w(0);
-#pragma unroll
-        for (int t = 1; t < Q; ++t)
-          if (pi == t) gw = (float)Gauss<Q>::w(t);
-#pragma unroll
-        for (int si = 0; si < 2; ++si) {
-          float pRow, qRow, tRow;
-          row_terms(C, L, row_coord<Q>(L, si, pi), pRow, qRow, tRow);
-          const float2 pR = f2(0.5f * pRow), qR = f2(qRow), tR = f2(tRow);
-#pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            // with h = p / 2 (the halves of the row and column terms, exact):
-            // r^2 = h + sqrt(h^2 + q), the root's p > 0 form
-            const float2 p = add2(pR, pJ2[k]);
-            const float2 q = add2(qR, qJ2[k]);
-            const float2 D2 = fma2(p, p, q);
-            const float2 rD2 = rsqrt2(D2);  // 2 / D
-            const float2 r2 = fma2(D2, rD2, p);
-            const float2 ir = rsqrt2(r2);
-            // at the root r^4 + a^2 z^2 = r^2 D, so f = 2 m r^3 / Sigma = 2 m r / D = m r rsqrt(D2)
-            float2 v;
-            if (K == 2) {
-              // f (1 - z^2 / r^2) = m rsqrt(D2) (r^2 - z^2) / r
-              v = fma2(mul2(mul2(f2(C.m), rD2), add2(r2, f2(nzz))), ir, f2(1.f));
-            } else {
-              // f (1 - k_K^2) with k_K = num / rho^2
-              const float2 r = mul2(r2, ir);
-              const float2 num = fma2(r, f2(L.XK), add2(tR, tJ2[k]));
-              const float2 kK = mul2(num, rcp2(add2(r2, f2(C.a2))));
-              const float2 omk2 = fma2(kK, make_float2(-kK.x, -kK.y), f2(1.f));
-              v = fma2(mul2(mul2(f2(C.m), r), rD2), omk2, f2(1.f));
-            }
-            float2 rv = rsqrt2(v);
-            if (mixed) {
-              const int bit = (si * Q + pi) * 2 * Q + 2 * k;
-              if (!(p.x > 0.f) || !(r2.x >= C.r2_fp64)) {
-                v.x = rv.x = 0.f;
-                slow |= 1ull << bit;
-              }
-              if (!(p.y > 0.f) || !(r2.y >= C.r2_fp64)) {
-                v.y = rv.y = 0.f;
-                slow |= 1ull << (bit + 1);
-              }
-            }
-            if (Q == 2) {
-              acc[si][k] = fma2(v, rv, acc[si][k]);  // unit Gauss weights
-            } else {
-              const float2 w = make_float2(gw * (float)Gauss<Q>::w((2 * k) % Q),
-                                           gw * (float)Gauss<Q>::w((2 * k + 1) % Q));
-              acc[si][k] = fma2(w, mul2(v, rv), acc[si][k]);
-            }
-          }
-        }
-      }
-      // S[si][sj]: the weighted integrand sums of the four sub-rectangles
-      float S[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-      for (int si = 0; si < 2; ++si)
-#pragma unroll
+      float A00, A10, A01, A11;  // sub-rectangle areas; a node's weight is the area opposite it
+      if constexpr (TAB) {
+        table_areas(atab + base * kAreaTableStride + 9 * K, frI, frJ, sel3(K, fr[0], fr[1], fr[2]), A00, A10,
+                    A01, A11);
+      } else {
+        FaceLattice L;
+        L.K = K;
+        L.i0 = (float)sel3(K, cy, cz, cx);
+        L.j0 = (float)sel3(K, cz, cx, cy);
+        L.PK = (float)sel3(K, cx, cy, cz) + sel3(K, fr[0], fr[1], fr[2]);
+        L.XK = L.PK - sel3(K, cen[0], cen[1], cen[2]);
+        L.PI = L.i0 + frI;
+        L.PJ = L.j0 + frJ;
+        L.cI = sel3(K, cen[1], cen[2], cen[0]);
+        L.cJ = sel3(K, cen[2], cen[0], cen[1]);
+        // sub-interval 0 = [i0, PI], 1 = [PI, i0 + 1] (likewise in J)
+        L.wI0 = frI;
+        L.wI1 = 1.f - frI;
+        const float wJ[2] = {frJ, 1.f - frJ};
+        // Per node the quartic needs p = R^2 - a^2 and q = a^2 z^2, k_K's numerator the spin term
+        // -a x^I (K = 0) or +a x^J (K = 1); z is x^K, x^I or x^J (K = 2, 1, 0).  Each of these is a
+        // sum of a face constant, a row term and a column term.
+        L.pK = L.XK * L.XK - C.a2;
+        L.qK = K == 2 ? C.a2 * L.XK * L.XK : 0.f;
+        L.qI = K == 1 ? C.a2 : 0.f;
+        L.tI = K == 0 ? -C.a : 0.f;
+        L.qJ = K == 0 ? C.a2 : 0.f;
+        L.tJ = K == 1 ? C.a : 0.f;
+        float2 pJ2[Q], qJ2[Q], tJ2[Q];
+  #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          S[si][(2 * k) >= Q ? 1 : 0] += acc[si][k].x;
-          S[si][(2 * k + 1) >= Q ? 1 : 0] += acc[si][k].y;
+          const float2 XJ = add2(make_float2(col_coord<Q>(L, 2 * k), col_coord<Q>(L, 2 * k + 1)), f2(-L.cJ));
+          const float2 sq = mul2(XJ, XJ);
+          pJ2[k] = mul2(f2(0.5f), sq);
+          qJ2[k] = mul2(f2(L.qJ), sq);
+          tJ2[k] = mul2(f2(L.tJ), XJ);
         }
-      // The marked nodes of FP32-mixed warps.  p and q in FP64 are sums of FP64 face, row and
-      // column terms, like their FP32 counterparts: face, row and column terms are formed once.
-      if (slow) {
-        const double cK = sel3(K, C.dxc, C.dyc, C.dzc), cI = sel3(K, C.dyc, C.dzc, C.dxc);
-        const double cJ = sel3(K, C.dzc, C.dxc, C.dyc);
-        const double XK64 = widen(L.PK) - cK;
-        const double pK64 = fma(XK64, XK64, -C.da2);
-        const double qK64 = K == 2 ? C.da2 * XK64 * XK64 : 0.0;
-        double sqJ[2 * Q];  // squared FP64 offsets of the columns
-#pragma unroll
-        for (int jb = 0; jb < 2 * Q; ++jb) {
-          const double XJ64 = widen(col_coord<Q>(L, jb)) - cJ;
-          sqJ[jb] = XJ64 * XJ64;
-        }
-        int row = -1;
-        double pRow64 = 0.0, qRow64 = 0.0;
-        do {
-          const int b = __ffsll((long long)slow) - 1;
-          slow &= slow - 1ull;
-          const int ia = b / (2 * Q), jb = b - ia * 2 * Q;
-          const int si = ia / Q, pi = ia - si * Q;
-          const float AIa = row_coord<Q>(L, si, pi), AJ = col_coord<Q>(L, jb);
-          float pRow, qRow, tRow, pJ, qJ, tJ;
-          row_terms(C, L, AIa, pRow, qRow, tRow);
-          col_terms(C, L, AJ, pJ, qJ, tJ);
-          const float p = pRow + pJ, q = qRow + qJ;
-          // FP32 root by the cancellation-free form; FP64 where the policy asks for it (a node
-          // with p > 0 was marked only for that)
-          const float D = sqrtf(fmaf(p, p, 4.f * q));
-          float r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
-          if (p > 0.f || !(r2 >= C.r2_fp64)) {
-            if (ia != row) {
-              row = ia;
-              const double XI64 = widen(AIa) - cI;
-              pRow64 = fma(XI64, XI64, pK64);
-              qRow64 = K == 1 ? C.da2 * XI64 * XI64 : qK64;
+        const float nzz = -(L.XK * L.XK);
+        // acc[si][k]: lane-wise sums over the rows of sub-interval si, node pair k of a row
+        float2 acc[2][Q];
+  #pragma unroll
+        for (int si = 0; si < 2; ++si)
+  #pragma unroll
+          for (int k = 0; k < Q; ++k) acc[si][k] = f2(0.f);
+        unsigned long long slow = 0ull;  // marked nodes, bit (si * Q + pi) * 2Q + jb
+  #pragma unroll 1
+        for (int pi = 0; pi < Q; ++pi) {
+          float gw = (float)Gauss<Q>::w(0);
+  #pragma unroll
+          for (int t = 1; t < Q; ++t)
+            if (pi == t) gw = (float)Gauss<Q>::w(t);
+  #pragma unroll
+          for (int si = 0; si < 2; ++si) {
+            float pRow, qRow, tRow;
+            row_terms(C, L, row_coord<Q>(L, si, pi), pRow, qRow, tRow);
+            const float2 pR = f2(0.5f * pRow), qR = f2(qRow), tR = f2(tRow);
+  #pragma unroll
+            for (int k = 0; k < Q; ++k) {
+              // with h = p / 2 (the halves of the row and column terms, exact):
+              // r^2 = h + sqrt(h^2 + q), the root's p > 0 form
+              const float2 p = add2(pR, pJ2[k]);
+              const float2 q = add2(qR, qJ2[k]);
+              const float2 D2 = fma2(p, p, q);
+              const float2 rD2 = rsqrt2(D2);  // 2 / D
+              const float2 r2 = fma2(D2, rD2, p);
+              const float2 ir = rsqrt2(r2);
+              // at the root r^4 + a^2 z^2 = r^2 D, so f = 2 m r^3 / Sigma = 2 m r / D = m r rsqrt(D2)
+              float2 v;
+              if (K == 2) {
+                // f (1 - z^2 / r^2) = m rsqrt(D2) (r^2 - z^2) / r
+                v = fma2(mul2(mul2(f2(C.m), rD2), add2(r2, f2(nzz))), ir, f2(1.f));
+              } else {
+                // f (1 - k_K^2) with k_K = num / rho^2
+                const float2 r = mul2(r2, ir);
+                const float2 num = fma2(r, f2(L.XK), add2(tR, tJ2[k]));
+                const float2 kK = mul2(num, rcp2(add2(r2, f2(C.a2))));
+                const float2 omk2 = fma2(kK, make_float2(-kK.x, -kK.y), f2(1.f));
+                v = fma2(mul2(mul2(f2(C.m), r), rD2), omk2, f2(1.f));
+              }
+              float2 rv = rsqrt2(v);
+              if (mixed) {
+                const int bit = (si * Q + pi) * 2 * Q + 2 * k;
+                if (!(p.x > 0.f) || !(r2.x >= C.r2_fp64)) {
+                  v.x = rv.x = 0.f;
+                  slow |= 1ull << bit;
+                }
+                if (!(p.y > 0.f) || !(r2.y >= C.r2_fp64)) {
+                  v.y = rv.y = 0.f;
+                  slow |= 1ull << (bit + 1);
+                }
+              }
+              if (Q == 2) {
+                acc[si][k] = fma2(v, rv, acc[si][k]);  // unit Gauss weights
+              } else {
+                const float2 w = make_float2(gw * (float)Gauss<Q>::w((2 * k) % Q),
+                                             gw * (float)Gauss<Q>::w((2 * k + 1) % Q));
+                acc[si][k] = fma2(w, mul2(v, rv), acc[si][k]);
+              }
             }
-            double sq = sqJ[0];
-#pragma unroll
-            for (int t = 1; t < 2 * Q; ++t)
-              if (jb == t) sq = sqJ[t];
-            const double p64 = pRow64 + sq;
-            const double q64 = K == 0 ? C.da2 * sq : qRow64;
-            r2 = node_newton64(p64, q64, r2, D);
-            ++n64;
           }
-          float w = (float)Gauss<Q>::w(0), wj = (float)Gauss<Q>::w(0);
-#pragma unroll
-          for (int t = 1; t < Q; ++t) {
-            if (pi == t) w = (float)Gauss<Q>::w(t);
-            if (jb % Q == t) wj = (float)Gauss<Q>::w(t);
+        }
+        // S[si][sj]: the weighted integrand sums of the four sub-rectangles
+        float S[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  #pragma unroll
+        for (int si = 0; si < 2; ++si)
+  #pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            S[si][(2 * k) >= Q ? 1 : 0] += acc[si][k].x;
+            S[si][(2 * k + 1) >= Q ? 1 : 0] += acc[si][k].y;
           }
-          const float add = w * wj * node_value(C, L, r2, q, tRow + tJ);
-          const int sj = jb >= Q ? 1 : 0;
-          S[0][0] += (si == 0 && sj == 0) ? add : 0.f;
-          S[0][1] += (si == 0 && sj == 1) ? add : 0.f;
-          S[1][0] += (si == 1 && sj == 0) ? add : 0.f;
-          S[1][1] += (si == 1 && sj == 1) ? add : 0.f;
-        } while (slow);
+        // The marked nodes of FP32-mixed warps.  p and q in FP64 are sums of FP64 face, row and
+        // column terms, like their FP32 counterparts: face, row and column terms are formed once.
+        if (slow) {
+          const double cK = sel3(K, C.dxc, C.dyc, C.dzc), cI = sel3(K, C.dyc, C.dzc, C.dxc);
+          const double cJ = sel3(K, C.dzc, C.dxc, C.dyc);
+          const double XK64 = widen(L.PK) - cK;
+          const double pK64 = fma(XK64, XK64, -C.da2);
+          const double qK64 = K == 2 ? C.da2 * XK64 * XK64 : 0.0;
+          double sqJ[2 * Q];  // squared FP64 offsets of the columns
+  #pragma unroll
+          for (int jb = 0; jb < 2 * Q; ++jb) {
+            const double XJ64 = widen(col_coord<Q>(L, jb)) - cJ;
+            sqJ[jb] = XJ64 * XJ64;
+          }
+          int row = -1;
+          double pRow64 = 0.0, qRow64 = 0.0;
+          do {
+            const int b = __ffsll((long long)slow) - 1;
+            slow &= slow - 1ull;
+            const int ia = b / (2 * Q), jb = b - ia * 2 * Q;
+            const int si = ia / Q, pi = ia - si * Q;
+            const float AIa = row_coord<Q>(L, si, pi), AJ = col_coord<Q>(L, jb);
+            float pRow, qRow, tRow, pJ, qJ, tJ;
+            row_terms(C, L, AIa, pRow, qRow, tRow);
+            col_terms(C, L, AJ, pJ, qJ, tJ);
+            const float p = pRow + pJ, q = qRow + qJ;
+            // FP32 root by the cancellation-free form; FP64 where the policy asks for it (a node
+            // with p > 0 was marked only for that)
+            const float D = sqrtf(fmaf(p, p, 4.f * q));
+            float r2 = p >= 0.f ? 0.5f * (p + D) : __fdividef(2.f * q, D - p);
+            if (p > 0.f || !(r2 >= C.r2_fp64)) {
+              if (ia != row) {
+                row = ia;
+                const double XI64 = widen(AIa) - cI;
+                pRow64 = fma(XI64, XI64, pK64);
+                qRow64 = K == 1 ? C.da2 * XI64 * XI64 : qK64;
+              }
+              double sq = sqJ[0];
+  #pragma unroll
+              for (int t = 1; t < 2 * Q; ++t)
+                if (jb == t) sq = sqJ[t];
+              const double p64 = pRow64 + sq;
+              const double q64 = K == 0 ? C.da2 * sq : qRow64;
+              r2 = node_newton64(p64, q64, r2, D);
+              ++n64;
+            }
+            float w = (float)Gauss<Q>::w(0), wj = (float)Gauss<Q>::w(0);
+  #pragma unroll
+            for (int t = 1; t < Q; ++t) {
+              if (pi == t) w = (float)Gauss<Q>::w(t);
+              if (jb % Q == t) wj = (float)Gauss<Q>::w(t);
+            }
+            const float add = w * wj * node_value(C, L, r2, q, tRow + tJ);
+            const int sj = jb >= Q ? 1 : 0;
+            S[0][0] += (si == 0 && sj == 0) ? add : 0.f;
+            S[0][1] += (si == 0 && sj == 1) ? add : 0.f;
+            S[1][0] += (si == 1 && sj == 0) ? add : 0.f;
+            S[1][1] += (si == 1 && sj == 1) ? add : 0.f;
+          } while (slow);
+        }
+        const float wI[2] = {L.wI0, L.wI1};
+        A00 = S[1][1] * 0.25f * wI[1] * wJ[1];
+        A10 = S[0][1] * 0.25f * wI[0] * wJ[1];
+        A01 = S[1][0] * 0.25f * wI[1] * wJ[0];
+        A11 = S[0][0] * 0.25f * wI[0] * wJ[0];
       }
-      const float wI[2] = {L.wI0, L.wI1};
-      // sub-rectangle areas; a node's weight is the area of the sub-rectangle opposite it
-      const float A00 = S[1][1] * 0.25f * wI[1] * wJ[1];
-      const float A10 = S[0][1] * 0.25f * wI[0] * wJ[1];
-      const float A01 = S[1][0] * 0.25f * wI[1] * wJ[0];
-      const float A11 = S[0][0] * 0.25f * wI[0] * wJ[0];
       const float rFA = __fdividef(1.f, A00 + A10 + A01 + A11);
       // the face's four nodes: into the block's J tile when they lie in it, else into global J
       const int tx = cx - jt.ox, ty = cy - jt.oy, tz = cz - jt.oz;
@@ -750,16 +819,19 @@ __device__ __forceinline__ double reload(const double* p) {
   return v;
 }
 
-// One particle-step of particle i: RK4 push, new state stored, removal flag and sort key
-// (written to *key_out: P.key + i, or a side array where another kernel still reads P.key
-// concurrently), then the deposit of the move (which needs only x_n and the increment).
-// mixed (T = float): the FP32-mixed policy applies to this warp's particles (a warp-uniform
-// flag; false only where every particle lies outside near_radius).  T = double ignores it.
+// The move of a particle-step, which is all the deposit needs: x_n, the increment, q gamma-bar and
+// whether to deposit at all (finite state, charged species).
+template <typename T>
+struct Move {
+  T x0[3], dx[3], qg;
+  bool go;
+};
+
+// One particle-step of particle i without its deposit (push_particle below, up to the deposit).
 template <typename T, int Q>
-__device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F, const Particles<T>& P,
-                                              const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
-                                              unsigned& n64, uint32_t* key_out, bool mixed,
-                                              const JTile& jt = JTile()) {
+__device__ __forceinline__ Move<T> push_move(const Grid& g, const Fields<T>& F, const Particles<T>& P,
+                                             const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
+                                             unsigned& n64, uint32_t* key_out, bool mixed) {
   // RK4 in proper time: stages at offsets 0, h/2, h/2, h; h = dt / gamma_1 (Eq. 16).  x^4 does
   // not enter a~ (the metric is stationary), so the stages carry x^1..x^3 only.
   T xs[3], us[4], a[4], sx[4], su[4];
@@ -839,13 +911,43 @@ __device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F,
     *key_out = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
   }
   if (fb) atomicAdd(&st->fallbacks, 1ull);
-  // deposit, J = rho gamma v
-  if (finite && C.qmacro != T(0)) {
-    if constexpr (sizeof(T) == sizeof(float))
-      deposit_lattice<Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags, n64, mixed, jt);
-    else
-      deposit<T, Q>(g, F, C, x0, dx, C.qmacro * gbar, C.inv_dt, flags);
+  Move<T> mv;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    mv.x0[q] = x0[q];
+    mv.dx[q] = dx[q];
   }
+  mv.qg = C.qmacro * gbar;  // J = rho gamma v
+  mv.go = finite && C.qmacro != T(0);
+  return mv;
+}
+
+// The deposit of a move (Sec. 4).  TAB (far-field warps, T = float): face areas from the per-cell
+// fits atab.
+template <typename T, int Q, bool TAB = false>
+__device__ __forceinline__ void deposit_move(const Grid& g, const Fields<T>& F, const Consts<T>& C, const Move<T>& mv,
+                                             unsigned& flags, unsigned& n64, bool mixed, const JTile& jt = JTile(),
+                                             const float4* atab = nullptr) {
+  if (!mv.go) return;
+  if constexpr (sizeof(T) == sizeof(float))
+    deposit_lattice<Q, TAB>(g, F, C, mv.x0, mv.dx, mv.qg, C.inv_dt, flags, n64, mixed, jt, atab);
+  else
+    deposit<T, Q>(g, F, C, mv.x0, mv.dx, mv.qg, C.inv_dt, flags);
+}
+
+// One particle-step of particle i: RK4 push, new state stored, removal flag and sort key
+// (written to *key_out: P.key + i, or a side array where another kernel still reads P.key
+// concurrently), then the deposit of the move (which needs only x_n and the increment).
+// mixed (T = float): the FP32-mixed policy applies to this warp's particles (a warp-uniform
+// flag; false only where every particle lies outside near_radius).  T = double ignores it.
+// TAB (far-field warps, T = float): the deposit takes its face areas from the per-cell fits atab.
+template <typename T, int Q, bool TAB = false>
+__device__ __forceinline__ void push_particle(const Grid& g, const Fields<T>& F, const Particles<T>& P,
+                                              const Consts<T>& C, long long i, DevStatus* st, unsigned& flags,
+                                              unsigned& n64, uint32_t* key_out, bool mixed,
+                                              const JTile& jt = JTile(), const float4* atab = nullptr) {
+  const Move<T> mv = push_move<T, Q>(g, F, P, C, i, st, flags, n64, key_out, mixed);
+  deposit_move<T, Q, TAB>(g, F, C, mv, flags, n64, mixed, jt, atab);
 }
 
 // Warp-aggregated status: flags, FP64 evaluations and particle-steps of the warp's lanes.

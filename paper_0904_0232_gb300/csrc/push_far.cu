@@ -68,10 +68,13 @@ __global__ void __launch_bounds__(128, MINB) k_push_far(const Grid g, const Fiel
 constexpr int kJTileFloats = 3072;
 
 // perm: the block -> particle-chunk map (spread_chunk in common.cuh; 1 = in order).
-template <int Q, int MINB, bool TILE>
+// TAB: the far-field copy deposits with the per-cell area fits atab; r_near2 is then
+// table_radius^2, so that every far particle lies where the fits hold.
+template <int Q, int MINB, bool TILE, bool TAB = false>
 __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const Fields<float> F,
                                                            const Particles<float> P, const Consts<float> C,
-                                                           float r_near2, unsigned perm, int lg, DevStatus* st) {
+                                                           float r_near2, unsigned perm, int lg, DevStatus* st,
+                                                           const float4* __restrict__ atab) {
   const unsigned chunk = spread_chunk(blockIdx.x, gridDim.x, perm, lg);
   const long long i = chunk * (long long)blockDim.x + threadIdx.x;
   unsigned flags = 0, n64 = 0;
@@ -131,8 +134,21 @@ __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const F
   // calls at all (a call site in the loop would cost every warp registers and stack traffic)
   if (__any_sync(0xffffffffu, near)) {
     if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, true, jt);
-  } else {
-    if (active) push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false, jt);
+  } else if constexpr (TAB) {
+    if (active) {
+      // the fits of x_n's cell (the deposit's first segment) into L2 now, read after the RK4 stages
+      const int nn[3] = {g.nx, g.ny, g.nz};
+      int c[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) c[ax] = min(max((int)floorf(x0[ax]), 0), nn[ax] - 2);
+      const char* t = reinterpret_cast<const char*>(atab + cell_index(g, c[0], c[1], c[2]) * kAreaTableStride);
+#pragma unroll
+      for (int b = 0; b < 16 * kAreaTableStride; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(t + b));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 16 * kAreaTableStride - 1));
+      push_particle<float, Q, true>(g, F, P, C, i, st, flags, n64, P.key + i, false, jt, atab);
+    }
+  } else if (active) {
+    push_particle<float, Q>(g, F, P, C, i, st, flags, n64, P.key + i, false, jt);
   }
   warp_status(st, flags, n64, active);
   if constexpr (TILE) {
@@ -202,26 +218,31 @@ unsigned coprime_multiplier(unsigned n) {
 }
 
 void launch_push_select(const Grid& g, const Fields<float>& F, const Particles<float>& P, const Species& sp,
-                        DevStatus* st, int minb, bool tile, int spread, cudaStream_t stream) {
+                        DevStatus* st, int minb, bool tile, int spread, const float4* atab, cudaStream_t stream) {
   if (P.n <= 0) return;
   const unsigned nb = blocks_for(P.n, 128);
   const Consts<float> C = make_consts<float>(g, sp);
-  const double rn = near_radius(g);
+  const bool tab = atab != nullptr && g.quad_order == 2 && !tile;
+  const double rn = tab ? table_radius(g) : near_radius(g);
   const float r_near2 = (float)(rn * rn);
   const int lg = spread > 0 ? spread_log2(spread) : 0;
   const unsigned perm = spread > 0 ? spread_multiplier(nb, lg) : 1u;
   if (g.quad_order == 1)
-    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<1, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
   else if (g.quad_order == 3)
-    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<3, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
+  else if (tab && minb >= 5)
+    k_push_select<2, 5, false, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, atab);
+  else if (tab)
+    k_push_select<2, 4, false, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, atab);
   else if (tile && minb >= 5)
-    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<2, 5, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
   else if (tile)
-    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<2, 4, true><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
   else if (minb >= 5)
-    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<2, 5, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
   else
-    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st);
+    k_push_select<2, 4, false><<<nb, 128, 0, stream>>>(g, F, P, C, r_near2, perm, lg, st, nullptr);
 }
 
 }  // namespace grpic

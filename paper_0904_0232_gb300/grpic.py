@@ -70,7 +70,7 @@ class grpic_invariants(ctypes.Structure):
 class grpic_tuning(ctypes.Structure):
     _fields_ = [("far_min_blocks", ctypes.c_int), ("near_blocks_per_sm", ctypes.c_int), ("sort_interval", ctypes.c_int),
                 ("overlap", ctypes.c_int), ("split", ctypes.c_int), ("j_tile", ctypes.c_int),
-                ("spread", ctypes.c_int)]
+                ("spread", ctypes.c_int), ("area_table", ctypes.c_int)]
 
 
 EXPORTS = {
@@ -389,9 +389,9 @@ def grpic_gauss_residual(ctx, shape=None):
 
 
 def grpic_set_tuning(ctx, far_min_blocks, near_blocks_per_sm, sort_interval, overlap=1, split=0, j_tile=0,
-                     spread=0):
+                     spread=0, area_table=0):
     t = grpic_tuning(int(far_min_blocks), int(near_blocks_per_sm), int(sort_interval), int(overlap), int(split),
-                     int(j_tile), int(spread))
+                     int(j_tile), int(spread), int(area_table))
     _check(ctx, load_library().grpic_set_tuning(ctx, ctypes.byref(t)), "grpic_set_tuning")
 
 
@@ -400,7 +400,7 @@ def grpic_get_tuning(ctx):
     _check(ctx, load_library().grpic_get_tuning(ctx, ctypes.byref(t)), "grpic_get_tuning")
     return dict(far_min_blocks=t.far_min_blocks, near_blocks_per_sm=t.near_blocks_per_sm,
                 sort_interval=t.sort_interval, overlap=t.overlap, split=t.split, j_tile=t.j_tile,
-                spread=t.spread)
+                spread=t.spread, area_table=t.area_table)
 
 
 def grpic_check_newton64(n=1 << 22):
@@ -627,9 +627,9 @@ class Simulation:
         return grpic_get_profile(self.handle, reset)
 
     def set_tuning(self, far_min_blocks=4, near_blocks_per_sm=4, sort_interval=1, overlap=1, split=0, j_tile=0,
-                   spread=1):
+                   spread=1, area_table=0):
         grpic_set_tuning(self.handle, far_min_blocks, near_blocks_per_sm, sort_interval, overlap, split, j_tile,
-                         spread)
+                         spread, area_table)
 
     def tuning(self):
         return grpic_get_tuning(self.handle)
