@@ -45,10 +45,22 @@ ALG_FLOPS = {1: 3401, 2: 6641, 3: 12041}
 # Nominal FP32 CUDA-core peak of GB300: 152 SMs x 128 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 
-# DRAM bytes per particle-step of the push kernel (dram__bytes_read + dram__bytes_write of one
-# launch over its particles), from an ncu capture at the bench size, valid for the push sources
-# whose hash is recorded with it.
-PUSH_TRAFFIC = {"sha": "89f6fa0125cae024", "bytes_per_particle": 1379.84e6 / 15.61e6}
+# DRAM bytes per particle-step of the per-warp select push kernel (dram__bytes_read +
+# dram__bytes_write of one launch over its particles), from ncu captures at the bench size, per
+# variant (far-field area fits on or off, resident blocks per SM), valid for the push sources whose
+# hash is recorded with them.
+PUSH_TRAFFIC = {"sha": "3b9222721cf111f9",
+                "bytes_per_particle": {"area_table0_minb4": 1380.6e6 / 15.61e6,
+                                       "area_table0_minb5": 1400.5e6 / 15.61e6,
+                                       "area_table1_minb5": 2464.9e6 / 15.61e6}}
+
+
+def push_variant(tuning):
+    """Key of PUSH_TRAFFIC for a tuning dict (None: the per-warp push with its default shapes)."""
+    t = tuning or {}
+    if t.get("split", 0) != 0:
+        return None
+    return f"area_table{int(t.get('area_table', 0))}_minb{int(t.get('far_min_blocks', 4))}"
 
 
 def kernel_sha():
@@ -82,6 +94,9 @@ def parse():
     p.add_argument("--single-kernel-steps", type=int, default=200,
                    help="steps of the comparison run with the single mixed push kernel; 0 skips it")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
+    p.add_argument("--tuning", default=None,
+                   help="launch shapes as a JSON object of grpic_tuning fields (no autotuning), e.g. "
+                        "'{\"far_min_blocks\": 5, \"spread\": 16, \"sort_interval\": 4}'")
     p.add_argument("--batch-n", type=int, default=64)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -312,7 +327,9 @@ def run_gpu(args, dist):
 
     # --- launch shapes from the autotuner, on a context of its own (tuning advances its state)
     sig = f"kerr_ion_electron_{args.grid}|Q{args.quad}|{wl.n_particles}"
-    if args.no_tune:
+    if args.tuning:
+        tuned = {"tuning": json.loads(args.tuning), "cached": False, "trials": 0, "ms_per_step": None}
+    elif args.no_tune:
         tuned = {"tuning": None, "cached": False, "trials": 0, "ms_per_step": None}
     else:
         simt = make_sim(wl, "fp32_mixed", args)
@@ -363,8 +380,9 @@ def run_gpu(args, dist):
     fp32_probe = grpic_probe_fma_peak(GRPIC_FP32_MIXED)
     sha = kernel_sha()
     traffic = None
-    if PUSH_TRAFFIC["sha"] == sha and PUSH_TRAFFIC["bytes_per_particle"]:
-        traffic = PUSH_TRAFFIC["bytes_per_particle"] * psteps / max(1, push_n)
+    per_particle = PUSH_TRAFFIC["bytes_per_particle"].get(push_variant(tuning_used))
+    if PUSH_TRAFFIC["sha"] == sha and per_particle:
+        traffic = per_particle * psteps / max(1, push_n)
 
     # --- the FP64 path over the measured window (its first steps when --steps is longer; it runs at a
     #     small fraction of the FP32 rate), beside the FP32-mixed path over the same steps
@@ -423,11 +441,17 @@ def run_gpu(args, dist):
         t0 = time.perf_counter()
         sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", quad_order=args.quad,
                          sort_interval=args.sort_interval)
-        sim.set_tuning(**tuned["tuning"])
+        if tuned["tuning"] is not None:
+            sim.set_tuning(**tuned["tuning"])
+        t1 = time.perf_counter()
         sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
         for s, (sp, (x, u, i)) in enumerate(zip(wl.species, host_in)):
             sim.load_particles(s, sp.q_over_m, sp.q_macro, x, u, i, umode=GRPIC_U_COV_SPATIAL)
+        sim.sync()
+        t2 = time.perf_counter()
         sim.step_async(args.steps)
+        sim.sync()
+        t3 = time.perf_counter()
         out_bytes = 0
         for s, (x, u, i) in enumerate(host_out):
             nn = ctypes.c_int64(x.shape[1])
@@ -436,12 +460,14 @@ def run_gpu(args, dist):
         assert lib.grpic_get_fields(sim.handle, *(ptr(f) for f in fields_out), GRPIC_MEM_HOST) == 0
         out_bytes += sum(f.nbytes for f in fields_out)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = el_local = time.perf_counter() - t0
         ps_e2e = sim.stats()["particle_steps"]
         sim.close()
         el = dist.max(el)
         e2e = {"value": dist.sum(ps_e2e) / el, "unit": UNIT, "h2d_bytes_per_step": int(d_h2d / args.steps),
                "d2h_bytes_per_step": int(out_bytes / args.steps),
+               "phases_ms": {"create_and_tune": round((t1 - t0) * 1e3, 1), "fields_and_load": round((t2 - t1) * 1e3, 1),
+                             "steps": round((t3 - t2) * 1e3, 1), "readback": round((t0 + el_local - t3) * 1e3, 1)},
                "includes": "context creation, field init, particle load from pinned host memory (u^4 completed on "
                            "the device), K steps, read-back of every particle and field into pinned host memory"}
         del host_in, host_out, fields_out
@@ -459,7 +485,7 @@ def run_gpu(args, dist):
         "config": {"workload": f"kerr_ion_electron_{args.grid}: Kerr a=0.9m, m=4 cells, {args.grid}^3 grid, "
                                "e-/ion (mass ratio 20), 8 ppc per species, u_th=0.05c, B_z=0.1, dt=0.4",
                    "particles": wl.n_particles, "quad_order": args.quad,
-                   "tuning": dict(tuning_used, autotuned=not args.no_tune, cached=tuned["cached"],
+                   "tuning": dict(tuning_used, autotuned=not (args.no_tune or args.tuning), cached=tuned["cached"],
                                   trials=tuned["trials"]),
                    "window": f"steps {args.warmup + 1}-{args.warmup + args.steps} from the start; every "
                              "comparison leg starts from the same state",

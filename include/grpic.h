@@ -304,7 +304,8 @@ grpic_status grpic_gauss_residual(grpic_ctx* ctx, double* res, int mem, double* 
  *                       groups of G consecutive chunks, spreading the near-hole (FP64-heavy) chunks over
  *                       the launch while each group keeps neighbouring cells together (larger G: more
  *                       L2 locality, less even FP64 load); 0 keeps them in order
- *   area_table:         split = 0, Q = 2, j_tile = 0, FP32_MIXED only: 1 takes the face AREAs of Eq. 18
+ *   area_table:         split = 0, Q = 2, j_tile = 0 (with j_tile = 1 refused), FP32_MIXED (FP64 contexts
+ *                       keep it and ignore it, like the other push shapes): 1 takes the face AREAs of Eq. 18
  *                       for far-field warps from per-cell polynomial fits of the integrand instead of
  *                       the Q x Q Gauss nodes, and raises the far-field radius to
  *                       max(r_fp64 + |a| + 4, 4 + (m / 4.5e-7)^(1/6)) cells, where the fits' weights

@@ -8,16 +8,18 @@
 // form (the mean of t^i over [0, u] is u^i / (i+1), over [u, 1] it is (1 + u + ... + u^i) / (i+1)),
 // with no evaluation of the metric per particle.
 //
-// The fit: the integrand in FP64 at the 5 x 5 x 5 Chebyshev points of the cell, the tensor
-// Chebyshev interpolant, its terms of total degree <= 4, re-expanded in monomials of (u, v, w).
-// Far from the hole (particles at R >= table_radius) the weights W of Eq. 18 it gives agree with
-// Gauss-Legendre quadrature at Q = 2 on every sub-rectangle to a few 1e-9: the truncated terms
-// scale as m / r^6.  Near the hole the push keeps the per-node quadrature.
+// The fit: the integrand at the 5 x 5 x 5 Chebyshev points of the cell, the tensor Chebyshev
+// interpolant, its terms of total degree <= 4, re-expanded in monomials of (u, v, w).  Far from the
+// hole (particles at R >= table_radius) the truncated terms, which scale as m / r^6, move the
+// weights W of Eq. 18 by a few 1e-9 from Gauss-Legendre quadrature at Q = 2 on every sub-rectangle.
+// The samples and the fit are FP32, like the per-node integrand of the FP32 deposit: the fit is
+// of delta = g - 1, formed as x / (1 + sqrt(1 + x)) with x = f (1 - k_K^2), which keeps its
+// relative precision, and the 1 goes back into the constant term.  Near the hole the push keeps
+// the per-node quadrature.
 #include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
-#include "metric.cuh"
 
 namespace grpic {
 
@@ -26,23 +28,25 @@ namespace {
 constexpr int kN = 5;  // Chebyshev points per axis (degree 4)
 
 // t_i: the Chebyshev points of the first kind on [0, 1]; cheb[p][i]: value i -> coefficient p of
-// T_p(2t - 1) (discrete orthogonality); mono[a][p]: coefficient of t^a in T_p(2t - 1).
+// T_p(2t - 1) (discrete orthogonality); mono[a][p]: coefficient of t^a in T_p(2t - 1).  Formed in
+// FP64 on the host, passed in FP32.
 struct FitMatrices {
-  double t[kN];
-  double cheb[kN][kN];
-  double mono[kN][kN];
+  float t[kN];
+  float cheb[kN][kN];
+  float mono[kN][kN];
 };
 
 FitMatrices fit_matrices() {
   FitMatrices M{};
   const double pi = 3.14159265358979323846;
   for (int i = 0; i < kN; ++i) {
-    M.t[i] = 0.5 - 0.5 * std::cos((2 * i + 1) * pi / (2 * kN));
+    const double t = 0.5 - 0.5 * std::cos((2 * i + 1) * pi / (2 * kN));
+    M.t[i] = (float)t;
     // c_p = (2 - [p = 0]) / N sum_i f_i T_p(s_i) at the points s_i = 2 t_i - 1 = -cos((2i+1) pi / 2N)
-    const double s = 2.0 * M.t[i] - 1.0;
+    const double s = 2.0 * t - 1.0;
     double tp = 1.0, tq = s;  // T_p(s), T_{p+1}(s)
     for (int p = 0; p < kN; ++p) {
-      M.cheb[p][i] = (p == 0 ? 1.0 : 2.0) / kN * tp;
+      M.cheb[p][i] = (float)((p == 0 ? 1.0 : 2.0) / kN * tp);
       const double tn = 2.0 * s * tq - tp;
       tp = tq;
       tq = tn;
@@ -59,28 +63,30 @@ FitMatrices fit_matrices() {
       T[p + 1][a] = 2.0 * sT - T[p - 1][a];
     }
   for (int a = 0; a < kN; ++a)
-    for (int p = 0; p < kN; ++p) M.mono[a][p] = T[p][a];
+    for (int p = 0; p < kN; ++p) M.mono[a][p] = (float)T[p][a];
   return M;
 }
 
-// Eq. 18 integrand of the three face orientations at (X, Y, Z) (offsets from the centre), FP64
-// with the seeded reciprocal and root (a Newton step from the FP32 value: ~1e-14 relative).
-__device__ __forceinline__ void integrands(double X, double Y, double Z, double m, double a, double out[3]) {
-  double D;
-  const double r2 = kerr_r2<double, SeededOps64>(X, Y, Z, a, &D);
-  if (!(r2 > 0.0)) {
-    out[0] = out[1] = out[2] = 1.0;
+// delta_K = sqrt(1 + f (1 - k_K^2)) - 1, the Eq. 18 integrand minus one, of the three face
+// orientations at (X, Y, Z) (offsets from the centre).  r^2 from Eq. 6 in its cancellation-free
+// form, f = 2 m r / D at the root (Sigma = r^2 D); r = 0 (the disk z = 0, R <= a) takes the flat
+// limit.
+__device__ __forceinline__ void deltas(float X, float Y, float Z, float m, float a, float out[3]) {
+  const float a2 = a * a, q = a2 * Z * Z;
+  const float p = fmaf(X, X, fmaf(Y, Y, fmaf(Z, Z, -a2)));
+  const float D = sqrtf(fmaf(p, p, 4.f * q));
+  const float r2 = p >= 0.f ? 0.5f * (p + D) : 2.f * q / (D - p);
+  if (!(r2 > 0.f) || !(D > 0.f)) {
+    out[0] = out[1] = out[2] = 0.f;
     return;
   }
-  const double a2 = a * a;
-  const double r = SeededOps64::root(r2);
-  const double inv_sig = SeededOps64::rcp(r2 * r2 + a2 * Z * Z);
-  const double irho2 = SeededOps64::rcp(r2 + a2);
-  const double tm = 2.0 * m * r;
-  const double kx = (r * X - a * Y) * irho2, ky = (r * Y + a * X) * irho2;
-  out[0] = SeededOps64::root(1.0 + tm * r2 * (1.0 - kx * kx) * inv_sig);
-  out[1] = SeededOps64::root(1.0 + tm * r2 * (1.0 - ky * ky) * inv_sig);
-  out[2] = SeededOps64::root(1.0 + tm * (r2 - Z * Z) * inv_sig);
+  const float r = sqrtf(r2);
+  const float f = 2.f * m * r / D;
+  const float rho2 = r2 + a2;
+  const float kx = (r * X - a * Y) / rho2, ky = (r * Y + a * X) / rho2;
+  const float x[3] = {f * (1.f - kx * kx), f * (1.f - ky * ky), f * (r2 - Z * Z) / r2};
+#pragma unroll
+  for (int K = 0; K < 3; ++K) out[K] = x[K] / (1.f + sqrtf(1.f + x[K]));
 }
 
 // One thread per cell: the fits of its three face orientations, kAreaTableStride float4 per cell
@@ -96,72 +102,75 @@ __global__ void k_area_table(const Grid g, const FitMatrices M, float4* __restri
     for (int q = 0; q < 4 * kAreaTableStride; ++q) out[q] = 0.f;
     return;
   }
-  double val[3][kN][kN][kN];  // [K][ix][iy][iz]
+  // offsets of the cell's corner from the centre (exact in FP64, then rounded once)
+  const float ox = (float)(cx - g.xc), oy = (float)(cy - g.yc), oz = (float)(cz - g.zc);
+  const float m = (float)g.m, a = (float)g.a;
+  float val[3][kN][kN][kN];  // [K][ix][iy][iz]
   for (int ix = 0; ix < kN; ++ix)
     for (int iy = 0; iy < kN; ++iy)
       for (int iz = 0; iz < kN; ++iz) {
-        double o[3];
-        integrands(cx + M.t[ix] - g.xc, cy + M.t[iy] - g.yc, cz + M.t[iz] - g.zc, g.m, g.a, o);
+        float o[3];
+        deltas(ox + M.t[ix], oy + M.t[iy], oz + M.t[iz], m, a, o);
         val[0][ix][iy][iz] = o[0];
         val[1][ix][iy][iz] = o[1];
         val[2][ix][iy][iz] = o[2];
       }
   for (int K = 0; K < 3; ++K) {
     // A[iu][iv][s]: Chebyshev coefficients along w; then along v, then along u (total degree <= 4)
-    double A[kN][kN][kN], C[kN][kN][kN];
+    float A[kN][kN][kN], C[kN][kN][kN];
     for (int iu = 0; iu < kN; ++iu)
       for (int iv = 0; iv < kN; ++iv)
         for (int s = 0; s < kN; ++s) {
-          double acc = 0.0;
+          float acc = 0.f;
           for (int iw = 0; iw < kN; ++iw) {
             int p3[3];
             p3[K] = iw;
             p3[(K + 1) % 3] = iu;
             p3[(K + 2) % 3] = iv;
-            acc += M.cheb[s][iw] * val[K][p3[0]][p3[1]][p3[2]];
+            acc = fmaf(M.cheb[s][iw], val[K][p3[0]][p3[1]][p3[2]], acc);
           }
           A[iu][iv][s] = acc;
         }
     for (int iu = 0; iu < kN; ++iu)
       for (int q = 0; q < kN; ++q)
         for (int s = 0; s < kN; ++s) {
-          double acc = 0.0;
+          float acc = 0.f;
           if (q + s < kN)
-            for (int iv = 0; iv < kN; ++iv) acc += M.cheb[q][iv] * A[iu][iv][s];
+            for (int iv = 0; iv < kN; ++iv) acc = fmaf(M.cheb[q][iv], A[iu][iv][s], acc);
           C[iu][q][s] = acc;
         }
     for (int p = 0; p < kN; ++p)
       for (int q = 0; q < kN; ++q)
         for (int s = 0; s < kN; ++s) {
-          double acc = 0.0;
+          float acc = 0.f;
           if (p + q + s < kN)
-            for (int iu = 0; iu < kN; ++iu) acc += M.cheb[p][iu] * C[iu][q][s];
+            for (int iu = 0; iu < kN; ++iu) acc = fmaf(M.cheb[p][iu], C[iu][q][s], acc);
           A[p][q][s] = acc;  // Chebyshev coefficients of total degree <= 4, zero above
         }
     // re-expansion in monomials, one axis at a time (T_p(2t - 1) has degree p, so the total
     // degree stays <= 4)
-    for (int a = 0; a < kN; ++a)
+    for (int a_ = 0; a_ < kN; ++a_)
       for (int q = 0; q < kN; ++q)
         for (int s = 0; s < kN; ++s) {
-          double acc = 0.0;
-          for (int p = a; p < kN; ++p) acc += M.mono[a][p] * A[p][q][s];
-          C[a][q][s] = acc;
+          float acc = 0.f;
+          for (int p = a_; p < kN; ++p) acc = fmaf(M.mono[a_][p], A[p][q][s], acc);
+          C[a_][q][s] = acc;
         }
-    for (int a = 0; a < kN; ++a)
+    for (int a_ = 0; a_ < kN; ++a_)
       for (int b = 0; b < kN; ++b)
         for (int s = 0; s < kN; ++s) {
-          double acc = 0.0;
-          for (int q = b; q < kN; ++q) acc += M.mono[b][q] * C[a][q][s];
-          A[a][b][s] = acc;
+          float acc = 0.f;
+          for (int q = b; q < kN; ++q) acc = fmaf(M.mono[b][q], C[a_][q][s], acc);
+          A[a_][b][s] = acc;
         }
     float* o = out + 36 * K;
     int n = 0;
     for (int j = 0; j < kN; ++j)
       for (int i = 0; i + j < kN; ++i)
         for (int k = 0; i + j + k < kN; ++k) {
-          double acc = 0.0;
-          for (int s = k; s < kN; ++s) acc += M.mono[k][s] * A[i][j][s];
-          o[n++] = (float)acc;
+          float acc = 0.f;
+          for (int s = k; s < kN; ++s) acc = fmaf(M.mono[k][s], A[i][j][s], acc);
+          o[n++] = (i + j + k == 0) ? 1.f + acc : acc;  // the integrand is 1 + delta
         }
     o[35] = 0.f;
   }

@@ -1162,9 +1162,8 @@ grpic_status grpic_set_tuning(grpic_ctx* c, const grpic_tuning* t) {
       t->spread < 0 || t->spread > 64 || (t->spread & (t->spread - 1)) != 0 ||
       (t->area_table != 0 && t->area_table != 1))
     return fail(c, GRPIC_ERR_INVALID, "tuning out of range");
-  if (t->area_table && (!c->mixed || t->j_tile))
-    return fail(c, GRPIC_ERR_INVALID, "area_table needs an FP32_MIXED context and j_tile = 0");
-  if (t->area_table && !c->atab) {
+  if (t->area_table && t->j_tile) return fail(c, GRPIC_ERR_INVALID, "area_table excludes j_tile");
+  if (t->area_table && c->mixed && !c->atab) {
     c->atab = static_cast<float4*>(dev_alloc(c, sizeof(float4) * kAreaTableStride * (size_t)c->g.ncell));
     if (!c->atab) return fail(c, GRPIC_ERR_OOM, "area table allocation");
     launch_area_table(c->g, c->atab, c->stream);

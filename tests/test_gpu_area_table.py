@@ -109,8 +109,8 @@ def test_whole_steps_against_oracle():
 
 
 def test_tuning_round_trip_and_refusals():
-    """area_table is FP32_MIXED only and excludes the J tile; the fits are kept when it is switched
-    off and on again."""
+    """area_table excludes the J tile; the fits are kept when it is switched off and on again; an FP64
+    context keeps the setting and ignores it (its deposit is the FP64 quadrature)."""
     wl = _workload(n=24)
     sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed")
     sim.set_tuning(area_table=1)
@@ -122,6 +122,8 @@ def test_tuning_round_trip_and_refusals():
     sim.set_tuning(area_table=1)
     sim.close()
     f64 = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision="fp64")
+    f64.set_tuning(area_table=1)
+    assert f64.tuning()["area_table"] == 1
     with pytest.raises(GrpicError):
-        f64.set_tuning(area_table=1)
+        f64.set_tuning(area_table=1, j_tile=1)
     f64.close()

@@ -110,8 +110,8 @@ def test_full_size_j_element_by_element(workload, oracle_fields, prec, shapes):
     """J node by node at the full 128^3 grid size: a strided 1/500 sample of both species (plus the
     300 particles of each closest to the hole) pushed and deposited into an empty J by a context of
     the bench's grid with the bench's launch shapes ("tuned": the per-warp select push with chunks
-    spread in groups of 16; "table": the same with the far-field face areas from the per-cell fits,
-    FP32-mixed only; "default": single chunks), and
+    spread in groups of 16; "table": as the autotuner picks with the far-field face areas from the
+    per-cell fits, 5 resident blocks per SM, FP32-mixed only; "default": single chunks), and
     by the oracle, from the fields after the first B half-step.  Every J node is compared (FP32: off
     the nodes of zig-zag splits decided within rounding of a face, and the total flux everywhere).
     Both sides start from positions representable in FP32: a grid coordinate near 100 rounds to FP32
@@ -128,9 +128,12 @@ def test_full_size_j_element_by_element(workload, oracle_fields, prec, shapes):
     if prec == "fp64" and shapes == "table":
         pytest.skip("the area fits are an FP32-mixed option")
     sim = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=prec)
-    if prec == "fp32_mixed" and shapes != "default":
+    if prec == "fp32_mixed" and shapes == "tuned":
         sim.set_tuning(far_min_blocks=4, near_blocks_per_sm=1, sort_interval=4, overlap=0, split=0, j_tile=0,
-                       spread=16, area_table=int(shapes == "table"))
+                       spread=16)
+    elif prec == "fp32_mixed" and shapes == "table":
+        sim.set_tuning(far_min_blocks=5, near_blocks_per_sm=1, sort_interval=4, overlap=1, split=0, j_tile=0,
+                       spread=16, area_table=1)
     sim.set_fields(dr, br)
     n = 0
     for s, sp in enumerate(wl.species):

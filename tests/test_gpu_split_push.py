@@ -104,19 +104,20 @@ def test_split_equals_single_kernel(mode):
         assert np.abs(xs - xq).max() <= 1e-5 * np.abs(xq).max()
 
 
-@pytest.mark.parametrize("far,near,overlap,split,j_tile,spread", [
-    (4, 1, 1, 1, 0, 0), (5, 2, 0, 1, 0, 0), (6, 3, 1, 1, 0, 0), (5, 4, 0, 1, 0, 0), (4, 4, 1, 0, 0, 0),
-    (5, 4, 1, 0, 0, 0), (4, 4, 1, 0, 1, 0), (5, 4, 1, 0, 1, 0), (4, 4, 1, 0, 0, 1), (5, 4, 1, 0, 1, 1),
-    (4, 4, 1, 0, 0, 4), (4, 4, 1, 0, 0, 16), (5, 4, 1, 0, 1, 64)])
-def test_tuning_variants_agree(far, near, overlap, split, j_tile, spread):
+@pytest.mark.parametrize("far,near,overlap,split,j_tile,spread,table", [
+    (4, 1, 1, 1, 0, 0, 0), (5, 2, 0, 1, 0, 0, 0), (6, 3, 1, 1, 0, 0, 0), (5, 4, 0, 1, 0, 0, 0),
+    (4, 4, 1, 0, 0, 0, 0), (5, 4, 1, 0, 0, 0, 0), (4, 4, 1, 0, 1, 0, 0), (5, 4, 1, 0, 1, 0, 0),
+    (4, 4, 1, 0, 0, 1, 0), (5, 4, 1, 0, 1, 1, 0), (4, 4, 1, 0, 0, 4, 0), (4, 4, 1, 0, 0, 16, 0),
+    (5, 4, 1, 0, 1, 64, 0), (4, 4, 1, 0, 0, 16, 1), (5, 4, 1, 0, 0, 1, 1)])
+def test_tuning_variants_agree(far, near, overlap, split, j_tile, spread, table):
     wl = _workload(seed=33)
     ref = oracle_start(wl)
     base = gpu_from_oracle(ref, wl, "fp32_mixed", flags=GRPIC_SINGLE_PUSH_KERNEL)
     var = gpu_from_oracle(ref, wl, "fp32_mixed")
     var.set_tuning(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap, split=split,
-                   j_tile=j_tile, spread=spread)
+                   j_tile=j_tile, spread=spread, area_table=table)
     assert var.tuning() == dict(far_min_blocks=far, near_blocks_per_sm=near, sort_interval=1, overlap=overlap,
-                                split=split, j_tile=j_tile, spread=spread)
+                                split=split, j_tile=j_tile, spread=spread, area_table=table)
     _push_once(base)
     _push_once(var)
     (pb, Jb, sb), (pv, Jv, sv) = _state(base), _state(var)
