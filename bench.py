@@ -384,39 +384,12 @@ def run_gpu(args, dist):
     if PUSH_TRAFFIC["sha"] == sha and per_particle:
         traffic = per_particle * psteps / max(1, push_n)
 
-    # --- the FP64 path over the measured window (its first steps when --steps is longer; it runs at a
-    #     small fraction of the FP32 rate), beside the FP32-mixed path over the same steps
-    fp64 = None
-    n64 = min(args.fp64_steps, args.steps)
-    if n64 > 0:
-        ms64, ps64, prof64, _, _, _ = leg("fp64", n64, args.warmup)
-        if n64 == args.steps:
-            msw, psw, profw = ms, psteps, prof
-        else:
-            msw, psw, profw, _, _, _ = leg("fp32_mixed", n64, args.warmup)
-        fp64 = summary(ms64, ps64, prof64, n64, f"steps {args.warmup + 1}-{args.warmup + n64} from the start")
-        fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, n64)
-
-    # --- the same steps with every particle through the FP32-mixed code (no far-field path)
-    single = None
-    if args.single_kernel_steps > 0:
-        ms1, ps1, prof1, _, _, _ = leg("fp32_mixed", args.single_kernel_steps, args.warmup,
-                                       flags=GRPIC_SINGLE_PUSH_KERNEL)
-        single = summary(ms1, ps1, prof1, args.single_kernel_steps,
-                         "GRPIC_SINGLE_PUSH_KERNEL: every particle through the FP32-mixed code")
-
-    # --- the same steps with the FP64 region switched off (all-FP32 metric evaluations)
-    fp32_all = None
-    if args.fp32_compare_steps > 0:
-        ms32, ps32, prof32, _, _, _ = leg("fp32_mixed", args.fp32_compare_steps, args.warmup, fp64_radius=-1.0)
-        fp32_all = summary(ms32, ps32, prof32, args.fp32_compare_steps,
-                           "fp64_radius < 0: no FP64 metric evaluations (the FP32-only comparison; its particle error against "
-                           "the FP64 oracle after one push is ~1e-7 relative, like the policy's)")
-
     # --- end to end through the C ABI with host buffers: the inputs and outputs live in pinned host
     # memory (prepared before the timed region, as a caller's staging buffers would be); inside it:
     # context creation, field init, particle load (host -> device, u^4 completed), K steps, and the
-    # read-back of every particle and field
+    # read-back of every particle and field.  It runs right after the main leg, in the process state a
+    # user's program has: after the comparison legs below, the read-back's staging allocations were
+    # 3-8x slower (the caching allocator's state), which is not the library's cost.
     e2e = None
     if not args.no_e2e:
         import ctypes
@@ -471,6 +444,35 @@ def run_gpu(args, dist):
                "includes": "context creation, field init, particle load from pinned host memory (u^4 completed on "
                            "the device), K steps, read-back of every particle and field into pinned host memory"}
         del host_in, host_out, fields_out
+
+    # --- the FP64 path over the measured window (its first steps when --steps is longer; it runs at a
+    #     small fraction of the FP32 rate), beside the FP32-mixed path over the same steps
+    fp64 = None
+    n64 = min(args.fp64_steps, args.steps)
+    if n64 > 0:
+        ms64, ps64, prof64, _, _, _ = leg("fp64", n64, args.warmup)
+        if n64 == args.steps:
+            msw, psw, profw = ms, psteps, prof
+        else:
+            msw, psw, profw, _, _, _ = leg("fp32_mixed", n64, args.warmup)
+        fp64 = summary(ms64, ps64, prof64, n64, f"steps {args.warmup + 1}-{args.warmup + n64} from the start")
+        fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, n64)
+
+    # --- the same steps with every particle through the FP32-mixed code (no far-field path)
+    single = None
+    if args.single_kernel_steps > 0:
+        ms1, ps1, prof1, _, _, _ = leg("fp32_mixed", args.single_kernel_steps, args.warmup,
+                                       flags=GRPIC_SINGLE_PUSH_KERNEL)
+        single = summary(ms1, ps1, prof1, args.single_kernel_steps,
+                         "GRPIC_SINGLE_PUSH_KERNEL: every particle through the FP32-mixed code")
+
+    # --- the same steps with the FP64 region switched off (all-FP32 metric evaluations)
+    fp32_all = None
+    if args.fp32_compare_steps > 0:
+        ms32, ps32, prof32, _, _, _ = leg("fp32_mixed", args.fp32_compare_steps, args.warmup, fp64_radius=-1.0)
+        fp32_all = summary(ms32, ps32, prof32, args.fp32_compare_steps,
+                           "fp64_radius < 0: no FP64 metric evaluations (the FP32-only comparison; its particle error against "
+                           "the FP64 oracle after one push is ~1e-7 relative, like the policy's)")
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu:
