@@ -310,8 +310,9 @@ grpic_status grpic_gauss_residual(grpic_ctx* ctx, double* res, int mem, double* 
  *                       the Q x Q Gauss nodes, and raises the far-field radius to
  *                       max(r_fp64 + |a| + 4, 4 + (m / 4.5e-7)^(1/6)) cells, where the fits' weights
  *                       agree with the Q = 2 quadrature to a few 1e-9.  The fits (total degree 4 in the
- *                       cell fractions, 36 FP32 coefficients per cell and face orientation: 432 bytes
- *                       per cell) are allocated and computed on the context's stream by the first
+ *                       cell fractions, 35 coefficients per cell and face orientation, the constant and
+ *                       linear ones in FP32, the others in FP16: 256 bytes per cell) are allocated and
+ *                       computed on the context's stream by the first
  *                       grpic_set_tuning that sets it (GRPIC_ERR_OOM if they do not fit) and kept
  *                       until grpic_destroy
  * grpic_set_tuning validates all fields (GRPIC_ERR_INVALID) and applies them from the next step. */

@@ -16,6 +16,8 @@
 // of delta = g - 1, formed as x / (1 + sqrt(1 + x)) with x = f (1 - k_K^2), which keeps its
 // relative precision, and the 1 goes back into the constant term.  Near the hole the push keeps
 // the per-node quadrature.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -90,8 +92,7 @@ __device__ __forceinline__ void deltas(float X, float Y, float Z, float m, float
 }
 
 // One thread per cell: the fits of its three face orientations, kAreaTableStride float4 per cell
-// (36 floats per K: for j = 0..4, i = 0..4-j, the coefficients of w^0..w^(4-i-j) of u^i v^j; the
-// 36th is zero).  Cells past n-2 on an axis (never a deposit cell) are zeroed.
+// (layout in common.cuh).  Cells past n-2 on an axis (never a deposit cell) are zeroed.
 __global__ void k_area_table(const Grid g, const FitMatrices M, float4* __restrict__ tab) {
   const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (cell >= g.ncell) return;
@@ -163,17 +164,27 @@ __global__ void k_area_table(const Grid g, const FitMatrices M, float4* __restri
           for (int q = b; q < kN; ++q) acc = fmaf(M.mono[b][q], C[a_][q][s], acc);
           A[a_][b][s] = acc;
         }
-    float* o = out + 36 * K;
+    float cf[kFitTerms];
     int n = 0;
     for (int j = 0; j < kN; ++j)
       for (int i = 0; i + j < kN; ++i)
         for (int k = 0; i + j + k < kN; ++k) {
           float acc = 0.f;
           for (int s = k; s < kN; ++s) acc = fmaf(M.mono[k][s], A[i][j][s], acc);
-          o[n++] = (i + j + k == 0) ? 1.f + acc : acc;  // the integrand is 1 + delta
+          cf[n++] = (i + j + k == 0) ? 1.f + acc : acc;  // the integrand is 1 + delta
         }
-    o[35] = 0.f;
+    float* o = out + 20 * K;
+    o[0] = cf[0];
+    o[1] = cf[1];
+    o[2] = cf[5];
+    o[3] = cf[15];
+    __half* h = reinterpret_cast<__half*>(o + 4);
+    int q = 0;
+    for (int t = 0; t < kFitTerms; ++t)
+      if (!fit_term_fp32(t)) h[q++] = __float2half_rn(cf[t]);
+    h[q] = __float2half_rn(0.f);
   }
+  for (int q = 60; q < 64; ++q) out[q] = 0.f;
 }
 
 }  // namespace

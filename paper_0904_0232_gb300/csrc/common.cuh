@@ -253,11 +253,17 @@ __host__ __device__ inline double near_radius(const Grid& g) {
 }
 
 // Far-field deposit from per-cell polynomial fits of the Eq. 18 integrand (area_table.cu):
-// kAreaTableStride float4 per cell (36 coefficients for each face orientation K), indexed by the
-// cell's linear index.  table_radius: a warp takes the table only if every particle has
-// R(x_n) >= table_radius (>= near_radius; where the fit's truncation error, ~m / r^6, leaves the
-// weights within a few 1e-9 of Q = 2 Gauss quadrature).
-constexpr int kAreaTableStride = 27;
+// kAreaTableStride float4 (256 bytes, two cache lines) per cell, indexed by the cell's linear index.
+// The fit of face orientation K (kFitTerms coefficients; term t enumerates u^i v^j w^k for j = 0..4,
+// i = 0..4-j, k = 0..4-i-j) takes the 5 float4 from 5K: four FP32 (terms 0, 1, 5, 15: the constant and
+// the linear terms w, u, v), then the other 31 terms in FP16 in term order and one zero; float4 15 is
+// zero.  The FP16 terms (second order and up: ~m / r^3 and smaller) keep absolute errors below 2e-7.
+// table_radius: a warp takes the fits only if every particle has R(x_n) >= table_radius
+// (>= near_radius; where the fit's truncation error, ~m / r^6, leaves the weights within a few 1e-9
+// of Q = 2 Gauss quadrature).
+constexpr int kAreaTableStride = 16;
+constexpr int kFitTerms = 35;
+__host__ __device__ constexpr bool fit_term_fp32(int t) { return t == 0 || t == 1 || t == 5 || t == 15; }
 double table_radius(const Grid& g);
 void launch_area_table(const Grid& g, float4* tab, cudaStream_t st);
 

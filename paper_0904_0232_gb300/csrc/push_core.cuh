@@ -25,6 +25,8 @@
 // the FP64 J accumulators are widened with integer operations (widen below).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cmath>
 
 #include "common.cuh"
@@ -500,20 +502,36 @@ __device__ __forceinline__ void interval_means(float x, float2 M[5]) {
 }
 
 // The four sub-rectangle AREAs of Eq. 18 in the face plane at fraction w along K of a cell, split
-// at fractions (u, v) along (I, J), from the cell's polynomial fit t (36 coefficients, area_table.cu:
-// for j = 0..4, i = 0..4-j, the coefficients of w^0..w^(4-i-j) of u^i v^j).  With c_ij the fit's
-// u^i v^j coefficient at w, the area over U x V is |U| |V| sum_ij c_ij mean_U(u^i) mean_V(v^j).
+// at fractions (u, v) along (I, J), from the cell's polynomial fit t (the 5 float4 of one face
+// orientation, layout at kAreaTableStride in common.cuh: term n enumerates, for j = 0..4, i = 0..4-j,
+// the coefficients of w^0..w^(4-i-j) of u^i v^j).  With c_ij the fit's u^i v^j coefficient at w, the
+// area over U x V is |U| |V| sum_ij c_ij mean_U(u^i) mean_V(v^j).
 // A00 = [u,1] x [v,1], A10 = [0,u] x [v,1], A01 = [u,1] x [0,v], A11 = [0,u] x [0,v].
 __device__ __forceinline__ void table_areas(const float4* __restrict__ t, float u, float v, float w, float& A00,
                                             float& A10, float& A01, float& A11) {
-  float c[36];
+  float c[kFitTerms];
+  const float4 e = __ldg(t);
+  c[0] = e.x;
+  c[1] = e.y;
+  c[5] = e.z;
+  c[15] = e.w;
+  float hv[32];  // the FP16 terms in term order
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const float4 e = __ldg(t + q);
-    c[4 * q] = e.x;
-    c[4 * q + 1] = e.y;
-    c[4 * q + 2] = e.z;
-    c[4 * q + 3] = e.w;
+  for (int q = 0; q < 4; ++q) {
+    const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(t + 1 + q));
+    const unsigned wd[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&wd[r]));
+      hv[8 * q + 2 * r] = f.x;
+      hv[8 * q + 2 * r + 1] = f.y;
+    }
+  }
+  {
+    int h = 0;
+#pragma unroll
+    for (int n = 0; n < kFitTerms; ++n)
+      if (!fit_term_fp32(n)) c[n] = hv[h++];
   }
   float2 Mu[5], Mv[5];
   interval_means(u, Mu);
@@ -607,7 +625,7 @@ __device__ __forceinline__ void deposit_lattice(const Grid& g, const Fields<floa
       const float frI = sel3(K, fr[1], fr[2], fr[0]), frJ = sel3(K, fr[2], fr[0], fr[1]);
       float A00, A10, A01, A11;  // sub-rectangle areas; a node's weight is the area opposite it
       if constexpr (TAB) {
-        table_areas(atab + base * kAreaTableStride + 9 * K, frI, frJ, sel3(K, fr[0], fr[1], fr[2]), A00, A10,
+        table_areas(atab + base * kAreaTableStride + 5 * K, frI, frJ, sel3(K, fr[0], fr[1], fr[2]), A00, A10,
                     A01, A11);
       } else {
         FaceLattice L;

@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(128, MINB) k_push_select(const Grid g, const F
       const char* t = reinterpret_cast<const char*>(atab + cell_index(g, c[0], c[1], c[2]) * kAreaTableStride);
 #pragma unroll
       for (int b = 0; b < 16 * kAreaTableStride; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(t + b));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(t + 16 * kAreaTableStride - 1));
       push_particle<float, Q, true>(g, F, P, C, i, st, flags, n64, P.key + i, false, jt, atab);
     }
   } else if (active) {
