@@ -83,6 +83,9 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=20,
                    help="steps of the FP64 comparison leg (at most --steps), after the same warm-up as the "
                         "measured window; 0 skips it")
+    p.add_argument("--fp64-late-steps", type=int, default=10,
+                   help="steps of the FP64 and FP32-mixed legs from the state at the end of the measured "
+                        "window (read back by the end-to-end leg); 0 skips them")
     p.add_argument("--fp32-compare-steps", type=int, default=200,
                    help="steps of the all-FP32 comparison run (no FP64 region); 0 skips it")
     p.add_argument("--workload", choices=["kerr128", "batch", "disk384", "jet", "fields"], default="kerr128",
@@ -227,7 +230,7 @@ def run_oracle_steps(wl, steps, warmup=0):
     return psteps, el, O.max_threads(), per_step
 
 
-def cpu_baseline(steps=20):
+def cpu_baseline(steps=150):
     wl = cpu_sample_workload()
     psteps, el, cores, _ = run_oracle_steps(wl, steps)
     return {"value": psteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -391,6 +394,7 @@ def run_gpu(args, dist):
     # user's program has: after the comparison legs below, the read-back's staging allocations were
     # 3-8x slower (the caching allocator's state), which is not the library's cost.
     e2e = None
+    late = None
     if not args.no_e2e:
         import ctypes
 
@@ -426,10 +430,12 @@ def run_gpu(args, dist):
         sim.sync()
         t3 = time.perf_counter()
         out_bytes = 0
+        counts = []
         for s, (x, u, i) in enumerate(host_out):
             nn = ctypes.c_int64(x.shape[1])
             assert lib.grpic_get_particles(sim.handle, s, ctypes.byref(nn), ptr(x), ptr(u), ptr(i), GRPIC_MEM_HOST) == 0
             out_bytes += nn.value * (x.itemsize * 8 + i.itemsize)
+            counts.append(nn.value)
         assert lib.grpic_get_fields(sim.handle, *(ptr(f) for f in fields_out), GRPIC_MEM_HOST) == 0
         out_bytes += sum(f.nbytes for f in fields_out)
         torch.cuda.synchronize()
@@ -443,6 +449,8 @@ def run_gpu(args, dist):
                              "steps": round((t3 - t2) * 1e3, 1), "readback": round((t0 + el_local - t3) * 1e3, 1)},
                "includes": "context creation, field init, particle load from pinned host memory (u^4 completed on "
                            "the device), K steps, read-back of every particle and field into pinned host memory"}
+        if args.fp64_late_steps > 0:
+            late = late_window(wl, args, dist, tuned["tuning"], host_out, counts, fields_out, summary)
         del host_in, host_out, fields_out
 
     # --- the FP64 path over the measured window (its first steps when --steps is longer; it runs at a
@@ -503,6 +511,7 @@ def run_gpu(args, dist):
                      "fma_probe_tflops": fp32_probe / 1e12,
                      "flops_per_particle_step": ALG_FLOPS[args.quad], "kernel_sha": sha},
         "fp64": fp64,
+        "fp64_late_window": late,
         "single_push_kernel": single,
         "fp32_no_fp64_region": fp32_all,
         "e2e": e2e,
@@ -512,6 +521,43 @@ def run_gpu(args, dist):
         "invariants": invariant_summary(invariants["start"], invariants["end"], args.steps),
     }
     return line
+
+
+def late_window(wl, args, dist, tuning, host_out, counts, fields_out, summary):
+    """The FP64 path against the FP32-mixed path at the END of the measured window, where the most
+    particles have gathered near the hole: both start from the state the end-to-end leg read back
+    after its K steps (every particle with its full u^a and own clock, and the fields b, d), take
+    one untimed step, then --fp64-late-steps timed steps."""
+    import torch
+
+    from paper_0904_0232_gb300.grpic import GRPIC_U_FULL, Simulation
+
+    out = {}
+    try:
+        for precision in ("fp64", "fp32_mixed"):
+            s_ = Simulation(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, precision=precision, quad_order=args.quad,
+                            sort_interval=args.sort_interval)
+            if tuning is not None:
+                s_.set_tuning(**tuning)
+            s_.set_fields(fields_out[0], fields_out[1])
+            for sidx, (sp, (x, u, i), nn) in enumerate(zip(wl.species, host_out, counts)):
+                # planes of the read-back are nn apart (the count written), not the buffers' capacity
+                x4 = x.reshape(-1)[:4 * nn].reshape(4, nn)
+                u4 = u.reshape(-1)[:4 * nn].reshape(4, nn)
+                s_.load_particles(sidx, sp.q_over_m, sp.q_macro, x4, u4, i[:nn], umode=GRPIC_U_FULL)
+            s_.set_profiling(True)
+            s_.step(1)
+            ms_, ps_, prof_, _ = timed_steps(s_, args.fp64_late_steps, dist)
+            s_.close()
+            del s_
+            torch.cuda.empty_cache()
+            out[precision] = summary(ms_, ps_, prof_, args.fp64_late_steps)
+    except Exception as exc:  # a comparison leg: report, do not lose the line
+        return {"error": repr(exc)}
+    k = args.fp64_late_steps
+    out["note"] = (f"steps {args.steps + 2}-{args.steps + 1 + k} of a run (from the state after the end-to-end leg's "
+                   f"{args.steps} steps, one untimed step)")
+    return out
 
 
 def invariant_summary(start, end, steps):
