@@ -487,6 +487,8 @@ def run_gpu(args, dist):
         cpu = cpu_baseline()
 
     stage_ms = {k: round(v[0] / max(1, args.steps), 4) for k, v in prof.items()}
+    hbm_stages = hbm_stage_summary(prof, args.steps, wl.nx * wl.ny * wl.nz, psteps / max(1, args.steps),
+                                   tuning_used.get("sort_interval", args.sort_interval))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -503,6 +505,7 @@ def run_gpu(args, dist):
                    "l2": "inputs larger than L2 (particle store %.2f GB)" % (wl.n_particles * 40 / 1e9)},
         "gpu_launches": int(launches),
         "stage_ms_per_step": stage_ms,
+        "hbm_stages": hbm_stages,
         "roofline": {"kernel": "push stage (k_push_select: far-field FP32 or FP32-mixed code per warp; with "
                                "tuning split=1 the k_classify_near + k_push_near + k_push_far kernels)",
                      "bound": "alu", "achieved": achieved / 1e12,
@@ -782,6 +785,41 @@ def run_jet(args, dist):
 # reads b, d and writes b^n (9 words); the second, time-centred, also reads b^{n-1/2} (12 words); the
 # E step reads b, d, J and writes d (9 words + 24 B); J = 0 writes 24 B.
 FIELD_BYTES = {"b_half": 36, "b_half2": 48, "e_step": 60, "zero_j": 24}
+
+
+# Sort: the key of every particle read by the histogram, then each 40-byte record (x^1..3, the
+# clock offset, u^1..4 in FP32, id) read and written by the scatter.
+SORT_BYTES = 4 + 2 * 40
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh).get("hbm_gbs", 6800.0)), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+def hbm_stage_summary(prof, steps, cells, particles, sort_interval):
+    """The HBM-bound stages of a measured run (the field stages and the sort) against their
+    algorithmic bytes: device time per step from the run's CUDA events, bytes per cell (fields) or
+    per particle and sort (sort; one sort every sort_interval steps)."""
+    hbm, src = measured_hbm_gbs()
+    out = {"peak_gbs": hbm, "peak_source": src}
+    for k, nbytes in FIELD_BYTES.items():
+        if k not in prof or prof[k][0] <= 0:
+            continue
+        t = prof[k][0] / max(1, steps) * 1e-3
+        gbs = nbytes * cells / t / 1e9
+        out[k] = {"ms": round(t * 1e3, 4), "algorithmic_bytes": nbytes * cells, "gbs": round(gbs, 1),
+                  "frac": round(gbs / hbm, 3)}
+    if "sort" in prof and prof["sort"][0] > 0:
+        t = prof["sort"][0] / max(1, steps) * 1e-3
+        nbytes = SORT_BYTES * particles / max(1, sort_interval)
+        gbs = nbytes / t / 1e9
+        out["sort"] = {"ms": round(t * 1e3, 4), "algorithmic_bytes": nbytes, "gbs": round(gbs, 1),
+                       "frac": round(gbs / hbm, 3), "sort_interval": sort_interval}
+    return out
 
 
 def run_fields(args, dist):
