@@ -465,6 +465,10 @@ def run_gpu(args, dist):
             msw, psw, profw, _, _, _ = leg("fp32_mixed", n64, args.warmup)
         fp64 = summary(ms64, ps64, prof64, n64, f"steps {args.warmup + 1}-{args.warmup + n64} from the start")
         fp64["fp32_mixed_same_window"] = summary(msw, psw, profw, n64)
+        if profw["push_deposit"][0] > 0:
+            # the push's fraction over these early steps, before particles gather near the hole
+            early_frac = ALG_FLOPS[args.quad] * psw / (profw["push_deposit"][0] * 1e-3) / FP32_PEAK_NOMINAL
+            fp64["fp32_mixed_same_window"]["push_roofline_frac"] = early_frac
 
     # --- the same steps with every particle through the FP32-mixed code (no far-field path)
     single = None
