@@ -692,7 +692,8 @@ def run_disk(args, dist):
     layers = dict(wl.layers)
     sim = Simulation(wl.n, wl.n, wl.n, wl.m, wl.a, wl.c, wl.dt, precision="fp32_mixed", quad_order=args.quad,
                      **layers)
-    sim.set_tuning(sort_interval=args.sort_interval)
+    tuning = json.loads(args.tuning) if args.tuning else {"sort_interval": args.sort_interval}
+    sim.set_tuning(**tuning)
     sim.set_uniform_field(B=(0.0, 0.0, wl.B0))
     for s, sp in enumerate(wl.species):
         sim.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.u4, sp.ids, umode=sp.umode)
@@ -720,7 +721,7 @@ def run_disk(args, dist):
                                    "e-/ion (mass ratio 20), B_z=0.1, dt=0.4",
                        "absorbing_layers": layers,
                        "particles": npart, "inner_edge_particles_per_cell": geo["n0"],
-                       "sort_interval": args.sort_interval},
+                       "tuning": tuning},
             "gpu_launches": int(launches),
             "stage_ms_per_step": {k: round(v[0] / max(1, args.steps), 4) for k, v in prof.items()},
             "clocks": clk,
