@@ -510,7 +510,8 @@ __device__ __forceinline__ void interval_means(float x, float2 M[5]) {
 __device__ __forceinline__ void table_areas(const float4* __restrict__ t, float u, float v, float w, float& A00,
                                             float& A10, float& A01, float& A11) {
   float c[kFitTerms];
-  const float4 e = __ldg(t);
+  // streaming loads (evicted from L1 and L2 first): a cell's fits serve its own particles only
+  const float4 e = __ldcs(t);
   c[0] = e.x;
   c[1] = e.y;
   c[5] = e.z;
@@ -518,7 +519,7 @@ __device__ __forceinline__ void table_areas(const float4* __restrict__ t, float 
   float hv[32];  // the FP16 terms in term order
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(t + 1 + q));
+    const uint4 w4 = __ldcs(reinterpret_cast<const uint4*>(t + 1 + q));
     const unsigned wd[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -897,10 +898,12 @@ __device__ __forceinline__ Move<T> push_move(const Grid& g, const Fields<T>& F, 
 #pragma unroll
   for (int q = 0; q < 3; ++q)
     if (!(fabs(x1[q] - x0[q]) < T(1))) flags |= ST_CFL;
+  // the new state is read again only by the next step (or the sort): streaming stores, evicted
+  // from L2 first, so that the fields, J and the area fits the other warps gather stay resident
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    P.x[q][i] = x1[q];
-    P.u[q][i] = u1[q];
+    __stcs(P.x[q] + i, x1[q]);
+    __stcs(P.u[q] + i, u1[q]);
   }
   // removal (r <= r_+ or outside [1, n-2]) and the sort key
   bool outer = !finite;
@@ -922,11 +925,11 @@ __device__ __forceinline__ Move<T> push_move(const Grid& g, const Fields<T>& F, 
     }
   }
   if (horizon || outer) {
-    *key_out = kDead;
+    __stcs(key_out, kDead);
     atomicAdd(horizon ? &st->removed_horizon : &st->removed_outer, 1ull);
   } else {
     const int ci = (int)floor(x1[0]), cj = (int)floor(x1[1]), ck = (int)floor(x1[2]);
-    *key_out = (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci);
+    __stcs(key_out, (uint32_t)(((long long)ck * g.ny + cj) * g.nx + ci));
   }
   if (fb) atomicAdd(&st->fallbacks, 1ull);
   Move<T> mv;
