@@ -49,10 +49,10 @@ FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9
 # dram__bytes_write of one launch over its particles), from ncu captures at the bench size, per
 # variant (far-field area fits on or off, resident blocks per SM), valid for the push sources whose
 # hash is recorded with them.
-PUSH_TRAFFIC = {"sha": "8be567d1def726c2",
-                "bytes_per_particle": {"area_table0_minb4": 1380.9e6 / 15.61e6,
-                                       "area_table0_minb5": 1401.0e6 / 15.61e6,
-                                       "area_table1_minb5": 2013.2e6 / 15.61e6}}
+PUSH_TRAFFIC = {"sha": "6af44e8d10042355",
+                "bytes_per_particle": {"area_table0_minb4": 1371.6e6 / 15.61e6,
+                                       "area_table0_minb5": 1376.4e6 / 15.61e6,
+                                       "area_table1_minb5": 2073.7e6 / 15.61e6}}
 
 
 def push_variant(tuning):

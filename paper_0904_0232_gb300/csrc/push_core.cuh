@@ -898,8 +898,7 @@ __device__ __forceinline__ Move<T> push_move(const Grid& g, const Fields<T>& F, 
 #pragma unroll
   for (int q = 0; q < 3; ++q)
     if (!(fabs(x1[q] - x0[q]) < T(1))) flags |= ST_CFL;
-  // the new state is read again only by the next step (or the sort): streaming stores, evicted
-  // from L2 first, so that the fields, J and the area fits the other warps gather stay resident
+  // streaming (evict-first) stores: the new state is read again only by the next step or the sort
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     __stcs(P.x[q] + i, x1[q]);
