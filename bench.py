@@ -530,6 +530,12 @@ def run_gpu(args, dist):
     return line
 
 
+def planar_head(buf, n):
+    """The (4, n) planar array grpic_get_particles wrote into the front of buf: its planes are n
+    (the count written) apart, not buf's row length (the capacity)."""
+    return buf.reshape(-1)[:4 * n].reshape(4, n)
+
+
 def late_window(wl, args, dist, tuning, host_out, counts, fields_out, summary):
     """The FP64 path against the FP32-mixed path at the END of the measured window, where the most
     particles have gathered near the hole: both start from the state the end-to-end leg read back
@@ -548,10 +554,8 @@ def late_window(wl, args, dist, tuning, host_out, counts, fields_out, summary):
                 s_.set_tuning(**tuning)
             s_.set_fields(fields_out[0], fields_out[1])
             for sidx, (sp, (x, u, i), nn) in enumerate(zip(wl.species, host_out, counts)):
-                # planes of the read-back are nn apart (the count written), not the buffers' capacity
-                x4 = x.reshape(-1)[:4 * nn].reshape(4, nn)
-                u4 = u.reshape(-1)[:4 * nn].reshape(4, nn)
-                s_.load_particles(sidx, sp.q_over_m, sp.q_macro, x4, u4, i[:nn], umode=GRPIC_U_FULL)
+                s_.load_particles(sidx, sp.q_over_m, sp.q_macro, planar_head(x, nn), planar_head(u, nn), i[:nn],
+                                  umode=GRPIC_U_FULL)
             s_.set_profiling(True)
             s_.step(1)
             ms_, ps_, prof_, _ = timed_steps(s_, args.fp64_late_steps, dist)
