@@ -206,10 +206,10 @@ def cpu_sample_workload():
     return synth.subsample(synth.kerr_ion_electron_128(seed=2, n=40), 20000)
 
 
-def run_oracle_steps(wl, steps, warmup=0):
+def run_oracle_steps(wl, steps, warmup=0, threads=0):
     import oracle as O
 
-    o = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=0)
+    o = O.Oracle(wl.nx, wl.ny, wl.nz, wl.m, wl.a, wl.c, wl.dt, threads=threads)
     o.init_uniform_field(B=(0.0, 0.0, wl.B0))
     for s, sp in enumerate(wl.species):
         o.load_particles(s, sp.q_over_m, sp.q_macro, sp.x4, sp.usp, sp.ids, umode=1)
@@ -227,15 +227,22 @@ def run_oracle_steps(wl, steps, warmup=0):
         psteps += n
     el = time.perf_counter() - t0
     del n_before
-    return psteps, el, O.max_threads(), per_step
+    return psteps, el, (threads if threads > 0 else O.max_threads()), per_step
 
 
-def cpu_baseline(steps=150):
+def cpu_baseline(steps=150, single_thread_steps=5):
+    """The oracle on all host cores over `steps` steps of the sample, and on one thread over its
+    first `single_thread_steps` steps."""
     wl = cpu_sample_workload()
     psteps, el, cores, _ = run_oracle_steps(wl, steps)
-    return {"value": psteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, Kerr a=0.9m m=4 on a {wl.nx}^3 window, {wl.n_particles} particles "
-                      f"(2 species), {steps} whole steps incl. field solve; {el:.1f} s wall"}
+    out = {"value": psteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle, Kerr a=0.9m m=4 on a {wl.nx}^3 window, {wl.n_particles} particles "
+                     f"(2 species), {steps} whole steps incl. field solve; {el:.1f} s wall"}
+    if single_thread_steps > 0:
+        ps1, el1, _, _ = run_oracle_steps(wl, single_thread_steps, threads=1)
+        out["single_thread"] = {"value": ps1 / el1, "unit": UNIT, "cores": 1,
+                                "sample": f"the first {single_thread_steps} steps of the same sample; {el1:.1f} s wall"}
+    return out
 
 
 def run_reference(args, dist):
